@@ -1,0 +1,148 @@
+"""Pins for the oracle's k-means, product quantizer, inverted file and IVFADC search."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_08734_gb300 import datagen
+
+
+def test_kmeans_single_centroid_is_global_mean():
+    x = datagen.gaussian_matrix(31, 999, 12)
+    c, obj, _ = oracle.kmeans(x, [17], 3)
+    np.testing.assert_array_equal(c[0], x.astype(np.float64).mean(0).astype(np.float32))
+    # objective before the 2nd update is the total scatter around the mean
+    mu = x.astype(np.float64).mean(0)
+    np.testing.assert_allclose(obj[1], ((x - mu) ** 2).sum(), rtol=1e-6)
+
+
+def test_kmeans_n_equals_k_reaches_zero():
+    x = datagen.gaussian_matrix(32, 64, 6)
+    c, obj, _ = oracle.kmeans(x, np.arange(64)[::-1], 2)
+    assert obj[0] == 0.0 and obj[1] == 0.0
+    assert sorted(map(tuple, c.tolist())) == sorted(map(tuple, x.tolist()))
+
+
+def test_kmeans_objective_non_increasing_and_sklearn():
+    x = datagen.mixture_points(datagen.mixture_centres(33, 20, 8), 34, 4000)
+    init = datagen.permutation_prefix(35, x.shape[0], 20)
+    c, obj, splits = oracle.kmeans(x, init, 12)
+    assert splits == 0
+    assert np.all(np.diff(obj) <= 1e-9 * obj[0])
+    sk = pytest.importorskip("sklearn.cluster")
+    km = sk.KMeans(n_clusters=20, init=x[init].astype(np.float64), n_init=1, max_iter=12,
+                   tol=0.0, algorithm="lloyd").fit(x.astype(np.float64))
+    if km.n_iter_ == 12:  # same number of updates (sklearn stops early at a fixed point)
+        np.testing.assert_allclose(c, km.cluster_centers_, rtol=1e-5, atol=1e-5)
+
+
+def test_kmeans_well_separated_clusters_recovered():
+    centres = np.eye(5, 16, dtype=np.float32) * 100
+    x = np.repeat(centres, 50, axis=0) + datagen.gaussian_matrix(36, 250, 16) * 0.01
+    init = np.arange(0, 250, 50)
+    c, _, _ = oracle.kmeans(x, init, 5)
+    for j in range(5):
+        np.testing.assert_allclose(c[j], x[j * 50:(j + 1) * 50].astype(np.float64).mean(0),
+                                   rtol=1e-6, atol=1e-6)
+
+
+def test_kmeans_empty_cluster_split_rule():
+    # Two identical initial rows: ties go to the lower centroid, so centroid 1 is empty
+    # after the first assignment and is re-seeded by splitting the largest cluster.
+    x = np.array([[1.0, 2.0], [1.0, 2.0], [1.5, 2.5], [10.0, 10.0]], np.float32)
+    c, _, splits = oracle.kmeans(x, [0, 1, 3], 1)
+    assert splits == 1
+    mean0 = np.array([(1 + 1 + 1.5) / 3, (2 + 2 + 2.5) / 3])
+    g = np.array([1.0, -1.0])
+    np.testing.assert_array_equal(c[1], (mean0.astype(np.float32).astype(np.float64)
+                                         * (1 + g / 1024)).astype(np.float32))
+    np.testing.assert_array_equal(c[0], (mean0.astype(np.float32).astype(np.float64)
+                                         * (1 - g / 1024)).astype(np.float32))
+    np.testing.assert_array_equal(c[2], [10.0, 10.0])
+
+
+def test_ivf_bucket_is_stable_argsort():
+    lists = datagen.randint(41, 0, 5000, 37)
+    off, order = oracle.ivf_bucket(lists, 37)
+    np.testing.assert_array_equal(order, np.argsort(lists, kind="stable"))
+    np.testing.assert_array_equal(np.diff(off), np.bincount(lists, minlength=37))
+
+
+def test_encode_ties_to_lowest_centroid():
+    coarse = np.zeros((2, 4), np.float32)
+    coarse[1] = 5.0
+    pq = np.zeros((2, 256, 2), np.float32)
+    pq[:, :, 0] = np.arange(256)[None, :] * 0.0 + 7.0
+    pq[0, 9] = [0.5, 0.0]
+    pq[0, 3] = [0.5, 0.0]          # duplicate of 9: lower index 3 wins
+    pq[1, 200] = [0.0, 0.25]
+    x = np.array([[0.5, 0.0, 0.0, 0.25]], np.float32)
+    lists, codes = oracle.ivfpq_encode(x, coarse, pq)
+    assert lists.tolist() == [0] and codes.tolist() == [[3, 200]]
+
+
+def _tiny_index(seed, n=3000, d=16, nlist=8, M=4, niter=6):
+    cen = datagen.mixture_centres(seed, 12, d)
+    x = datagen.mixture_points(cen, seed + 1, n)
+    coarse, _, _ = oracle.kmeans(x, datagen.permutation_prefix(seed + 2, n, nlist), niter)
+    res = oracle.residual_training_set(x, coarse)
+    books = oracle.train_pq(res, M, datagen.permutation_prefix(seed + 3, n, 256), niter)
+    lists, codes = oracle.ivfpq_encode(x, coarse, books)
+    off, order = oracle.ivf_bucket(lists, nlist)
+    return x, coarse, books, off, codes[order], order.astype(np.int64)
+
+
+def test_adc_two_forms_agree_eq10():
+    x, coarse, books, off, codes, ids = _tiny_index(50)
+    xq = datagen.mixture_points(datagen.mixture_centres(50, 12, 16), 60, 20)
+    Dr, Ir = oracle.ivfadc_search(xq, coarse, books, off, codes, ids, 30, 3, form="recon")
+    Dl, Il = oracle.ivfadc_search(xq, coarse, books, off, codes, ids, 30, 3, form="lut")
+    np.testing.assert_allclose(Dr, Dl, rtol=1e-12)
+    np.testing.assert_array_equal(Ir, Il)
+
+
+def test_ivfadc_full_probe_equals_brute_force_over_reconstructions():
+    x, coarse, books, off, codes, ids = _tiny_index(70)
+    lists = np.repeat(np.arange(coarse.shape[0]), np.diff(off))
+    M, _, dsub = books.shape
+    recon = coarse[lists].astype(np.float64) + np.concatenate(
+        [books[m][codes[:, m]].astype(np.float64) for m in range(M)], axis=1)
+    xq = datagen.gaussian_matrix(71, 15, 16) * 2
+    D, I = oracle.ivfadc_search(xq, coarse, books, off, codes, ids, 25, coarse.shape[0])
+    for q in range(xq.shape[0]):
+        dist = ((recon - xq[q].astype(np.float64)) ** 2).sum(1)
+        order = np.lexsort((ids, dist))[:25]
+        np.testing.assert_array_equal(I[q], ids[order])
+        np.testing.assert_allclose(D[q], dist[order], rtol=1e-12)
+
+
+def test_lossless_pq_makes_ivfadc_exact():
+    # Residual sub-vectors take <= 256 distinct values, so the product quantizer can be
+    # lossless; with every list probed, IVFADC then equals exact search (Eq. 6 = Eq. 1).
+    d, M, n, nlist = 8, 4, 600, 4
+    coarse = (np.arange(nlist, dtype=np.float32)[:, None] * 50.0).repeat(d, 1)
+    L = datagen.randint(80, 0, n, nlist)
+    sub = (datagen.randint(81, 0, n * M, 16).reshape(n, M) - 8).astype(np.float32)
+    resid = np.repeat(sub, d // M, axis=1) * np.float32(0.5)
+    x = (coarse[L] + resid).astype(np.float32)
+    lists_chk, _ = oracle.assign(x, coarse)
+    assert np.array_equal(lists_chk, L)
+    books = np.zeros((M, 256, d // M), np.float32)
+    books[:, :16, :] = ((np.arange(16) - 8) * 0.5)[None, :, None]
+    books[:, 16:, :] = 1e6
+    lists, codes = oracle.ivfpq_encode(x, coarse, books)
+    off, order = oracle.ivf_bucket(lists, nlist)
+    xq = datagen.gaussian_matrix(82, 12, d) * 40
+    D, I = oracle.ivfadc_search(xq, coarse, books, off, codes[order], order, 10, nlist)
+    De, Ie = oracle.knn(xq, x, 10)
+    np.testing.assert_array_equal(I, Ie)
+    np.testing.assert_allclose(D, De, rtol=1e-12)
+
+
+def test_ivfadc_pads_when_fewer_than_k():
+    x, coarse, books, off, codes, ids = _tiny_index(90, n=400, nlist=8)
+    xq = x[:3]
+    D, I = oracle.ivfadc_search(xq, coarse, books, off, codes, ids, 150, 1)
+    for q in range(3):
+        got = int((I[q] >= 0).sum())
+        assert np.all(I[q, got:] == -1) and np.all(np.isinf(D[q, got:]))
+        assert np.all(np.diff(D[q, :got]) >= 0)
