@@ -1,0 +1,73 @@
+// Shared host-side plumbing of the CUDA library: status codes, the thread-local error
+// message, the scratch allocator hook and cached device properties.
+#pragma once
+#include <cstdint>
+#include <cstdio>
+#include <cuda_runtime.h>
+#include <string>
+
+#include "../../include/gbknn.h"
+
+namespace gbk {
+
+// Records a message for gbk_last_error() and returns the status.
+gbk_status set_error(gbk_status st, const char* fmt, ...);
+gbk_status clear_error();
+
+// Scratch memory from the installed allocator (default: the stream-ordered pool).
+void* scratch_alloc(size_t bytes, cudaStream_t stream, gbk_status* st);
+void scratch_free(void* p, cudaStream_t stream);
+
+struct DeviceInfo {
+  int device;
+  int sm_count;
+  size_t smem_optin;
+};
+const DeviceInfo& device_info();
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// RAII scratch buffer (freed stream-ordered at scope exit).
+struct Scratch {
+  void* p = nullptr;
+  cudaStream_t stream = nullptr;
+  Scratch() = default;
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  gbk_status alloc(size_t bytes, cudaStream_t s) {
+    gbk_status st = GBK_OK;
+    stream = s;
+    p = bytes ? scratch_alloc(bytes, s, &st) : nullptr;
+    return st;
+  }
+  ~Scratch() {
+    if (p) scratch_free(p, stream);
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+}  // namespace gbk
+
+#define GBK_CUDA_CHECK(expr)                                                                 \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return ::gbk::set_error(GBK_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #expr,          \
+                              cudaGetErrorString(e_));                                       \
+  } while (0)
+
+#define GBK_LAUNCH_CHECK()                                                                   \
+  do {                                                                                       \
+    cudaError_t e_ = cudaGetLastError();                                                     \
+    if (e_ != cudaSuccess)                                                                   \
+      return ::gbk::set_error(GBK_ECUDA, "%s:%d launch: %s", __FILE__, __LINE__,            \
+                              cudaGetErrorString(e_));                                       \
+  } while (0)
+
+#define GBK_REQUIRE(cond, ...)                                                               \
+  do {                                                                                       \
+    if (!(cond)) return ::gbk::set_error(GBK_EINVAL, __VA_ARGS__);                           \
+  } while (0)

@@ -1,0 +1,352 @@
+// Standalone row-wise k-selection (section 2 "k-selection" and section 4's goal: one
+// pass over the input at memory bandwidth).
+//
+// One thread block per (row, segment).  Threads stream the segment with 16-byte
+// loads (cache-streaming), compare each value once against the block threshold and
+// append the rare survivors to a shared buffer (select_core.cuh).  Long rows are cut
+// into segments when there are too few rows to fill the GPU; each segment leaves its
+// k best composites in scratch and a merge kernel selects across segments - the
+// paper's two-pass k-selection (section 5.3, "Multi-pass kernels").  k = 1 is a plain
+// argmin/argmax reduction (section 6.2 notes that k = 1 needs no selection structure).
+#include <algorithm>
+
+#include "common.cuh"
+#include "kselect.cuh"
+#include "select_core.cuh"
+
+namespace gbk {
+
+namespace {
+
+template <int THREADS, int KP, int UNROLL, bool LARGEST>
+struct KselCfg {
+  static constexpr int CHUNK = THREADS * UNROLL * 4;
+  static constexpr int CAP = 2 * CHUNK;
+  using Sel = BlockSelect<THREADS, KP, CAP>;
+  static constexpr size_t SMEM = sizeof(typename Sel::Smem);
+};
+
+template <int THREADS, int KP, int UNROLL, bool LARGEST>
+__global__ void __launch_bounds__(THREADS)
+    kselect_rows_kernel(const float* __restrict__ vals, int64_t len, int k, int segs,
+                        int64_t seg_len, float* __restrict__ outD, int64_t* __restrict__ outI,
+                        uint64_t* __restrict__ part) {
+  using C = KselCfg<THREADS, KP, UNROLL, LARGEST>;
+  using Sel = typename C::Sel;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int64_t row = blockIdx.x / segs;
+  const int seg = blockIdx.x % segs;
+  const float* rowp = vals + row * len;
+  const int64_t s0 = (int64_t)seg * seg_len;
+  const int64_t s1 = min(len, s0 + seg_len);
+  const int64_t n = s1 - s0;
+  const float* p = rowp + s0;
+
+  Sel::init(s);
+  __syncthreads();
+  ValueFilter f;
+  f.set(NAN_KEY, LARGEST);
+
+  // scalar head (until 16-byte alignment) and tail
+  const int64_t head_e = (int64_t)(((16u - ((uintptr_t)p & 15u)) & 15u) / 4);
+  const int head = (int)(n < head_e ? n : head_e);
+  const int64_t n4 = (n - head) / 4;
+  const int tail = (int)(n - head - n4 * 4);
+  {
+    uint64_t c[1];
+    uint32_t mask = 0;
+    int64_t e = -1;
+    if (tid < head) e = tid;
+    else if (tid >= 32 && tid < 32 + tail) e = head + n4 * 4 + (tid - 32);
+    if (e >= 0) {
+      float v = p[e];
+      if (f.pass(v)) {
+        c[0] = composite(ordered_key(v, LARGEST), (uint32_t)(s0 + e));
+        mask = 1u;
+      }
+    }
+    Sel::template push<1>(s, mask, c);
+  }
+  const float4* p4 = reinterpret_cast<const float4*>(p + head);
+  const uint32_t idx0 = (uint32_t)(s0 + head);
+  for (int64_t base = 0; base < n4; base += (int64_t)THREADS * UNROLL) {
+    float4 v[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; u++) {
+      const int64_t i = base + u * THREADS + tid;
+      if (i < n4) v[u] = __ldcs(p4 + i);
+    }
+    uint64_t c[UNROLL * 4];
+    uint32_t mask = 0;
+#pragma unroll
+    for (int u = 0; u < UNROLL; u++) {
+      const int64_t i = base + u * THREADS + tid;
+      if (i < n4) {
+        const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          if (f.pass(x[j])) {
+            mask |= 1u << (u * 4 + j);
+            c[u * 4 + j] = composite(ordered_key(x[j], LARGEST), idx0 + (uint32_t)(i * 4 + j));
+          }
+        }
+      }
+    }
+    Sel::template push<UNROLL * 4>(s, mask, c);
+    __syncthreads();
+    if (s.n_buf > C::CAP - C::CHUNK) {
+      Sel::compact(s, k);
+      f.set((uint32_t)(s.thr >> 32), LARGEST);
+    }
+  }
+  Sel::finish(s, k);
+  if (segs == 1) {
+    for (int j = tid; j < k; j += THREADS) {
+      const uint64_t e = s.top[j];
+      const uint32_t idx = (uint32_t)e;
+      outD[row * k + j] = rowp[idx];
+      outI[row * k + j] = (int64_t)idx;
+    }
+  } else {
+    uint64_t* dst = part + ((int64_t)row * segs + seg) * k;
+    for (int j = tid; j < k; j += THREADS) dst[j] = s.top[j];
+  }
+}
+
+// k = 1: every thread keeps its best (key, index) - indices grow along a thread's walk,
+// so a strict compare keeps the lowest index among equal keys - then a block reduction.
+template <int THREADS, bool LARGEST>
+__global__ void __launch_bounds__(THREADS)
+    kselect_k1_kernel(const float* __restrict__ vals, int64_t len, int segs, int64_t seg_len,
+                      float* __restrict__ outD, int64_t* __restrict__ outI,
+                      uint64_t* __restrict__ part) {
+  __shared__ uint64_t red[THREADS / 32];
+  const int tid = threadIdx.x;
+  const int64_t row = blockIdx.x / segs;
+  const int seg = blockIdx.x % segs;
+  const float* rowp = vals + row * len;
+  const int64_t s0 = (int64_t)seg * seg_len;
+  const int64_t s1 = min(len, s0 + seg_len);
+  const int64_t n = s1 - s0;
+  const float* p = rowp + s0;
+  const int64_t head_e = (int64_t)(((16u - ((uintptr_t)p & 15u)) & 15u) / 4);
+  const int head = (int)(n < head_e ? n : head_e);
+  const int64_t n4 = (n - head) / 4;
+  const int tail = (int)(n - head - n4 * 4);
+  uint64_t best = ~0ull;
+  if (tid < head) best = composite(ordered_key(p[tid], LARGEST), (uint32_t)(s0 + tid));
+  if (tid >= 32 && tid < 32 + tail) {
+    const int64_t e = head + n4 * 4 + (tid - 32);
+    best = min(best, composite(ordered_key(p[e], LARGEST), (uint32_t)(s0 + e)));
+  }
+  uint32_t bk = (uint32_t)(best >> 32), bi = (uint32_t)best;
+  const float4* p4 = reinterpret_cast<const float4*>(p + head);
+  const uint32_t idx0 = (uint32_t)(s0 + head);
+  constexpr int UNROLL = 4;
+  for (int64_t base = 0; base < n4; base += (int64_t)THREADS * UNROLL) {
+    float4 v[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; u++) {
+      const int64_t i = base + u * THREADS + tid;
+      if (i < n4) v[u] = __ldcs(p4 + i);
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; u++) {
+      const int64_t i = base + u * THREADS + tid;
+      if (i < n4) {
+        const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const uint32_t key = ordered_key(x[j], LARGEST);
+          const uint32_t idx = idx0 + (uint32_t)(i * 4 + j);
+          // head/tail elements may carry larger indices than body ones: full compare
+          if (key < bk || (key == bk && idx < bi)) {
+            bk = key;
+            bi = idx;
+          }
+        }
+      }
+    }
+  }
+  best = composite(bk, bi);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(FULL_MASK, best, o));
+  if ((tid & 31) == 0) red[tid >> 5] = best;
+  __syncthreads();
+  if (tid < 32) {
+    best = tid < THREADS / 32 ? red[tid] : ~0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(FULL_MASK, best, o));
+    if (tid == 0) {
+      if (segs == 1) {
+        const uint32_t idx = (uint32_t)best;
+        outD[row] = rowp[idx];
+        outI[row] = (int64_t)idx;
+      } else {
+        part[row * segs + seg] = best;
+      }
+    }
+  }
+}
+
+// Selection across the segments' partial results (already composites).
+template <int THREADS, int KP>
+__global__ void __launch_bounds__(THREADS)
+    kselect_merge_kernel(const uint64_t* __restrict__ part, int64_t nper, int k,
+                         const float* __restrict__ vals, int64_t len, float* __restrict__ outD,
+                         int64_t* __restrict__ outI) {
+  constexpr int CAP = 4096;
+  using Sel = BlockSelect<THREADS, KP, CAP>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(smem_raw);
+  const int64_t row = blockIdx.x;
+  const uint64_t* src = part + row * nper;
+  Sel::init(s);
+  __syncthreads();
+  uint64_t thr = ~0ull;
+  for (int64_t base = 0; base < nper; base += THREADS) {
+    const int64_t i = base + threadIdx.x;
+    uint64_t c[1];
+    uint32_t mask = 0;
+    if (i < nper) {
+      c[0] = src[i];
+      mask = (c[0] != ~0ull && c[0] <= thr) ? 1u : 0u;
+    }
+    Sel::template push<1>(s, mask, c);
+    __syncthreads();
+    if (s.n_buf > CAP - THREADS) {
+      Sel::compact(s, k);
+      thr = s.thr;
+    }
+  }
+  Sel::finish(s, k);
+  const float* rowp = vals + row * len;
+  for (int j = threadIdx.x; j < k; j += THREADS) {
+    const uint64_t e = s.top[j];
+    const uint32_t idx = (uint32_t)e;
+    outD[row * k + j] = rowp[idx];
+    outI[row * k + j] = (int64_t)idx;
+  }
+}
+
+template <int THREADS, int KP, int UNROLL, bool LARGEST>
+gbk_status launch_rows(const float* vals, int64_t rows, int64_t len, int k, int segs,
+                       int64_t seg_len, float* D, int64_t* I, uint64_t* part,
+                       cudaStream_t stream) {
+  using C = KselCfg<THREADS, KP, UNROLL, LARGEST>;
+  auto kern = kselect_rows_kernel<THREADS, KP, UNROLL, LARGEST>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)C::SMEM));
+    attr_set = true;
+  }
+  kern<<<(unsigned)(rows * segs), THREADS, C::SMEM, stream>>>(vals, len, k, segs, seg_len, D, I,
+                                                                part);
+  GBK_LAUNCH_CHECK();
+  return GBK_OK;
+}
+
+template <int KP>
+gbk_status launch_merge(const uint64_t* part, int64_t rows, int64_t nper, int k,
+                        const float* vals, int64_t len, float* D, int64_t* I,
+                        cudaStream_t stream) {
+  constexpr int THREADS = 256;
+  using Sel = BlockSelect<THREADS, KP, 4096>;
+  auto kern = kselect_merge_kernel<THREADS, KP>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sizeof(typename Sel::Smem)));
+    attr_set = true;
+  }
+  kern<<<(unsigned)rows, THREADS, sizeof(typename Sel::Smem), stream>>>(part, nper, k, vals, len,
+                                                                         D, I);
+  GBK_LAUNCH_CHECK();
+  return GBK_OK;
+}
+
+template <bool LARGEST>
+gbk_status dispatch_rows(const float* vals, int64_t rows, int64_t len, int k, int segs,
+                         int64_t seg_len, float* D, int64_t* I, uint64_t* part,
+                         cudaStream_t st, const KselectTuning& tu) {
+  const bool wide = tu.unroll >= 4;
+#define GBK_ROWS(KP)                                                                         \
+  return wide ? launch_rows<256, KP, 4, LARGEST>(vals, rows, len, k, segs, seg_len, D, I,  \
+                                                 part, st)                                  \
+              : launch_rows<256, KP, 2, LARGEST>(vals, rows, len, k, segs, seg_len, D, I,  \
+                                                 part, st)
+  if (k <= 32) GBK_ROWS(32);
+  if (k <= 64) GBK_ROWS(64);
+  if (k <= 128) GBK_ROWS(128);
+  if (k <= 256) GBK_ROWS(256);
+  if (k <= 512) GBK_ROWS(512);
+  GBK_ROWS(1024);
+#undef GBK_ROWS
+}
+
+gbk_status dispatch_merge(const uint64_t* part, int64_t rows, int64_t nper, int k,
+                          const float* vals, int64_t len, float* D, int64_t* I,
+                          cudaStream_t st) {
+  if (k <= 32) return launch_merge<32>(part, rows, nper, k, vals, len, D, I, st);
+  if (k <= 64) return launch_merge<64>(part, rows, nper, k, vals, len, D, I, st);
+  if (k <= 128) return launch_merge<128>(part, rows, nper, k, vals, len, D, I, st);
+  if (k <= 256) return launch_merge<256>(part, rows, nper, k, vals, len, D, I, st);
+  if (k <= 512) return launch_merge<512>(part, rows, nper, k, vals, len, D, I, st);
+  return launch_merge<1024>(part, rows, nper, k, vals, len, D, I, st);
+}
+
+}  // namespace
+
+KselectTuning kselect_default_tuning(int64_t rows, int64_t len, int k) {
+  KselectTuning t;
+  const int sms = device_info().sm_count;
+  t.unroll = (k > 256) ? 4 : 2;
+  // enough blocks to fill the GPU several times over; segments no shorter than 8K
+  const int64_t target = 4ll * sms;
+  int64_t segs = 1;
+  if (rows < target) {
+    const int64_t min_seg = std::max<int64_t>(8192, 8ll * k);
+    segs = std::min<int64_t>((target + rows - 1) / rows, std::max<int64_t>(1, len / min_seg));
+    segs = std::max<int64_t>(1, std::min<int64_t>(segs, 4096));
+  }
+  t.segs = (int)segs;
+  return t;
+}
+
+gbk_status kselect_run(const float* vals, int64_t rows, int64_t len, int k, bool largest,
+                       float* D, int64_t* I, cudaStream_t st, const KselectTuning* tuning) {
+  if (rows == 0) return GBK_OK;
+  KselectTuning tu = tuning ? *tuning : kselect_default_tuning(rows, len, k);
+  int64_t segs = std::max(1, tu.segs);
+  int64_t seg_len = (len + segs - 1) / segs;
+  seg_len = (seg_len + 3) & ~int64_t(3);
+  segs = (len + seg_len - 1) / seg_len;
+  Scratch part;
+  if (segs > 1) {
+    gbk_status r = part.alloc(sizeof(uint64_t) * (size_t)(rows * segs * k), st);
+    if (r != GBK_OK) return r;
+  }
+  uint64_t* pp = part.as<uint64_t>();
+  gbk_status r;
+  if (k == 1) {
+    if (largest)
+      kselect_k1_kernel<256, true><<<(unsigned)(rows * segs), 256, 0, st>>>(vals, len, (int)segs,
+                                                                           seg_len, D, I, pp);
+    else
+      kselect_k1_kernel<256, false><<<(unsigned)(rows * segs), 256, 0, st>>>(vals, len, (int)segs,
+                                                                            seg_len, D, I, pp);
+    GBK_LAUNCH_CHECK();
+    r = GBK_OK;
+  } else {
+    r = largest ? dispatch_rows<true>(vals, rows, len, k, (int)segs, seg_len, D, I, pp, st, tu)
+                : dispatch_rows<false>(vals, rows, len, k, (int)segs, seg_len, D, I, pp, st, tu);
+  }
+  if (r != GBK_OK || segs == 1) return r;
+  const int64_t nper = segs * (k == 1 ? 1 : k);
+  return dispatch_merge(pp, rows, nper, k, vals, len, D, I, st);
+}
+
+}  // namespace gbk

@@ -1,0 +1,274 @@
+// Block-wide streaming k-selection used by every selecting kernel of the library.
+//
+// Definition followed: section 2 "k-selection" of the paper (the k lowest values of an
+// array, sorted, with their indices).  The kernels never keep a sorted order while
+// streaming.  Instead:
+//   * every candidate is a 64-bit composite  (ordered 32-bit key << 32) | 32-bit index,
+//     where the ordered key maps float order to unsigned order (NaN worst, -0 == +0).
+//     Composite order is then the library's total order: value first, lower index on
+//     ties, so one unsigned compare settles everything and all composites are distinct;
+//   * threads filter incoming values against the block's threshold (the value of the
+//     k-th best composite seen so far) held in a register, and append survivors to a
+//     shared-memory buffer with one atomic per warp;
+//   * when the buffer nears capacity the block computes the exact k best of
+//     (kept set U buffer) with an MSB-first radix select over the composites and keeps
+//     only those; the threshold drops to their maximum.
+// The paper's own design (WarpSelect: per-lane register queues merged with odd-size
+// bitonic networks, section 4) is prior art for Maxwell; this one spends shared memory
+// instead of registers, which sm_103a has in abundance (228 KB per SM), and touches each
+// input element with one compare.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gbk {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+constexpr uint32_t NAN_KEY = 0xffffffffu;
+
+// Map a float to an unsigned key whose order is the selection order.  `largest`
+// selects the highest values: the key of v is then the key of -v.
+__device__ __forceinline__ uint32_t ordered_key(float v, bool largest) {
+  if (largest) v = -v;
+  uint32_t b = __float_as_uint(v);
+  if (v != v) return NAN_KEY;
+  if (b == 0x80000000u) b = 0u;  // -0 ranks with +0
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Inverse of ordered_key for non-NaN keys (returns the value in the original sense).
+__device__ __forceinline__ float key_value(uint32_t k, bool largest) {
+  uint32_t b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  float v = __uint_as_float(b);
+  return largest ? -v : v;
+}
+
+__device__ __forceinline__ uint64_t composite(uint32_t key, uint32_t idx) {
+  return ((uint64_t)key << 32) | (uint64_t)idx;
+}
+
+__device__ __forceinline__ uint64_t shr64(uint64_t x, int s) { return s >= 64 ? 0ull : (x >> s); }
+
+// Threshold filter in value space: pass(v) is true for every v whose key is <= the
+// threshold key (ties pass and are settled exactly at compaction).
+struct ValueFilter {
+  float thr;
+  bool nan_ok;
+  bool largest;
+  __device__ __forceinline__ void set(uint32_t thr_key, bool lg) {
+    largest = lg;
+    if (thr_key == NAN_KEY) {
+      nan_ok = true;
+      thr = lg ? -__int_as_float(0x7f800000) : __int_as_float(0x7f800000);
+    } else {
+      nan_ok = false;
+      thr = key_value(thr_key, lg);
+    }
+  }
+  __device__ __forceinline__ bool pass(float v) const {
+    return (largest ? (v >= thr) : (v <= thr)) || nan_ok;
+  }
+};
+
+template <int THREADS, int KP, int CAP>
+struct BlockSelect {
+  static_assert(THREADS % 32 == 0, "whole warps");
+  static_assert((KP & (KP - 1)) == 0 && KP >= 32, "KP power of two >= 32");
+  struct Smem {
+    uint64_t top[KP];   // kept set (unordered until finish)
+    uint64_t buf[CAP];  // candidates appended since the last compaction
+    uint32_t hist[256];
+    uint64_t thr;       // max kept composite once n_top == k, else ~0 (everything passes)
+    uint64_t diff, tmax, P;
+    int n_top, n_buf, need, shift, done, cnt;
+  };
+
+  __device__ static void init(Smem& s) {
+    if (threadIdx.x == 0) {
+      s.n_top = 0;
+      s.n_buf = 0;
+      s.thr = ~0ull;
+    }
+  }
+
+  // Warp-aggregated append.  Every lane of the warp must call it; lane l offers the
+  // composites c[j] for which bit j of `mask` is set.
+  template <int NV>
+  __device__ __forceinline__ static void push(Smem& s, uint32_t mask, const uint64_t (&c)[NV]) {
+    const int lane = threadIdx.x & 31;
+    if (!__any_sync(FULL_MASK, mask != 0u)) return;
+    int cnt = __popc(mask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(FULL_MASK, incl, o);
+      if (lane >= o) incl += t;
+    }
+    int base = 0;
+    if (lane == 31) base = atomicAdd(&s.n_buf, incl);
+    base = __shfl_sync(FULL_MASK, base, 31);
+    int pos = base + incl - cnt;
+#pragma unroll
+    for (int j = 0; j < NV; j++) {
+      if (mask & (1u << j)) s.buf[pos++] = c[j];
+    }
+  }
+
+  // Exact k best of top U buf; all threads call it after a __syncthreads().
+  __device__ static void compact(Smem& s, int k) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int n_top = s.n_top, n_buf = s.n_buf;
+    const int total = n_top + n_buf;
+    if (total <= k) {
+      for (int i = tid; i < n_buf; i += THREADS) s.top[n_top + i] = s.buf[i];
+      __syncthreads();
+      if (tid == 0) {
+        s.n_top = total;
+        s.n_buf = 0;
+        s.tmax = 0ull;
+      }
+      __syncthreads();
+      if (total == k) {
+        uint64_t m = 0ull;
+        for (int i = tid; i < total; i += THREADS) m = max(m, s.top[i]);
+        atomicMax((unsigned long long*)&s.tmax, (unsigned long long)m);
+        __syncthreads();
+        if (tid == 0) s.thr = s.tmax;
+      }
+      __syncthreads();
+      return;
+    }
+    // 1. bits shared by every element
+    const uint64_t x0 = n_top > 0 ? s.top[0] : s.buf[0];
+    if (tid == 0) s.diff = 0ull;
+    __syncthreads();
+    uint64_t dacc = 0ull;
+    for (int i = tid; i < total; i += THREADS) {
+      uint64_t e = i < n_top ? s.top[i] : s.buf[i - n_top];
+      dacc |= e ^ x0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dacc |= __shfl_xor_sync(FULL_MASK, dacc, o);
+    if (lane == 0 && dacc) atomicOr((unsigned long long*)&s.diff, (unsigned long long)dacc);
+    __syncthreads();
+    int shift = 64 - __clzll((long long)s.diff);  // distinct composites -> diff != 0
+    uint64_t P = shr64(x0, shift);
+    int need = k;
+    // 2. MSB-first radix select of the need-th smallest composite
+    for (;;) {
+      const int w = shift < 8 ? shift : 8;
+      const int nshift = shift - w;
+      const uint32_t dmask = (1u << w) - 1u;
+      for (int i = tid; i < 256; i += THREADS) s.hist[i] = 0u;
+      __syncthreads();
+      for (int i = tid; i < total; i += THREADS) {
+        uint64_t e = i < n_top ? s.top[i] : s.buf[i - n_top];
+        if (shr64(e, shift) == P) atomicAdd(&s.hist[(uint32_t)(e >> nshift) & dmask], 1u);
+      }
+      __syncthreads();
+      if (tid < 32) {
+        // lane owns bins [8*lane, 8*lane+8)
+        uint32_t h[8];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          h[j] = s.hist[lane * 8 + j];
+          sum += h[j];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          uint32_t t = __shfl_up_sync(FULL_MASK, incl, o);
+          if (lane >= o) incl += t;
+        }
+        uint32_t excl = incl - sum;
+        if (excl < (uint32_t)need && (uint32_t)need <= incl) {
+          uint32_t cum = excl;
+#pragma unroll
+          for (int j = 0; j < 8; j++) {
+            if (cum < (uint32_t)need && (uint32_t)need <= cum + h[j]) {
+              const int nneed = need - (int)cum;
+              s.need = nneed;
+              s.P = (P << w) | (uint64_t)(lane * 8 + j);
+              s.shift = nshift;
+              s.done = (h[j] == (uint32_t)nneed) || nshift == 0;
+            }
+            cum += h[j];
+          }
+        }
+      }
+      __syncthreads();
+      need = s.need;
+      P = s.P;
+      shift = s.shift;
+      const int done = s.done;
+      __syncthreads();
+      if (done) break;
+    }
+    // 3. keep e iff (e >> shift) <= P : exactly k elements
+    constexpr int TPT = (KP + THREADS - 1) / THREADS;
+    uint64_t mine[TPT];
+#pragma unroll
+    for (int j = 0; j < TPT; j++) {
+      int i = tid + j * THREADS;
+      mine[j] = i < n_top ? s.top[i] : ~0ull;
+    }
+    if (tid == 0) {
+      s.cnt = 0;
+      s.tmax = 0ull;
+    }
+    __syncthreads();
+    uint64_t m = 0ull;
+#pragma unroll
+    for (int j = 0; j < TPT; j++) {
+      int i = tid + j * THREADS;
+      if (i < n_top && shr64(mine[j], shift) <= P) {
+        int pos = atomicAdd(&s.cnt, 1);
+        s.top[pos] = mine[j];
+        m = max(m, mine[j]);
+      }
+    }
+    for (int i = tid; i < n_buf; i += THREADS) {
+      uint64_t e = s.buf[i];
+      if (shr64(e, shift) <= P) {
+        int pos = atomicAdd(&s.cnt, 1);
+        s.top[pos] = e;
+        m = max(m, e);
+      }
+    }
+    atomicMax((unsigned long long*)&s.tmax, (unsigned long long)m);
+    __syncthreads();
+    if (tid == 0) {
+      s.n_top = s.cnt;
+      s.n_buf = 0;
+      s.thr = s.tmax;
+    }
+    __syncthreads();
+  }
+
+  // Final compaction and ascending sort of the kept set into top[0..KP); padding ~0.
+  __device__ static void finish(Smem& s, int k) {
+    __syncthreads();
+    compact(s, k);
+    const int n = s.n_top;
+    for (int i = n + threadIdx.x; i < KP; i += THREADS) s.top[i] = ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= KP; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = threadIdx.x; t < KP / 2; t += THREADS) {
+          int lo = 2 * t - (t & (stride - 1));
+          int hi = lo + stride;
+          bool asc = (lo & size) == 0;
+          uint64_t a = s.top[lo], b = s.top[hi];
+          if ((a > b) == asc) {
+            s.top[lo] = b;
+            s.top[hi] = a;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+};
+
+}  // namespace gbk
