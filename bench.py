@@ -1,0 +1,303 @@
+"""Benchmark of the exact-search hot path on one GB300 (one JSON line on stdout).
+
+Workload (one "step"): the k-selection + exact k-NN configuration of the paper's section
+6.1/6.3 experiments at GB300 scale, on seeded synthetic data:
+  * k-selection of 10,000 rows x 65,536 float32 U[0,1) values for k = 1, 32, 256, 1024;
+  * exact squared-L2 k-NN of 10,000 queries against 1,000,000 database vectors, d = 128,
+    i.i.d. N(0,1), float32-accurate (TF32 hi/lo), k = 10 and k = 100.
+`value` is exact k-NN queries per second over the step's k-NN calls (20,000 queries per
+step).  All inputs (2.6 GB + 0.5 GB) exceed the 129 MB L2, so no flush is needed.
+
+--impl reference times the CPU oracle (plain double-precision C, all host cores) on a
+bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NQ, NB, D = 10000, 1000000, 128
+KSEL_ROWS, KSEL_LEN = 10000, 65536
+KSEL_K = (1, 32, 256, 1024)
+KNN_K = (10, 100)
+METRIC = "IVFPQ queries/s at fixed R@10 vs plain; exact k-NN q/s; k-select % of HBM peak"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), float(j["bf16_tflops"]), float(j.get("bf16_tflops_sustained", 0)), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.rows = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-i", os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0],
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        mhz = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for nm, v in zip(names, r[3:7]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        mhz.sort()
+        return {"sm_mhz": mhz[len(mhz) // 2] if mhz else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores: a bounded sample of the workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1702_08734_gb300 import datagen
+    nthreads = oracle.default_threads()
+    ks_rows, knn_q = 64, 8  # per step: 64 k-select rows x 4 k's, 8 queries x 2 k's over 1M
+    xb = datagen.gaussian_matrix(211, NB, D)
+    xq = datagen.gaussian_matrix(212, knn_q, D)
+    vals = datagen.uniform_matrix(201, ks_rows, KSEL_LEN)
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for k in KSEL_K:
+            oracle.kselect(vals, k, threads=nthreads)
+        tk = time.perf_counter()
+        for k in KNN_K:
+            oracle.knn(xq, xb, k, threads=nthreads)
+        t1 = time.perf_counter()
+        if it >= args.warmup:
+            times.append((t0, tk, t1))
+    knn_s = sum(t1 - tk for _, tk, t1 in times)
+    step_s = sum(t1 - t0 for t0, _, t1 in times) / len(times)
+    value = len(KNN_K) * knn_q * len(times) / knn_s
+    sample = "%d k-NN queries x k in %s over the full 1M x 128 database + %d k-select rows x k in %s per step" % (
+        knn_q, list(KNN_K), ks_rows, list(KSEL_K))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded N(0,1) / U[0,1))",
+        "config": {"workload": "exact k-NN nb=1e6 nq=1e4 d=128 k in {10,100} + k-select 1e4 x 65536",
+                   "l2_flush": "inputs larger than L2"},
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": "queries/s", "cores": nthreads,
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline_oracle():
+    """~10-30 s of oracle work on a bounded sample of the exact k-NN part."""
+    import oracle
+    from paper_1702_08734_gb300 import datagen
+    nthreads = oracle.default_threads()
+    xb = datagen.gaussian_matrix(211, NB, D)
+    xq = datagen.gaussian_matrix(212, 32, D)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle.knn(xq[:16], xb, 10, threads=nthreads)
+        n += 16
+        if time.perf_counter() - t0 > 10.0:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n / el, "unit": "queries/s", "cores": nthreads, "kind": "oracle",
+            "sample": "exact L2 k=10 for %d queries (16 per call) against the full 1M x 128 database, %.1f s" % (n, el)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+
+    import paper_1702_08734_gb300 as g
+    from paper_1702_08734_gb300 import datagen
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    g.load()
+    # replicas: every rank runs the full single-GPU workload (exact search does not shard
+    # without an extra merge; each GPU answers its own query batch)
+    vals = torch.from_numpy(datagen.uniform_matrix(201, KSEL_ROWS, KSEL_LEN)).cuda()
+    xb_h = datagen.gaussian_matrix(211, NB, D)
+    xq_h = datagen.gaussian_matrix(212 + 1000 * rank, NQ, D)
+    xb = torch.from_numpy(xb_h).cuda()
+    xq = torch.from_numpy(xq_h).cuda()
+    outs = {k: (torch.empty((KSEL_ROWS, k), device="cuda"),
+                torch.empty((KSEL_ROWS, k), dtype=torch.int64, device="cuda")) for k in KSEL_K}
+    kouts = {k: (torch.empty((NQ, k), device="cuda"),
+                 torch.empty((NQ, k), dtype=torch.int64, device="cuda")) for k in KNN_K}
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        for k in KSEL_K:
+            g.kselect(vals, k, out=outs[k])
+        if evs is not None:
+            evs.append(torch.cuda.Event(enable_timing=True))
+            evs[-1].record(stream)
+        for k in KNN_K:
+            g.knn_brute(xq, xb, k, out=kouts[k])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler()
+    clocks.start()
+    time.sleep(0.3)
+    g.profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    mids = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    starts = []
+    for _ in range(args.steps):
+        st = torch.cuda.Event(enable_timing=True)
+        st.record(stream)
+        starts.append(st)
+        step(mids)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g.profile_enable(False)
+    prof = g.profile_read()
+    clk = clocks.stop()
+    total_ms = e0.elapsed_time(e1)
+    ksel_ms = sum(starts[i].elapsed_time(mids[i]) for i in range(args.steps))
+    knn_ms = total_ms - ksel_ms
+    if world > 1:
+        t = torch.tensor([total_ms, knn_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, knn_ms = t.tolist()
+    queries = len(KNN_K) * NQ * args.steps * world
+    value = queries / (knn_ms / 1e3)
+    # per-kernel times from the library's own events
+    by = {}
+    for name, ms in prof:
+        by.setdefault(name, []).append(ms)
+    hbm, bf16, bf16s, src = peaks()
+    ks_ms = by.get("kselect_stream", [])
+    k1_ms = by.get("kselect_k1", [])
+    gemm_ms = by.get("dist_gemm_tf32x3", [])
+    ksel_bytes = KSEL_ROWS * KSEL_LEN * 4
+    ks_detail = {}
+    if k1_ms:
+        ks_detail["k1"] = ksel_bytes / (sum(k1_ms) / len(k1_ms) / 1e3) / 1e9
+    for i, k in enumerate(KSEL_K[1:]):
+        sel = ks_ms[i::len(KSEL_K) - 1]
+        if sel:
+            ks_detail["k%d" % k] = ksel_bytes / (sum(sel) / len(sel) / 1e3) / 1e9
+    gemm_avg = sum(gemm_ms) / len(gemm_ms) if gemm_ms else None
+    flops = 2.0 * NQ * NB * D
+    tf32_peak = bf16 / 2.0  # TF32 dense rate is half the BF16 rate (nominal ratio)
+    traffic = None
+    roof = {"bound": "tensor", "kernel": "dist_gemm_tf32x3 (3 TF32 passes per product)",
+            "achieved": flops / (gemm_avg / 1e3) / 1e12 if gemm_avg else None,
+            "peak": tf32_peak, "unit": "TFLOP/s",
+            "frac": (flops / (gemm_avg / 1e3) / 1e12) / tf32_peak if gemm_avg else None,
+            "traffic": traffic,
+            "peak_source": "%s bf16 %.0f TFLOP/s x 1/2 (TF32:BF16 nominal ratio)" % (src, bf16)}
+    kselect_obj = {"unit": "GB/s", "peak_hbm_gbs": hbm, "peak_source": src,
+                   "gbs": ks_detail, "frac": {k: v / hbm for k, v in ks_detail.items()}}
+
+    # end to end through the public API: host buffers in, host results out
+    e2e = None
+    if rank == 0:
+        xb_p = torch.from_numpy(xb_h).pin_memory()
+        xq_p = torch.from_numpy(xq_h).pin_memory()
+        Dh = torch.empty((NQ, 10)).pin_memory()
+        Ih = torch.empty((NQ, 10), dtype=torch.int64).pin_memory()
+        for it in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xbd = xb_p.cuda(non_blocking=True)
+            xqd = xq_p.cuda(non_blocking=True)
+            Dd, Id = g.knn_brute(xqd, xbd, 10)
+            Dh.copy_(Dd, non_blocking=True)
+            Ih.copy_(Id, non_blocking=True)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+        e2e = {"value": NQ / el, "unit": "queries/s", "what": "k=10 exact k-NN from pinned host inputs to host results",
+               "h2d_bytes_per_step": int(xb_h.nbytes + xq_h.nbytes),
+               "d2h_bytes_per_step": int(Dh.numel() * 4 + Ih.numel() * 8)}
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline else cpu_baseline_oracle()
+        launches = len(prof)
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded N(0,1) database/queries, U[0,1) k-select rows)",
+            "config": {"workload": "exact k-NN nb=1e6 nq=1e4 d=128 k in {10,100} (TF32x3, float32-accurate) + k-select 1e4 x 65536 k in {1,32,256,1024}",
+                       "l2_flush": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU",
+                       "knn_ms_per_step": knn_ms / args.steps, "kselect_ms_per_step": ksel_ms / args.steps},
+            "roofline": roof, "kselect": kselect_obj, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+            "kernel_ms": {k: sum(v) / len(v) for k, v in by.items()},
+        }), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -43,6 +43,11 @@ typedef int32_t gbk_status;
 #define GBK_METRIC_L2 0 /* squared Euclidean distance, ascending  */
 #define GBK_METRIC_IP 1 /* inner product, descending              */
 
+/* Arithmetic of the distance GEMM (the -2<x,y> term of Eq. (2)). */
+#define GBK_PREC_FP32 0 /* float32-accurate: TF32 hi/lo split, 3 tensor-core passes */
+#define GBK_PREC_BF16 1 /* one BF16 pass, float32 accumulation                      */
+#define GBK_PREC_FP8 2  /* one FP8 E4M3 pass with per-row scales, float32 accumulation */
+
 #define GBK_MAX_K 1024 /* largest k any selection accepts (the paper's WarpSelect bound, section 4.2) */
 
 /* Pluggable scratch allocator.  alloc returns a device pointer (or NULL on failure)
@@ -63,6 +68,18 @@ const char* gbk_last_error(void);
  * with respect to calls in flight on other threads. */
 gbk_status gbk_set_allocator(const gbk_allocator* allocator);
 
+/* Kernel timing for benchmarks and tracing.  While enabled, every library kernel launch
+ * is bracketed by a CUDA event pair on its stream.  gbk_profile_read waits for the
+ * recorded events, writes up to max_records (name: 32 bytes each, NUL-terminated; time in
+ * ms) in launch order, clears the record list and returns the count written. */
+void gbk_profile_enable(int32_t on);
+int32_t gbk_profile_read(char* names, float* ms, int32_t max_records);
+
+/* Synchronise `stream`, then report (and clear) the device status word that kernels set
+ * instead of trapping: GBK_ETIMEOUT when a bounded device-side wait gave up (the kernel
+ * skipped its remaining work; its outputs are undefined), GBK_EDEVICE for other flags. */
+gbk_status gbk_device_status(void* stream);
+
 /*
  * Row-wise k-selection (section 2, "k-selection"; batched over rows as in "Batching").
  *   vals    [rows][len] float32 input
@@ -76,11 +93,141 @@ gbk_status gbk_set_allocator(const gbk_allocator* allocator);
 gbk_status gbk_kselect(const float* vals, int64_t rows, int64_t len, int32_t k,
                        int32_t largest, float* D, int64_t* I, void* stream);
 
+/* Launch parameters of gbk_kselect_ex; 0 selects the library default. */
+typedef struct gbk_kselect_opts {
+  int32_t segments; /* thread blocks per row (>1: two-pass selection, section 5.3) */
+  int32_t unroll;   /* 16-byte loads in flight per thread per iteration: 4 or 8      */
+} gbk_kselect_opts;
+
+/* gbk_kselect with explicit launch parameters (opts may be NULL).  Results do not
+ * depend on the parameters.  Extra error: GBK_EINVAL for unroll other than 0, 4, 8. */
+gbk_status gbk_kselect_ex(const float* vals, int64_t rows, int64_t len, int32_t k,
+                          int32_t largest, float* D, int64_t* I, const gbk_kselect_opts* opts,
+                          void* stream);
+
 /*
  * Squared L2 norms of the rows of x (the precomputable terms of Eq. (2), section 2).
  *   x [n][d] float32 in, out [n] float32 out.  Errors: GBK_EINVAL, GBK_ECUDA.
  */
 gbk_status gbk_row_norms(const float* x, int64_t n, int32_t d, float* out, void* stream);
+
+/* Options of gbk_knn_brute (NULL = defaults). */
+typedef struct gbk_knn_opts {
+  int32_t precision; /* GBK_PREC_FP32 (default), GBK_PREC_BF16 or GBK_PREC_FP8          */
+  int32_t kprime;    /* BF16/FP8: candidates re-ranked in float32 (0 = 4k, >= k, <= 1024) */
+  int32_t chunks;    /* database chunks of the work decomposition (0 = planned)          */
+  int32_t* certified; /* BF16/FP8, optional device [nq]: 1 if the result provably equals
+                         the float32 top-k (see gbk_knn_brute), else 0                  */
+  float* error_bound; /* BF16/FP8, optional device [nq]: bound on |low-precision - float32|
+                         distance used by the certificate                              */
+} gbk_knn_opts;
+
+/*
+ * Exact k nearest neighbours of each query (Eq. (1), section 2; computed through the
+ * decomposition of Eq. (2) with the GEMM on the tensor cores and the k-selection fused
+ * into its epilogue, section 5.1).
+ *   xq [nq][d], xb [nb][d] float32;  1 <= k <= min(nb, GBK_MAX_K);  metric GBK_METRIC_*
+ *   D  [nq][k] float32 out: squared L2 distances ascending (clamped at 0), or inner
+ *      products descending;  I [nq][k] int64 out: database row numbers.
+ * GBK_PREC_FP32 keeps float32 accuracy (TF32 hi/lo split).  BF16/FP8 select kprime
+ * candidates in low precision, then recompute their distances directly in float32 and
+ * keep the best k.  A query is certified when the k'-th low-precision distance minus
+ * the error bound exceeds the k-th re-ranked distance (plus, for inner product), which
+ * proves no other database row belongs to the top k.
+ * Limits: nb, nq < 2^31; d <= 128 for k <= 256 (larger k tiles the distance matrix over
+ * queries and allows d <= 160).  Errors: GBK_EINVAL, GBK_EUNSUPPORTED (d too large),
+ * GBK_ENOMEM, GBK_ECUDA.  Inputs must be finite.
+ */
+gbk_status gbk_knn_brute(const float* xq, int64_t nq, const float* xb, int64_t nb, int32_t d,
+                         int32_t k, int32_t metric, float* D, int64_t* I,
+                         const gbk_knn_opts* opts, void* stream);
+
+/*
+ * All pairwise distances out[i*ldo + j] between xq[i] and xb[j] (section 2, "Exact
+ * search": the matrix D): max(0, ||x||^2 + ||y||^2 - 2<x,y>) for GBK_METRIC_L2, <x,y> for
+ * GBK_METRIC_IP, with the GEMM in the given precision.  ldo >= nb.  Same limits as
+ * gbk_knn_brute.
+ */
+gbk_status gbk_pairwise_distances(const float* xq, int64_t nq, const float* xb, int64_t nb,
+                                  int32_t d, int32_t metric, int32_t precision, float* out,
+                                  int64_t ldo, void* stream);
+
+/*
+ * Lloyd's k-means (section 2: the coarse quantizer is "trained via k-means"; section 6.2
+ * uses exact search with k = 1 for the assignment).
+ *   x [n][d] device float32; init_idx: HOST array of nc row numbers of x (the initial
+ *   centroids; e.g. a seeded random permutation's prefix); centroids [nc][d] device out;
+ *   objective: optional DEVICE [niter] doubles, the sum of squared distances of the
+ *   assignment of each iteration; n_split: optional DEVICE int64, empty clusters re-seeded.
+ * Assignment ties go to the lowest centroid; each update is the float64 mean of the
+ * members (summed in member order), rounded to float32; an empty cluster e (in increasing
+ * order) takes the most populated cluster s (lowest index on ties): c_e = c_s (1 + g/1024),
+ * c_s = c_s (1 - g/1024), g = +1 on even, -1 on odd dimensions; s's count is halved.
+ * direct_assign = 1 uses direct float32 distances (d <= 32, nc <= 256), else the tensor
+ * cores.  Errors: GBK_EINVAL, GBK_EUNSUPPORTED, GBK_ENOMEM, GBK_ECUDA.
+ */
+gbk_status gbk_kmeans(const float* x, int64_t n, int32_t d, int32_t nc, int32_t niter,
+                      const int64_t* init_idx, float* centroids, double* objective,
+                      int64_t* n_split, int32_t direct_assign, void* stream);
+
+/* ------------------------------------------------------------------ IVFADC index */
+
+/* An IVFADC index (section 2 "Compressed-domain search"): a coarse quantizer of nlist
+ * centroids, a product quantizer of M sub-quantizers with 256 centroids (8-bit codes),
+ * and inverted lists stored as two arrays, codes and 64-bit ids (section 5.3).  The index
+ * owns its device memory.  Not thread-safe: serialise calls on one index. */
+typedef struct gbk_index gbk_index;
+
+/* d % M == 0, M in {8, 16, 32}, d / M <= 32, nbits == 8, metric == GBK_METRIC_L2 (the
+ * paper's IVFADC is defined for L2, Eq. 6; others give GBK_EUNSUPPORTED). */
+gbk_status gbk_ivfpq_create(int32_t d, int32_t nlist, int32_t M, int32_t nbits, int32_t metric,
+                            gbk_index** out);
+void gbk_ivfpq_destroy(gbk_index* index);
+
+typedef struct gbk_train_opts {
+  int32_t niter;              /* coarse k-means iterations (0 = 20)                     */
+  int32_t pq_niter;           /* product-quantizer k-means iterations (0 = niter)       */
+  const int64_t* coarse_init; /* HOST [nlist] initial coarse centroid rows (NULL = 0..) */
+  const int64_t* pq_init;     /* HOST [256] initial sub-quantizer rows (NULL = 0..255)  */
+  int32_t use_precomputed;    /* 1: term-1 table of Eq. (11), nlist*M*256 floats; 0: per
+                                 (query, list) tables computed in the scan kernel       */
+} gbk_train_opts;
+
+/* Train q1 by k-means on x [n][d] (device), then the product quantizer on the residuals
+ * y - q1(y) (Eq. 3), each sub-quantizer by 256-centroid k-means.  Discards no data already
+ * added.  max(nlist, 256) <= n < 2^31. */
+gbk_status gbk_ivfpq_train(gbk_index* index, const float* x, int64_t n,
+                           const gbk_train_opts* opts, void* stream);
+
+/* Install externally trained quantizers: coarse [nlist][d], pq [M][256][d/M] (device or
+ * host float32). */
+gbk_status gbk_ivfpq_set_quantizers(gbk_index* index, const float* coarse, const float* pq,
+                                    int32_t use_precomputed, void* stream);
+
+/* Encode and append x [n][d] (device): list = nearest coarse centroid (ties lowest), code
+ * byte m = nearest centroid of sub-quantizer m to sub-vector m of the residual (ties
+ * lowest).  ids: device [n] int64, or NULL for running numbers 0, 1, ...  Lists keep
+ * insertion order.  At most 2^32 - 1 vectors in total. */
+gbk_status gbk_ivfpq_add(gbk_index* index, const float* x, int64_t n, const int64_t* ids,
+                         void* stream);
+
+/* IVFADC batch search (Algorithm 4): the nprobe nearest coarse centroids of each query
+ * (Eq. 5), ADC distances of every vector of those lists (Eq. 6, 10-11), k smallest.
+ *   D [nq][k] squared distances ascending, I [nq][k] ids; when the probed lists hold
+ *   fewer than k vectors the tail is (+inf, -1).  Equal distances: lower list position
+ *   first (= lower id when ids are running numbers).  1 <= k, nprobe <= GBK_MAX_K,
+ *   nprobe <= nlist. */
+gbk_status gbk_ivfpq_search(gbk_index* index, const float* xq, int64_t nq, int32_t k,
+                            int32_t nprobe, float* D, int64_t* I, void* stream);
+
+/* Sizes of the index (synchronises `stream` when lists must be rebuilt). */
+gbk_status gbk_ivfpq_info(gbk_index* index, int64_t* ntotal, int32_t* nlist, int32_t* d,
+                          int32_t* M, void* stream);
+
+/* Copy out (any pointer may be NULL; host or device): coarse [nlist][d], pq [M][256][d/M],
+ * list_off [nlist+1], codes [ntotal][M] and ids [ntotal] in list order. */
+gbk_status gbk_ivfpq_export(gbk_index* index, float* coarse, float* pq, int64_t* list_off,
+                            uint8_t* codes, int64_t* ids, void* stream);
 
 #ifdef __cplusplus
 }

@@ -39,7 +39,11 @@ class GbkError(RuntimeError):
 # (name, argtypes); every entry point returns gbk_status (int32)
 _SIGNATURES = {
     "gbk_kselect": [_vp, _i64, _i64, _i32, _i32, _vp, _vp, _vp],
+    "gbk_kselect_ex": [_vp, _i64, _i64, _i32, _i32, _vp, _vp, _vp, _vp],
     "gbk_row_norms": [_vp, _i64, _i32, _vp, _vp],
+    "gbk_device_status": [_vp],
+    "gbk_knn_brute": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
+    "gbk_pairwise_distances": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _vp, _i64, _vp],
 }
 
 
@@ -63,7 +67,13 @@ def load(path: str | None = None):
                 fn.argtypes = args
                 fn.restype = ctypes.c_int32
             lib.gbk_last_error.restype = ctypes.c_char_p
+            lib.gbk_profile_enable.argtypes = [ctypes.c_int32]
+            lib.gbk_profile_enable.restype = None
+            lib.gbk_profile_read.argtypes = [ctypes.c_char_p, ctypes.c_void_p, ctypes.c_int32]
+            lib.gbk_profile_read.restype = ctypes.c_int32
             lib.gbk_version.restype = ctypes.c_int32
+            lib.gbk_ivfpq_destroy.argtypes = [ctypes.c_void_p]
+            lib.gbk_ivfpq_destroy.restype = None
             _lib = lib
     return _lib
 
@@ -93,8 +103,21 @@ def _dev(t, dtype, name):
     return t
 
 
-def kselect(vals: torch.Tensor, k: int, largest: bool = False, out=None):
-    """Row-wise k smallest (largest) values and their int64 indices, sorted best first."""
+class KselectOpts(ctypes.Structure):
+    _fields_ = [("segments", ctypes.c_int32), ("unroll", ctypes.c_int32)]
+
+
+def device_status():
+    """Synchronise the current stream and raise if a kernel flagged an error."""
+    _call("gbk_device_status", _stream())
+
+
+def kselect(vals: torch.Tensor, k: int, largest: bool = False, out=None, segments: int = 0,
+            unroll: int = 0):
+    """Row-wise k smallest (largest) values and their int64 indices, sorted best first.
+
+    segments / unroll are launch parameters (0 = library default); results never depend
+    on them."""
     _dev(vals, torch.float32, "vals")
     if vals.dim() != 2:
         raise ValueError("vals must be 2-D")
@@ -104,8 +127,13 @@ def kselect(vals: torch.Tensor, k: int, largest: bool = False, out=None):
         I = torch.empty((rows, k), dtype=torch.int64, device=vals.device)
     else:
         D, I = out
-    _call("gbk_kselect", _ptr(vals), rows, length, int(k), int(bool(largest)), _ptr(D), _ptr(I),
-          _stream())
+    if segments or unroll:
+        opts = KselectOpts(int(segments), int(unroll))
+        _call("gbk_kselect_ex", _ptr(vals), rows, length, int(k), int(bool(largest)), _ptr(D),
+              _ptr(I), ctypes.byref(opts), _stream())
+    else:
+        _call("gbk_kselect", _ptr(vals), rows, length, int(k), int(bool(largest)), _ptr(D),
+              _ptr(I), _stream())
     return D, I
 
 
@@ -116,3 +144,191 @@ def row_norms(x: torch.Tensor, out=None):
     o = torch.empty(n, dtype=torch.float32, device=x.device) if out is None else out
     _call("gbk_row_norms", _ptr(x), n, int(d), _ptr(o), _stream())
     return o
+
+
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+
+
+class KnnOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("kprime", ctypes.c_int32),
+                ("chunks", ctypes.c_int32), ("certified", ctypes.c_void_p),
+                ("error_bound", ctypes.c_void_p)]
+
+
+def _metric(m):
+    return {"l2": METRIC_L2, "ip": METRIC_IP}[m] if isinstance(m, str) else int(m)
+
+
+def knn_brute(xq: torch.Tensor, xb: torch.Tensor, k: int, metric="l2", precision="fp32",
+              kprime: int = 0, chunks: int = 0, out=None, certify: bool = False):
+    """Exact k-NN (squared L2 ascending, or inner product descending) with int64 ids.
+
+    precision "bf16"/"fp8": over-fetch kprime candidates, exact float32 re-rank; with
+    certify=True also returns (certified [nq] int32, error_bound [nq] float32)."""
+    _dev(xq, torch.float32, "xq")
+    _dev(xb, torch.float32, "xb")
+    nq, d = xq.shape
+    nb = xb.shape[0]
+    if xb.shape[1] != d:
+        raise ValueError("dimension mismatch")
+    if out is None:
+        D = torch.empty((nq, k), dtype=torch.float32, device=xq.device)
+        I = torch.empty((nq, k), dtype=torch.int64, device=xq.device)
+    else:
+        D, I = out
+    cert = eb = None
+    if certify:
+        cert = torch.empty(nq, dtype=torch.int32, device=xq.device)
+        eb = torch.empty(nq, dtype=torch.float32, device=xq.device)
+    opts = KnnOpts(PRECISIONS[precision], int(kprime), int(chunks),
+                   cert.data_ptr() if cert is not None else None,
+                   eb.data_ptr() if eb is not None else None)
+    _call("gbk_knn_brute", _ptr(xq), nq, _ptr(xb), nb, int(d), int(k), _metric(metric), _ptr(D),
+          _ptr(I), ctypes.byref(opts), _stream())
+    return (D, I, cert, eb) if certify else (D, I)
+
+
+def pairwise_distances(xq: torch.Tensor, xb: torch.Tensor, metric="l2", precision="fp32"):
+    """Full [nq][nb] squared L2 distance (or inner product) matrix on the tensor cores."""
+    _dev(xq, torch.float32, "xq")
+    _dev(xb, torch.float32, "xb")
+    nq, d = xq.shape
+    nb = xb.shape[0]
+    out = torch.empty((nq, nb), dtype=torch.float32, device=xq.device)
+    _call("gbk_pairwise_distances", _ptr(xq), nq, _ptr(xb), nb, int(d), _metric(metric),
+          PRECISIONS[precision], _ptr(out), nb, _stream())
+    return out
+
+
+def profile_enable(on: bool = True):
+    """Record a CUDA event pair around every library kernel launch (see profile_read)."""
+    load().gbk_profile_enable(int(bool(on)))
+
+
+def profile_read(max_records: int = 4096):
+    """[(kernel name, ms)] recorded since the last read, in launch order."""
+    names = ctypes.create_string_buffer(32 * max_records)
+    ms = (ctypes.c_float * max_records)()
+    n = load().gbk_profile_read(names, ctypes.cast(ms, ctypes.c_void_p), max_records)
+    raw = names.raw
+    return [(raw[32 * i:32 * i + 32].split(b"\0", 1)[0].decode(), float(ms[i])) for i in range(n)]
+
+
+# ---------------------------------------------------------------------------- k-means / IVFPQ
+
+_SIGNATURES.update({
+    "gbk_kmeans": [_vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _i32, _vp],
+    "gbk_ivfpq_create": [_i32, _i32, _i32, _i32, _i32, _vp],
+    "gbk_ivfpq_train": [_vp, _vp, _i64, _vp, _vp],
+    "gbk_ivfpq_set_quantizers": [_vp, _vp, _vp, _i32, _vp],
+    "gbk_ivfpq_add": [_vp, _vp, _i64, _vp, _vp],
+    "gbk_ivfpq_search": [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp],
+    "gbk_ivfpq_info": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "gbk_ivfpq_export": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
+})
+
+
+def _host_i64(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def kmeans(x: torch.Tensor, init_idx, niter: int, direct: bool = False):
+    """Lloyd's k-means on the GPU.  init_idx: row numbers of x used as initial centroids.
+    Returns (centroids [nc][d] CUDA tensor, objective per iteration (host float64 array),
+    number of empty-cluster re-seeds)."""
+    import numpy as np
+    _dev(x, torch.float32, "x")
+    n, d = x.shape
+    ii, iip = _host_i64(init_idx)
+    nc = ii.size
+    cent = torch.empty((nc, d), dtype=torch.float32, device=x.device)
+    obj = torch.zeros(max(niter, 1), dtype=torch.float64, device=x.device)
+    ns = torch.zeros(1, dtype=torch.int64, device=x.device)
+    _call("gbk_kmeans", _ptr(x), n, int(d), int(nc), int(niter), iip, _ptr(cent), _ptr(obj),
+          _ptr(ns), int(bool(direct)), _stream())
+    return cent, obj[:niter].cpu().numpy(), int(ns.item())
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("niter", ctypes.c_int32), ("pq_niter", ctypes.c_int32),
+                ("coarse_init", ctypes.c_void_p), ("pq_init", ctypes.c_void_p),
+                ("use_precomputed", ctypes.c_int32)]
+
+
+class IVFPQIndex:
+    """IVFADC index on the GPU (coarse quantizer + 8-bit product quantizer, inverted lists)."""
+
+    def __init__(self, d: int, nlist: int, M: int, nbits: int = 8, metric="l2"):
+        self.d, self.nlist, self.M = int(d), int(nlist), int(M)
+        h = ctypes.c_void_p()
+        _call("gbk_ivfpq_create", self.d, self.nlist, self.M, int(nbits), _metric(metric),
+              ctypes.byref(h))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.gbk_ivfpq_destroy(self._h)
+            self._h = None
+
+    def train(self, x: torch.Tensor, niter: int = 20, pq_niter: int = 0, coarse_init=None,
+              pq_init=None, use_precomputed: bool = True):
+        _dev(x, torch.float32, "x")
+        ci = pi = None
+        cip = pip = None
+        if coarse_init is not None:
+            ci, cip = _host_i64(coarse_init)
+        if pq_init is not None:
+            pi, pip = _host_i64(pq_init)
+        o = TrainOpts(int(niter), int(pq_niter), cip, pip, int(bool(use_precomputed)))
+        _call("gbk_ivfpq_train", self._h, _ptr(x), x.shape[0], ctypes.byref(o), _stream())
+        torch.cuda.current_stream().synchronize()
+        return self
+
+    def set_quantizers(self, coarse: torch.Tensor, pq: torch.Tensor, use_precomputed=True):
+        _dev(coarse, torch.float32, "coarse")
+        _dev(pq, torch.float32, "pq")
+        _call("gbk_ivfpq_set_quantizers", self._h, _ptr(coarse), _ptr(pq),
+              int(bool(use_precomputed)), _stream())
+        return self
+
+    def add(self, x: torch.Tensor, ids: torch.Tensor = None):
+        _dev(x, torch.float32, "x")
+        if ids is not None:
+            _dev(ids, torch.int64, "ids")
+        _call("gbk_ivfpq_add", self._h, _ptr(x), x.shape[0], _ptr(ids), _stream())
+        return self
+
+    def search(self, xq: torch.Tensor, k: int, nprobe: int, out=None):
+        _dev(xq, torch.float32, "xq")
+        nq = xq.shape[0]
+        if out is None:
+            D = torch.empty((nq, k), dtype=torch.float32, device=xq.device)
+            I = torch.empty((nq, k), dtype=torch.int64, device=xq.device)
+        else:
+            D, I = out
+        _call("gbk_ivfpq_search", self._h, _ptr(xq), nq, int(k), int(nprobe), _ptr(D), _ptr(I),
+              _stream())
+        return D, I
+
+    @property
+    def ntotal(self):
+        n = ctypes.c_int64()
+        _call("gbk_ivfpq_info", self._h, ctypes.byref(n), None, None, None, _stream())
+        return n.value
+
+    def export(self):
+        """Host copies: coarse [nlist][d], pq [M][256][d/M], list_off, codes, ids."""
+        import numpy as np
+        n = self.ntotal
+        coarse = np.empty((self.nlist, self.d), np.float32)
+        pq = np.empty((self.M, 256, self.d // self.M), np.float32)
+        off = np.empty(self.nlist + 1, np.int64)
+        codes = np.empty((max(n, 1), self.M), np.uint8)
+        ids = np.empty(max(n, 1), np.int64)
+        _call("gbk_ivfpq_export", self._h, coarse.ctypes.data_as(_vp), pq.ctypes.data_as(_vp),
+              off.ctypes.data_as(_vp), codes.ctypes.data_as(_vp), ids.ctypes.data_as(_vp),
+              _stream())
+        torch.cuda.current_stream().synchronize()
+        return {"coarse": coarse, "pq": pq, "list_off": off, "codes": codes[:n], "ids": ids[:n]}

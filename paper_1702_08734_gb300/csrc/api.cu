@@ -4,9 +4,12 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "kselect.cuh"
+#include "knn.cuh"
+#include "ivf.cuh"
 
 namespace gbk {
 
@@ -77,6 +80,49 @@ const DeviceInfo& device_info() {
   return cache;
 }
 
+namespace {
+struct ProfRec {
+  char name[32];
+  cudaEvent_t e0, e1;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+}  // namespace
+
+ProfScope::ProfScope(const char* name, cudaStream_t st) : stream(st) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on || g_prof.size() >= 4096) return;
+  ProfRec r;
+  snprintf(r.name, sizeof(r.name), "%s", name);
+  if (cudaEventCreate(&r.e0) != cudaSuccess) return;
+  if (cudaEventCreate(&r.e1) != cudaSuccess) return;
+  cudaEventRecord(r.e0, st);
+  g_prof.push_back(r);
+  slot = (int)g_prof.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (slot < (int)g_prof.size()) cudaEventRecord(g_prof[slot].e1, stream);
+}
+
+uint32_t* device_status() {
+  static std::mutex mu;
+  static uint32_t* words[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!words[dev]) {
+    uint32_t* p = nullptr;
+    if (cudaMalloc(&p, sizeof(uint32_t)) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, sizeof(uint32_t)) != cudaSuccess) return nullptr;
+    words[dev] = p;
+  }
+  return words[dev];
+}
+
 }  // namespace gbk
 
 using namespace gbk;
@@ -101,6 +147,12 @@ gbk_status gbk_set_allocator(const gbk_allocator* allocator) {
 
 gbk_status gbk_kselect(const float* vals, int64_t rows, int64_t len, int32_t k, int32_t largest,
                        float* D, int64_t* I, void* stream) {
+  return gbk_kselect_ex(vals, rows, len, k, largest, D, I, nullptr, stream);
+}
+
+gbk_status gbk_kselect_ex(const float* vals, int64_t rows, int64_t len, int32_t k,
+                          int32_t largest, float* D, int64_t* I, const gbk_kselect_opts* opts,
+                          void* stream) {
   clear_error();
   GBK_REQUIRE(rows >= 0, "gbk_kselect: rows < 0");
   if (rows == 0) return GBK_OK;
@@ -111,7 +163,123 @@ gbk_status gbk_kselect(const float* vals, int64_t rows, int64_t len, int32_t k, 
   GBK_REQUIRE(vals && D && I, "gbk_kselect: NULL pointer");
   GBK_REQUIRE(largest == 0 || largest == 1, "gbk_kselect: largest must be 0 or 1");
   GBK_REQUIRE(rows * (int64_t)k < (int64_t(1) << 40), "gbk_kselect: output too large");
-  return kselect_run(vals, rows, len, k, largest != 0, D, I, as_stream(stream), nullptr);
+  KselectTuning tu = kselect_default_tuning(rows, len, k);
+  if (opts) {
+    GBK_REQUIRE(opts->unroll == 0 || opts->unroll == 4 || opts->unroll == 8,
+                "gbk_kselect_ex: unroll must be 0, 4 or 8");
+    GBK_REQUIRE(opts->segments >= 0, "gbk_kselect_ex: segments < 0");
+    if (opts->unroll) tu.unroll = opts->unroll;
+    if (opts->segments) tu.segs = opts->segments;
+  }
+  return kselect_run(vals, rows, len, k, largest != 0, D, I, as_stream(stream), &tu);
+}
+
+void gbk_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+}
+
+int32_t gbk_profile_read(char* names, float* ms, int32_t max_records) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  int32_t n = 0;
+  for (auto& r : g_prof) {
+    cudaEventSynchronize(r.e1);
+    if (n < max_records) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, r.e0, r.e1);
+      if (ms) ms[n] = t;
+      if (names) snprintf(names + 32 * n, 32, "%s", r.name);
+    }
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+    n++;
+  }
+  g_prof.clear();
+  return n < max_records ? n : max_records;
+}
+
+gbk_status gbk_device_status(void* stream) {
+  clear_error();
+  uint32_t* w = device_status();
+  if (!w) return set_error(GBK_ECUDA, "device status word unavailable");
+  GBK_CUDA_CHECK(cudaStreamSynchronize(as_stream(stream)));
+  uint32_t v = 0;
+  GBK_CUDA_CHECK(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost));
+  if (v == 0) return GBK_OK;
+  GBK_CUDA_CHECK(cudaMemset(w, 0, sizeof(uint32_t)));
+  if (v & 1u) return set_error(GBK_ETIMEOUT, "a device-side wait gave up (status 0x%x)", v);
+  return set_error(GBK_EDEVICE, "kernel status word 0x%x", v);
+}
+
+gbk_status gbk_knn_brute(const float* xq, int64_t nq, const float* xb, int64_t nb, int32_t d,
+                         int32_t k, int32_t metric, float* D, int64_t* I,
+                         const gbk_knn_opts* opts, void* stream) {
+  clear_error();
+  GBK_REQUIRE(nq >= 0 && nq < (int64_t(1) << 31), "gbk_knn_brute: nq out of range");
+  GBK_REQUIRE(nb >= 1 && nb < (int64_t(1) << 31), "gbk_knn_brute: nb out of range");
+  GBK_REQUIRE(d >= 1, "gbk_knn_brute: d < 1");
+  GBK_REQUIRE(k >= 1 && k <= GBK_MAX_K && k <= nb, "gbk_knn_brute: k=%d out of [1, min(nb, %d)]",
+              k, GBK_MAX_K);
+  GBK_REQUIRE(metric == GBK_METRIC_L2 || metric == GBK_METRIC_IP, "gbk_knn_brute: bad metric");
+  if (nq == 0) return GBK_OK;
+  GBK_REQUIRE(xq && xb && D && I, "gbk_knn_brute: NULL pointer");
+  KnnPlan plan;
+  if (opts) {
+    GBK_REQUIRE(opts->precision >= GBK_PREC_FP32 && opts->precision <= GBK_PREC_FP8,
+                "gbk_knn_brute: bad precision");
+    GBK_REQUIRE(opts->chunks >= 0, "gbk_knn_brute: chunks < 0");
+    GBK_REQUIRE(opts->kprime == 0 || (opts->kprime >= k && opts->kprime <= GBK_MAX_K),
+                "gbk_knn_brute: kprime must be 0 or in [k, %d]", GBK_MAX_K);
+    plan.prec = opts->precision;
+    plan.chunks = opts->chunks;
+    plan.kprime = opts->kprime;
+    plan.certified = opts->certified;
+    plan.error_bound = opts->error_bound;
+  }
+  return knn_run(xq, nq, xb, nb, d, k, metric, D, I, plan, as_stream(stream));
+}
+
+gbk_status gbk_pairwise_distances(const float* xq, int64_t nq, const float* xb, int64_t nb,
+                                  int32_t d, int32_t metric, int32_t precision, float* out,
+                                  int64_t ldo, void* stream) {
+  clear_error();
+  GBK_REQUIRE(nq >= 0 && nq < (int64_t(1) << 31), "gbk_pairwise_distances: nq out of range");
+  GBK_REQUIRE(nb >= 1 && nb < (int64_t(1) << 31), "gbk_pairwise_distances: nb out of range");
+  GBK_REQUIRE(d >= 1 && ldo >= nb, "gbk_pairwise_distances: bad d or ldo");
+  GBK_REQUIRE(metric == GBK_METRIC_L2 || metric == GBK_METRIC_IP,
+              "gbk_pairwise_distances: bad metric");
+  GBK_REQUIRE(precision >= GBK_PREC_FP32 && precision <= GBK_PREC_FP8,
+              "gbk_pairwise_distances: bad precision");
+  if (nq == 0) return GBK_OK;
+  GBK_REQUIRE(xq && xb && out, "gbk_pairwise_distances: NULL pointer");
+  cudaStream_t st = as_stream(stream);
+  PreparedOperand Q, B;
+  gbk_status r;
+  const int64_t ntiles = (nb + 127) / 128;
+  if ((r = prepare_operand(xq, nq, d, precision, nq, 0.f, &Q, st)) != GBK_OK) return r;
+  if ((r = prepare_operand(xb, nb, d, precision, ntiles * 128, 0.f, &B, st)) != GBK_OK) return r;
+  return pairwise_run(Q, B, metric == GBK_METRIC_IP, out, ldo, st);
+}
+
+gbk_status gbk_kmeans(const float* x, int64_t n, int32_t d, int32_t nc, int32_t niter,
+                      const int64_t* init_idx, float* centroids, double* objective,
+                      int64_t* n_split, int32_t direct_assign, void* stream) {
+  clear_error();
+  GBK_REQUIRE(x && init_idx && centroids, "gbk_kmeans: NULL argument");
+  GBK_REQUIRE(n >= 1 && n < (int64_t(1) << 31) && d >= 1 && nc >= 1 && nc <= n && niter >= 0,
+              "gbk_kmeans: bad sizes");
+  for (int i = 0; i < nc; i++)
+    GBK_REQUIRE(init_idx[i] >= 0 && init_idx[i] < n, "gbk_kmeans: init_idx out of range");
+  cudaStream_t st = as_stream(stream);
+  Scratch ii;
+  gbk_status r;
+  if ((r = ii.alloc(sizeof(int64_t) * (size_t)nc, st)) != GBK_OK) return r;
+  GBK_CUDA_CHECK(cudaMemcpyAsync(ii.p, init_idx, sizeof(int64_t) * (size_t)nc,
+                                 cudaMemcpyHostToDevice, st));
+  r = kmeans_run(x, n, d, d, nc, niter, ii.as<int64_t>(), centroids, objective,
+                 reinterpret_cast<long long*>(n_split), direct_assign != 0, st);
+  if (r == GBK_OK) GBK_CUDA_CHECK(cudaStreamSynchronize(st));  // host init array reused
+  return r;
 }
 
 gbk_status gbk_row_norms(const float* x, int64_t n, int32_t d, float* out, void* stream) {

@@ -25,7 +25,20 @@ struct DeviceInfo {
 };
 const DeviceInfo& device_info();
 
+// Per-device error word that kernels set instead of trapping (bit 0: a bounded wait
+// gave up).  Allocated and zeroed on first use for the current device.
+uint32_t* device_status();
+
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Optional per-kernel timing (gbk_profile_*): when enabled, a scope records a CUDA event
+// pair on the launch stream around the kernel(s) it covers.
+struct ProfScope {
+  int slot = -1;
+  cudaStream_t stream = nullptr;
+  ProfScope(const char* name, cudaStream_t st);
+  ~ProfScope();
+};
 
 // RAII scratch buffer (freed stream-ordered at scope exit).
 struct Scratch {

@@ -1,0 +1,429 @@
+// Host driver of the fused distance GEMM: operand preparation, work planning, TMA
+// descriptors, the cross-chunk merge (the paper's two-pass k-selection, section 5.3)
+// and the large-k path that tiles the distance matrix over queries (section 5.1).
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "dist_gemm.cuh"
+#include "dist_gemm_launch.cuh"
+#include "dist_gemm_kernel.cuh"
+#include "kselect.cuh"
+#include "knn.cuh"
+
+namespace gbk {
+
+// ------------------------------------------------------------------ prep kernels
+
+__global__ void prep_tf32x3_kernel(const float* __restrict__ x, int64_t n, int d, int dpad,
+                                   float* __restrict__ hi, float* __restrict__ lo,
+                                   float* __restrict__ norms, int64_t nrows_pad,
+                                   float pad_norm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (row >= nrows_pad) return;
+  if (row >= n) {
+    if (lane == 0) norms[row] = pad_norm;
+    return;
+  }
+  float s = 0.f;
+  for (int t = lane; t < dpad; t += 32) {
+    const float v = t < d ? x[row * d + t] : 0.f;
+    const float h = tf32_rna(v);
+    const float l = tf32_rna(v - h);
+    hi[row * dpad + t] = h;
+    lo[row * dpad + t] = l;
+    s = fmaf(v, v, s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
+  if (lane == 0) norms[row] = s;
+}
+
+__global__ void prep_bf16_kernel(const float* __restrict__ x, int64_t n, int d, int dpad,
+                                 __nv_bfloat16* __restrict__ out, float* __restrict__ norms,
+                                 int64_t nrows_pad, float pad_norm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (row >= nrows_pad) return;
+  if (row >= n) {
+    if (lane == 0) norms[row] = pad_norm;
+    return;
+  }
+  float s = 0.f;
+  for (int t = lane; t < dpad; t += 32) {
+    const float v = t < d ? x[row * d + t] : 0.f;
+    out[row * dpad + t] = __float2bfloat16_rn(v);
+    s = fmaf(v, v, s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
+  if (lane == 0) norms[row] = s;
+}
+
+__global__ void prep_fp8_kernel(const float* __restrict__ x, int64_t n, int d, int dpad,
+                                __nv_fp8_e4m3* __restrict__ out, float* __restrict__ scale,
+                                float* __restrict__ norms, int64_t nrows_pad, float pad_norm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (row >= nrows_pad) return;
+  if (row >= n) {
+    if (lane == 0) {
+      norms[row] = pad_norm;
+      scale[row] = 0.f;
+    }
+    return;
+  }
+  float s = 0.f, amax = 0.f;
+  for (int t = lane; t < d; t += 32) {
+    const float v = x[row * d + t];
+    s = fmaf(v, v, s);
+    amax = fmaxf(amax, fabsf(v));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(FULL_MASK, s, o);
+    amax = fmaxf(amax, __shfl_xor_sync(FULL_MASK, amax, o));
+  }
+  const float sc = amax > 0.f ? amax / 448.f : 1.f;
+  const float inv = 1.f / sc;
+  for (int t = lane; t < dpad; t += 32) {
+    const float v = t < d ? x[row * d + t] * inv : 0.f;
+    out[row * dpad + t] = __nv_fp8_e4m3(v);
+  }
+  if (lane == 0) {
+    norms[row] = s;
+    scale[row] = sc;
+  }
+}
+
+namespace {
+
+// ------------------------------------------------------------------ cross-chunk merge
+
+template <int KP>
+__global__ void __launch_bounds__(256)
+    knn_merge_kernel(const uint64_t* __restrict__ part, int chunks, int kp, int k,
+                     const float* __restrict__ xnorm, int largest, float* __restrict__ D,
+                     int64_t* __restrict__ I) {
+  constexpr int THREADS = 256, CAP = 4096;
+  using Sel = BlockSelect<THREADS, KP, CAP>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(smem_raw);
+  const int64_t q = blockIdx.x;
+  const uint64_t* src = part + q * (int64_t)chunks * kp;
+  const int64_t nper = (int64_t)chunks * k;
+  Sel::init(s);
+  __syncthreads();
+  uint64_t thr = ~0ull;
+  for (int64_t base = 0; base < nper; base += THREADS) {
+    const int64_t i = base + threadIdx.x;
+    uint64_t c[1];
+    uint32_t mask = 0;
+    if (i < nper) {
+      const int64_t ch = i / k, j = i % k;
+      c[0] = src[ch * kp + j];
+      mask = (c[0] != ~0ull && c[0] <= thr) ? 1u : 0u;
+    }
+    Sel::template push<1>(s, mask, c);
+    __syncthreads();
+    if (s.n_buf > CAP - THREADS) {
+      Sel::compact(s, k);
+      thr = s.thr;
+    }
+  }
+  Sel::finish(s, k);
+  const float xn = xnorm ? xnorm[q] : 0.f;
+  for (int j = threadIdx.x; j < k; j += THREADS) {
+    const uint64_t e = s.top[j];
+    float dv;
+    int64_t id;
+    if (e == ~0ull) {
+      dv = largest ? -INFINITY : INFINITY;
+      id = -1;
+    } else {
+      dv = key_value((uint32_t)(e >> 32), largest != 0);
+      if (!largest) dv = fmaxf(dv + xn, 0.f);
+      id = (int64_t)(uint32_t)e;
+    }
+    D[q * k + j] = dv;
+    I[q * k + j] = id;
+  }
+}
+
+template <int KP>
+gbk_status launch_knn_merge(const uint64_t* part, int64_t nq, int chunks, int kp, int k,
+                            const float* xnorm, int largest, float* D, int64_t* I,
+                            cudaStream_t st) {
+  using Sel = BlockSelect<256, KP, 4096>;
+  auto kern = knn_merge_kernel<KP>;
+  static bool attr = false;
+  if (!attr) {
+    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sizeof(typename Sel::Smem)));
+    attr = true;
+  }
+  kern<<<(unsigned)nq, 256, sizeof(typename Sel::Smem), st>>>(part, chunks, kp, k, xnorm,
+                                                              largest, D, I);
+  GBK_LAUNCH_CHECK();
+  return GBK_OK;
+}
+
+gbk_status knn_merge(const uint64_t* part, int64_t nq, int chunks, int kp, int k,
+                     const float* xnorm, int largest, float* D, int64_t* I, cudaStream_t st) {
+  ProfScope prof("knn_merge", st);
+  if (k <= 32) return launch_knn_merge<32>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);
+  if (k <= 64) return launch_knn_merge<64>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);
+  if (k <= 128) return launch_knn_merge<128>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);
+  return launch_knn_merge<256>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);
+}
+
+// ------------------------------------------------------------------ TMA descriptors
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn(gbk_status* st) {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  if (!fn) *st = set_error(GBK_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  return fn;
+}
+
+// Row-major [rows][cols] operand (cols already padded to a 128-byte multiple), boxes of
+// 128 rows x 128 bytes with 128-byte swizzle; rows beyond `rows` read as zero.
+gbk_status make_operand_map(CUtensorMap* m, const void* base, int64_t rows, int cols,
+                            int elem_bytes) {
+  gbk_status st = GBK_OK;
+  EncodeTiledFn enc = encode_fn(&st);
+  if (!enc) return st;
+  const CUtensorMapDataType dt = elem_bytes == 4   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * elem_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), 128u};
+  cuuint32_t es[2] = {1u, 1u};
+  CUresult r = enc(m, dt, 2, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(GBK_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return GBK_OK;
+}
+
+int elem_bytes_of(int prec) { return prec == GBK_PREC_BF16 ? 2 : prec == GBK_PREC_FP8 ? 1 : 4; }
+int pieces_of(int prec) { return prec == GBK_PREC_FP32 ? 2 : 1; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ operand sets
+
+gbk_status prepare_operand(const float* x, int64_t n, int d, int prec, int64_t nrows_pad,
+                           float pad_norm, PreparedOperand* out, cudaStream_t st) {
+  const int eb = elem_bytes_of(prec);
+  const int dpad = (int)(((int64_t)d * eb + 127) / 128 * 128 / eb);
+  out->prec = prec;
+  out->n = n;
+  out->d = d;
+  out->dpad = dpad;
+  out->nkb = dpad * eb / 128;
+  const size_t piece = (size_t)std::max<int64_t>(n, 1) * dpad * eb;
+  gbk_status r = out->data.alloc(piece * pieces_of(prec), st);
+  if (r != GBK_OK) return r;
+  r = out->norms.alloc(sizeof(float) * (size_t)nrows_pad, st);
+  if (r != GBK_OK) return r;
+  if (prec == GBK_PREC_FP8) {
+    r = out->scale.alloc(sizeof(float) * (size_t)nrows_pad, st);
+    if (r != GBK_OK) return r;
+  }
+  unsigned char* base = out->data.as<unsigned char>();
+  out->piece[0] = base;
+  out->piece[1] = prec == GBK_PREC_FP32 ? base + piece : nullptr;
+  const int warps = 8;
+  const unsigned blocks = (unsigned)((nrows_pad + warps - 1) / warps);
+  if (nrows_pad == 0) return GBK_OK;
+  ProfScope prof("prep_operand", st);
+  if (prec == GBK_PREC_FP32)
+    prep_tf32x3_kernel<<<blocks, warps * 32, 0, st>>>(
+        x, n, d, dpad, (float*)out->piece[0], (float*)out->piece[1], out->norms.as<float>(),
+        nrows_pad, pad_norm);
+  else if (prec == GBK_PREC_BF16)
+    prep_bf16_kernel<<<blocks, warps * 32, 0, st>>>(x, n, d, dpad, (__nv_bfloat16*)out->piece[0],
+                                                   out->norms.as<float>(), nrows_pad, pad_norm);
+  else
+    prep_fp8_kernel<<<blocks, warps * 32, 0, st>>>(x, n, d, dpad, (__nv_fp8_e4m3*)out->piece[0],
+                                                  out->scale.as<float>(), out->norms.as<float>(),
+                                                  nrows_pad, pad_norm);
+  GBK_LAUNCH_CHECK();
+  return GBK_OK;
+}
+
+// Chunks S minimising (waves x tiles per chunk); ties to fewer chunks.
+int plan_chunks(int nqt, int ntiles, int grid_cap) {
+  int best = 1;
+  int64_t best_cost = INT64_MAX;
+  for (int S = 1; S <= std::min(ntiles, 512); S++) {
+    const int64_t waves = ((int64_t)nqt * S + grid_cap - 1) / grid_cap;
+    const int64_t tpc = (ntiles + S - 1) / S;
+    const int64_t cost = waves * tpc * 64 + S;  // small penalty per chunk (merge work)
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = S;
+    }
+  }
+  return best;
+}
+
+gbk_status gemm_launch(int mode, int kpr, bool largest, const PreparedOperand& Q,
+                       const PreparedOperand& B, GemmArgs a, cudaStream_t st) {
+  const int prec = Q.prec;
+  const int pieces = pieces_of(prec);
+  const int eb = elem_bytes_of(prec);
+  CUtensorMap maps[4];
+  gbk_status r;
+  if ((r = make_operand_map(&maps[0], Q.piece[0], Q.n, Q.dpad, eb)) != GBK_OK) return r;
+  if ((r = make_operand_map(&maps[2], B.piece[0], B.n, B.dpad, eb)) != GBK_OK) return r;
+  if (pieces > 1) {
+    if ((r = make_operand_map(&maps[1], Q.piece[1], Q.n, Q.dpad, eb)) != GBK_OK) return r;
+    if ((r = make_operand_map(&maps[3], B.piece[1], B.n, B.dpad, eb)) != GBK_OK) return r;
+  } else {
+    maps[1] = maps[0];
+    maps[3] = maps[2];
+  }
+  const DeviceInfo& di = device_info();
+  const bool queues = mode == MODE_SELECT && kpr > 0;
+  const GemmSmemLayout l0 = gemm_smem_layout(pieces, Q.nkb, 0, queues);
+  const int64_t avail = (int64_t)di.smem_optin - 1024 - l0.total;
+  const int64_t stage_bytes = (int64_t)pieces * GEMM_TILE_BYTES + 16;
+  int stages = (int)std::min<int64_t>(8, avail / stage_bytes);
+  if (stages < 2)
+    return set_error(GBK_EUNSUPPORTED, "d=%d too large for the fused tensor-core kernel", Q.d);
+  a.stages = stages;
+  a.nkb = Q.nkb;
+  // at least half the SM's shared memory, so one CTA per SM owns the TMEM it allocates
+  const size_t smem = std::max<size_t>(gemm_smem_layout(pieces, Q.nkb, stages, queues).total + 1024,
+                                       di.smem_optin / 2 + 1024);
+  const int nitems = a.nqt * a.chunks;
+  const int grid = std::min(nitems, di.sm_count);
+  a.status = device_status();
+  if (!a.status) return set_error(GBK_ECUDA, "device status word unavailable");
+  ProfScope prof(prec == GBK_PREC_FP32 ? "dist_gemm_tf32x3"
+                 : prec == GBK_PREC_BF16 ? "dist_gemm_bf16" : "dist_gemm_fp8", st);
+  if (prec == GBK_PREC_FP32)
+    return launch_dist_gemm_tf32x3(mode, kpr, largest, maps, a, grid, smem, st);
+  if (prec == GBK_PREC_BF16)
+    return launch_dist_gemm_bf16(mode, kpr, largest, maps, a, grid, smem, st);
+  return launch_dist_gemm_fp8(mode, kpr, largest, maps, a, grid, smem, st);
+}
+
+// Distances of every (query, database) pair: max(0, ||x||^2 + ||y||^2 - 2<x,y>) for L2,
+// <x,y> for inner product.
+gbk_status pairwise_run(const PreparedOperand& Q, const PreparedOperand& B, bool ip, float* out,
+                        int64_t ldo, cudaStream_t st) {
+  GemmArgs a = {};
+  a.nq = (int)Q.n;
+  a.nb = (int)B.n;
+  a.nqt = (int)((Q.n + GEMM_BM - 1) / GEMM_BM);
+  a.ntiles = (int)((B.n + GEMM_BN - 1) / GEMM_BN);
+  a.chunks = plan_chunks(a.nqt, a.ntiles, device_info().sm_count);
+  a.tpc = (a.ntiles + a.chunks - 1) / a.chunks;
+  a.chunks = (a.ntiles + a.tpc - 1) / a.tpc;
+  a.ynorm = B.norms.as<float>();
+  a.xnorm = ip ? nullptr : Q.norms.as<float>();
+  a.qscale = Q.scale.as<float>();
+  a.bscale = B.scale.as<float>();
+  a.out = out;
+  a.ldo = ldo;
+  return gemm_launch(MODE_STORE, 0, ip, Q, B, a, st);
+}
+
+// Top-k (ascending distance / descending inner product) of prepared operands in their
+// own precision, written as full distances D and database rows I.
+static gbk_status select_run(const float* xq, const PreparedOperand& Q, const PreparedOperand& B,
+                             int64_t nq, int64_t nb, int d, int k, bool ip, int chunks_opt,
+                             float* D, int64_t* I, cudaStream_t st) {
+  gbk_status r;
+  const int ntiles = (int)((nb + GEMM_BN - 1) / GEMM_BN);
+  if (k > 256) {
+    // Large k: distance blocks of t_q queries x nb (section 5.1 tiling over queries), each
+    // followed by a row-wise k-selection of the full distances.
+    const int64_t budget = (int64_t)1 << 31;  // bytes of distance block
+    int64_t tq = std::max<int64_t>(GEMM_BM, budget / (4 * nb) / GEMM_BM * GEMM_BM);
+    tq = std::min(tq, nq);
+    Scratch blk;
+    if ((r = blk.alloc(sizeof(float) * (size_t)(tq * nb), st)) != GBK_OK) return r;
+    for (int64_t q0 = 0; q0 < nq; q0 += tq) {
+      const int64_t nqb = std::min(tq, nq - q0);
+      PreparedOperand Qb;
+      if ((r = prepare_operand(xq + q0 * d, nqb, d, Q.prec, nqb, 0.f, &Qb, st)) != GBK_OK)
+        return r;
+      if ((r = pairwise_run(Qb, B, ip, blk.as<float>(), nb, st)) != GBK_OK) return r;
+      if ((r = kselect_run(blk.as<float>(), nqb, nb, k, ip, D + q0 * k, I + q0 * k, st,
+                           nullptr)) != GBK_OK)
+        return r;
+    }
+    return GBK_OK;
+  }
+  GemmArgs a = {};
+  a.nq = (int)nq;
+  a.nb = (int)nb;
+  a.nqt = (int)((nq + GEMM_BM - 1) / GEMM_BM);
+  a.ntiles = ntiles;
+  a.chunks = chunks_opt > 0 ? std::min(chunks_opt, ntiles)
+                            : plan_chunks(a.nqt, ntiles, device_info().sm_count);
+  a.tpc = (ntiles + a.chunks - 1) / a.chunks;
+  a.chunks = (ntiles + a.tpc - 1) / a.tpc;
+  a.k = k;
+  a.kp = k == 1 ? 1 : std::max(32, 1 << (32 - __builtin_clz((unsigned)(k - 1))));
+  a.ynorm = B.norms.as<float>();
+  a.qscale = Q.scale.as<float>();
+  a.bscale = B.scale.as<float>();
+  Scratch part, thr;
+  if ((r = part.alloc(sizeof(uint64_t) * (size_t)nq * a.chunks * a.kp, st)) != GBK_OK) return r;
+  if ((r = thr.alloc(sizeof(uint32_t) * (size_t)nq, st)) != GBK_OK) return r;
+  GBK_CUDA_CHECK(cudaMemsetAsync(thr.p, 0xff, sizeof(uint32_t) * (size_t)nq, st));
+  a.part = part.as<uint64_t>();
+  a.thr_key = thr.as<uint32_t>();
+  const int kpr = k == 1 ? 0 : a.kp / 32;
+  if ((r = gemm_launch(MODE_SELECT, kpr, ip, Q, B, a, st)) != GBK_OK) return r;
+  return knn_merge(a.part, nq, a.chunks, a.kp, k, ip ? nullptr : Q.norms.as<float>(), ip, D, I,
+                   st);
+}
+
+gbk_status knn_run(const float* xq, int64_t nq, const float* xb, int64_t nb, int d, int k,
+                   int metric, float* D, int64_t* I, const KnnPlan& plan, cudaStream_t st) {
+  if (nq == 0) return GBK_OK;
+  const bool ip = metric == GBK_METRIC_IP;
+  const int ntiles = (int)((nb + GEMM_BN - 1) / GEMM_BN);
+  PreparedOperand Q, B;
+  gbk_status r;
+  if ((r = prepare_operand(xq, nq, d, plan.prec, nq, 0.f, &Q, st)) != GBK_OK) return r;
+  if ((r = prepare_operand(xb, nb, d, plan.prec, (int64_t)ntiles * GEMM_BN, 0.f, &B, st)) !=
+      GBK_OK)
+    return r;
+  if (plan.prec == GBK_PREC_FP32) return select_run(xq, Q, B, nq, nb, d, k, ip, plan.chunks, D, I, st);
+  // low precision: over-fetch k' candidates, then exact float32 re-rank + certificate
+  int kp = plan.kprime > 0 ? plan.kprime : std::min(4 * k, GBK_MAX_K);
+  kp = (int)std::min<int64_t>(std::max(kp, k), nb);
+  Scratch Dc, Ic;
+  if ((r = Dc.alloc(sizeof(float) * (size_t)nq * kp, st)) != GBK_OK) return r;
+  if ((r = Ic.alloc(sizeof(int64_t) * (size_t)nq * kp, st)) != GBK_OK) return r;
+  if ((r = select_run(xq, Q, B, nq, nb, d, kp, ip, plan.chunks, Dc.as<float>(), Ic.as<int64_t>(),
+                      st)) != GBK_OK)
+    return r;
+  return rerank_run(xq, xb, nq, nb, d, kp, k, ip, plan.prec, Q.norms.as<float>(),
+                    Q.scale.as<float>(), B.norms.as<float>(), B.scale.as<float>(),
+                    Ic.as<int64_t>(), Dc.as<float>(), D, I, plan.certified, plan.error_bound, st);
+}
+
+}  // namespace gbk

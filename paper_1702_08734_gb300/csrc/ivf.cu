@@ -1,0 +1,395 @@
+// IVFADC index (section 2 "Compressed-domain search", section 5.2-5.3): coarse quantizer
+// q1 trained by k-means, product quantizer q2 on the residuals, inverted lists stored as
+// two arrays (codes, ids), and the batch search of Algorithm 4.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "ivf.cuh"
+#include "knn.cuh"
+
+namespace gbk {
+
+gbk_status ivf_scan_run(int M, int64_t nq, int nprobe, int k, const int64_t* cl_I,
+                        const float* cl_D, const float* T, const float* t3, const float* xq,
+                        const float* coarse, const float* pq, int d, bool direct,
+                        const int64_t* list_off, const uint8_t* codes, const int64_t* ids,
+                        float* D, int64_t* I, cudaStream_t st);
+gbk_status pq_encode_run(const float* x, int64_t n, int d, int M, const float* coarse,
+                         const int32_t* lists, const float* pq, uint8_t* codes, cudaStream_t st);
+gbk_status term1_run(const float* coarse, const float* pq, int nlist, int d, int M, float* T,
+                     cudaStream_t st);
+gbk_status term3_run(const float* xq, int64_t nq, const float* pq, int d, int M, float* t3,
+                     cudaStream_t st);
+
+// Persistent device allocation owned by an index (freed in gbk_ivfpq_destroy).
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  gbk_status alloc(size_t b) {
+    release();
+    if (b == 0) return GBK_OK;
+    if (cudaMalloc(&p, b) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return set_error(GBK_ENOMEM, "cudaMalloc(%zu) failed for index storage", b);
+    }
+    bytes = b;
+    return GBK_OK;
+  }
+  // grow to at least b bytes, keeping the first `keep` bytes (stream-ordered copy)
+  gbk_status grow(size_t b, size_t keep, cudaStream_t st) {
+    if (b <= bytes) return GBK_OK;
+    void* q = nullptr;
+    if (cudaMalloc(&q, b) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(GBK_ENOMEM, "cudaMalloc(%zu) failed for index storage", b);
+    }
+    if (keep) GBK_CUDA_CHECK(cudaMemcpyAsync(q, p, keep, cudaMemcpyDeviceToDevice, st));
+    GBK_CUDA_CHECK(cudaStreamSynchronize(st));
+    release();
+    p = q;
+    bytes = b;
+    return GBK_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+}  // namespace gbk
+
+struct gbk_index {
+  int d = 0, nlist = 0, M = 0, dsub = 0;
+  bool trained = false;
+  int use_precomputed = 1;
+  gbk::DevBuf coarse, pq, T;
+  // insertion-order staging: every added vector's list, code and id
+  gbk::DevBuf st_list, st_codes, st_ids;
+  int64_t n_staged = 0, cap_staged = 0;
+  // inverted file (built from the staging arrays on demand)
+  gbk::DevBuf list_off, codes, ids;
+  int64_t ntotal = 0;
+  bool dirty = true;
+  int64_t max_list = 0;
+  ~gbk_index() {
+    coarse.release();
+    pq.release();
+    T.release();
+    st_list.release();
+    st_codes.release();
+    st_ids.release();
+    list_off.release();
+    codes.release();
+    ids.release();
+  }
+};
+
+namespace gbk {
+
+namespace {
+
+__global__ void residual_kernel(const float* __restrict__ x, int64_t n, int d,
+                                const float* __restrict__ coarse, const int64_t* __restrict__ a,
+                                float* __restrict__ r) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * d;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / d;
+    const int t = (int)(e % d);
+    r[e] = x[e] - coarse[a[i] * d + t];
+  }
+}
+
+__global__ void stage_lists_kernel(const int64_t* __restrict__ a, int64_t n,
+                                   int32_t* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (int32_t)a[i];
+}
+
+__global__ void stage_ids_kernel(const int64_t* __restrict__ ids, int64_t n, int64_t first,
+                                 int64_t* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = ids ? ids[i] : first + i;
+}
+
+// codes/ids in list order: out[j] = in[order[j]]
+__global__ void gather_codes_kernel(const uint8_t* __restrict__ in, const int64_t* __restrict__ order,
+                                    int64_t n, int M, uint8_t* __restrict__ out,
+                                    const int64_t* __restrict__ ids_in, int64_t* __restrict__ ids_out) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t src = order[j];
+    if ((M & 15) == 0) {
+      const uint4* s4 = reinterpret_cast<const uint4*>(in + src * M);
+      uint4* d4 = reinterpret_cast<uint4*>(out + j * M);
+      for (int w = 0; w < M / 16; w++) d4[w] = s4[w];
+    } else {
+      for (int m = 0; m < M; m++) out[j * M + m] = in[src * M + m];
+    }
+    ids_out[j] = ids_in[src];
+  }
+}
+
+int grid_for(int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256,
+                                                     (int64_t)device_info().sm_count * 16));
+}
+
+gbk_status finalize(gbk_index* ix, cudaStream_t st) {
+  if (!ix->dirty) return GBK_OK;
+  gbk_status r;
+  const int64_t n = ix->n_staged;
+  if ((r = ix->list_off.alloc(sizeof(int64_t) * (size_t)(ix->nlist + 1))) != GBK_OK) return r;
+  if ((r = ix->codes.alloc((size_t)std::max<int64_t>(n, 1) * ix->M)) != GBK_OK) return r;
+  if ((r = ix->ids.alloc(sizeof(int64_t) * (size_t)std::max<int64_t>(n, 1))) != GBK_OK) return r;
+  Scratch order;
+  if ((r = order.alloc(sizeof(int64_t) * (size_t)std::max<int64_t>(n, 1), st)) != GBK_OK) return r;
+  if ((r = bucket_stable(ix->st_list.as<int32_t>(), n, ix->nlist, ix->list_off.as<int64_t>(),
+                         order.as<int64_t>(), st)) != GBK_OK)
+    return r;
+  if (n > 0) {
+    gather_codes_kernel<<<grid_for(n), 256, 0, st>>>(ix->st_codes.as<uint8_t>(),
+                                                     order.as<int64_t>(), n, ix->M,
+                                                     ix->codes.as<uint8_t>(),
+                                                     ix->st_ids.as<int64_t>(),
+                                                     ix->ids.as<int64_t>());
+    GBK_LAUNCH_CHECK();
+  }
+  ix->ntotal = n;
+  ix->dirty = false;
+  return GBK_OK;
+}
+
+}  // namespace
+
+}  // namespace gbk
+
+using namespace gbk;
+
+extern "C" {
+
+gbk_status gbk_ivfpq_create(int32_t d, int32_t nlist, int32_t M, int32_t nbits, int32_t metric,
+                            gbk_index** out) {
+  clear_error();
+  GBK_REQUIRE(out, "gbk_ivfpq_create: out is NULL");
+  GBK_REQUIRE(d >= 1 && nlist >= 1 && nlist < (1 << 30), "gbk_ivfpq_create: bad d or nlist");
+  GBK_REQUIRE(M >= 1 && d % M == 0, "gbk_ivfpq_create: M must divide d");
+  if (nbits != 8) return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: only 8-bit codes");
+  if (metric != GBK_METRIC_L2)
+    return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: IVFADC is defined for L2 (Eq. 6)");
+  if (M != 8 && M != 16 && M != 32)
+    return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: M must be 8, 16 or 32");
+  if (d / M > 32) return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: d/M must be <= 32");
+  gbk_index* ix = new gbk_index();
+  ix->d = d;
+  ix->nlist = nlist;
+  ix->M = M;
+  ix->dsub = d / M;
+  *out = ix;
+  return GBK_OK;
+}
+
+void gbk_ivfpq_destroy(gbk_index* ix) { delete ix; }
+
+gbk_status gbk_ivfpq_train(gbk_index* ix, const float* x, int64_t n, const gbk_train_opts* opts,
+                           void* stream) {
+  clear_error();
+  GBK_REQUIRE(ix && x, "gbk_ivfpq_train: NULL argument");
+  GBK_REQUIRE(n >= ix->nlist && n >= 256 && n < (int64_t(1) << 31),
+              "gbk_ivfpq_train: need max(nlist, 256) <= n < 2^31 training vectors");
+  cudaStream_t st = as_stream(stream);
+  const int niter = opts && opts->niter > 0 ? opts->niter : 20;
+  const int pq_niter = opts && opts->pq_niter > 0 ? opts->pq_niter : niter;
+  std::vector<int64_t> cinit(ix->nlist), pinit(256);
+  for (int i = 0; i < ix->nlist; i++) cinit[i] = opts && opts->coarse_init ? opts->coarse_init[i] : i;
+  for (int i = 0; i < 256; i++) pinit[i] = opts && opts->pq_init ? opts->pq_init[i] : i;
+  for (int64_t v : cinit) GBK_REQUIRE(v >= 0 && v < n, "gbk_ivfpq_train: coarse_init out of range");
+  for (int64_t v : pinit) GBK_REQUIRE(v >= 0 && v < n, "gbk_ivfpq_train: pq_init out of range");
+  if (opts) ix->use_precomputed = opts->use_precomputed;
+  gbk_status r;
+  const int d = ix->d, M = ix->M, dsub = ix->dsub;
+  if ((r = ix->coarse.alloc(sizeof(float) * (size_t)ix->nlist * d)) != GBK_OK) return r;
+  if ((r = ix->pq.alloc(sizeof(float) * (size_t)M * 256 * dsub)) != GBK_OK) return r;
+  Scratch ci, pi, a, dist, res, sub;
+  if ((r = ci.alloc(sizeof(int64_t) * ix->nlist, st)) != GBK_OK) return r;
+  if ((r = pi.alloc(sizeof(int64_t) * 256, st)) != GBK_OK) return r;
+  GBK_CUDA_CHECK(cudaMemcpyAsync(ci.p, cinit.data(), sizeof(int64_t) * ix->nlist,
+                                 cudaMemcpyHostToDevice, st));
+  GBK_CUDA_CHECK(cudaMemcpyAsync(pi.p, pinit.data(), sizeof(int64_t) * 256, cudaMemcpyHostToDevice,
+                                 st));
+  // coarse quantizer q1 (Eq. 3) by k-means, assignment on the tensor cores
+  if ((r = kmeans_run(x, n, d, d, ix->nlist, niter, ci.as<int64_t>(), ix->coarse.as<float>(),
+                      nullptr, nullptr, false, st)) != GBK_OK)
+    return r;
+  // residuals y - q1(y)
+  if ((r = a.alloc(sizeof(int64_t) * (size_t)n, st)) != GBK_OK) return r;
+  if ((r = dist.alloc(sizeof(float) * (size_t)n, st)) != GBK_OK) return r;
+  if ((r = res.alloc(sizeof(float) * (size_t)n * d, st)) != GBK_OK) return r;
+  KnnPlan plan;
+  if ((r = knn_run(x, n, ix->coarse.as<float>(), ix->nlist, d, 1, GBK_METRIC_L2, dist.as<float>(),
+                   a.as<int64_t>(), plan, st)) != GBK_OK)
+    return r;
+  residual_kernel<<<grid_for(n * d), 256, 0, st>>>(x, n, d, ix->coarse.as<float>(),
+                                                    a.as<int64_t>(), res.as<float>());
+  GBK_LAUNCH_CHECK();
+  // product quantizer: 256-centroid k-means per sub-vector block (section 2)
+  for (int m = 0; m < M; m++) {
+    if ((r = kmeans_run(res.as<float>() + m * dsub, n, dsub, d, 256, pq_niter, pi.as<int64_t>(),
+                        ix->pq.as<float>() + (size_t)m * 256 * dsub, nullptr, nullptr, true,
+                        st)) != GBK_OK)
+      return r;
+  }
+  // term-1 table (Eq. 11)
+  if (ix->use_precomputed) {
+    if ((r = ix->T.alloc(sizeof(float) * (size_t)ix->nlist * M * 256)) != GBK_OK) return r;
+    if ((r = term1_run(ix->coarse.as<float>(), ix->pq.as<float>(), ix->nlist, d, M,
+                       ix->T.as<float>(), st)) != GBK_OK)
+      return r;
+  }
+  ix->trained = true;
+  return GBK_OK;
+}
+
+gbk_status gbk_ivfpq_set_quantizers(gbk_index* ix, const float* coarse, const float* pq,
+                                    int32_t use_precomputed, void* stream) {
+  clear_error();
+  GBK_REQUIRE(ix && coarse && pq, "gbk_ivfpq_set_quantizers: NULL argument");
+  cudaStream_t st = as_stream(stream);
+  gbk_status r;
+  const size_t cb = sizeof(float) * (size_t)ix->nlist * ix->d;
+  const size_t pb = sizeof(float) * (size_t)ix->M * 256 * ix->dsub;
+  if ((r = ix->coarse.alloc(cb)) != GBK_OK) return r;
+  if ((r = ix->pq.alloc(pb)) != GBK_OK) return r;
+  GBK_CUDA_CHECK(cudaMemcpyAsync(ix->coarse.p, coarse, cb, cudaMemcpyDefault, st));
+  GBK_CUDA_CHECK(cudaMemcpyAsync(ix->pq.p, pq, pb, cudaMemcpyDefault, st));
+  ix->use_precomputed = use_precomputed;
+  if (use_precomputed) {
+    if ((r = ix->T.alloc(sizeof(float) * (size_t)ix->nlist * ix->M * 256)) != GBK_OK) return r;
+    if ((r = term1_run(ix->coarse.as<float>(), ix->pq.as<float>(), ix->nlist, ix->d, ix->M,
+                       ix->T.as<float>(), st)) != GBK_OK)
+      return r;
+  }
+  ix->trained = true;
+  return GBK_OK;
+}
+
+gbk_status gbk_ivfpq_add(gbk_index* ix, const float* x, int64_t n, const int64_t* ids,
+                         void* stream) {
+  clear_error();
+  GBK_REQUIRE(ix, "gbk_ivfpq_add: NULL index");
+  GBK_REQUIRE(ix->trained, "gbk_ivfpq_add: index not trained");
+  GBK_REQUIRE(n >= 0, "gbk_ivfpq_add: n < 0");
+  if (n == 0) return GBK_OK;
+  GBK_REQUIRE(x, "gbk_ivfpq_add: NULL x");
+  GBK_REQUIRE(ix->n_staged + n < (int64_t(1) << 32) - 1, "gbk_ivfpq_add: index full (2^32)");
+  cudaStream_t st = as_stream(stream);
+  gbk_status r;
+  const int64_t need = ix->n_staged + n;
+  if (need > ix->cap_staged) {
+    int64_t cap = std::max<int64_t>(need, ix->cap_staged * 2);
+    const size_t keep = (size_t)ix->n_staged;
+    if ((r = ix->st_list.grow(sizeof(int32_t) * cap, sizeof(int32_t) * keep, st)) != GBK_OK) return r;
+    if ((r = ix->st_codes.grow((size_t)cap * ix->M, keep * ix->M, st)) != GBK_OK) return r;
+    if ((r = ix->st_ids.grow(sizeof(int64_t) * cap, sizeof(int64_t) * keep, st)) != GBK_OK) return r;
+    ix->cap_staged = cap;
+  }
+  Scratch a, dist;
+  if ((r = a.alloc(sizeof(int64_t) * (size_t)n, st)) != GBK_OK) return r;
+  if ((r = dist.alloc(sizeof(float) * (size_t)n, st)) != GBK_OK) return r;
+  KnnPlan plan;
+  // q1(y): nearest coarse centroid (exact, k = 1)
+  if ((r = knn_run(x, n, ix->coarse.as<float>(), ix->nlist, ix->d, 1, GBK_METRIC_L2,
+                   dist.as<float>(), a.as<int64_t>(), plan, st)) != GBK_OK)
+    return r;
+  int32_t* lists = ix->st_list.as<int32_t>() + ix->n_staged;
+  stage_lists_kernel<<<grid_for(n), 256, 0, st>>>(a.as<int64_t>(), n, lists);
+  stage_ids_kernel<<<grid_for(n), 256, 0, st>>>(ids, n, ix->n_staged,
+                                                ix->st_ids.as<int64_t>() + ix->n_staged);
+  GBK_LAUNCH_CHECK();
+  if ((r = pq_encode_run(x, n, ix->d, ix->M, ix->coarse.as<float>(), lists, ix->pq.as<float>(),
+                         ix->st_codes.as<uint8_t>() + (size_t)ix->n_staged * ix->M, st)) != GBK_OK)
+    return r;
+  ix->n_staged += n;
+  ix->dirty = true;
+  return GBK_OK;
+}
+
+gbk_status gbk_ivfpq_search(gbk_index* ix, const float* xq, int64_t nq, int32_t k, int32_t nprobe,
+                            float* D, int64_t* I, void* stream) {
+  clear_error();
+  GBK_REQUIRE(ix, "gbk_ivfpq_search: NULL index");
+  GBK_REQUIRE(ix->trained, "gbk_ivfpq_search: index not trained");
+  GBK_REQUIRE(k >= 1 && k <= GBK_MAX_K, "gbk_ivfpq_search: k out of [1, %d]", GBK_MAX_K);
+  GBK_REQUIRE(nprobe >= 1 && nprobe <= ix->nlist && nprobe <= GBK_MAX_K,
+              "gbk_ivfpq_search: nprobe out of [1, min(nlist, %d)]", GBK_MAX_K);
+  GBK_REQUIRE(nq >= 0 && nq < (int64_t(1) << 31), "gbk_ivfpq_search: nq out of range");
+  if (nq == 0) return GBK_OK;
+  GBK_REQUIRE(xq && D && I, "gbk_ivfpq_search: NULL pointer");
+  cudaStream_t st = as_stream(stream);
+  gbk_status r;
+  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  Scratch clD, clI, t3;
+  if ((r = clD.alloc(sizeof(float) * (size_t)nq * nprobe, st)) != GBK_OK) return r;
+  if ((r = clI.alloc(sizeof(int64_t) * (size_t)nq * nprobe, st)) != GBK_OK) return r;
+  // L_IVF (Eq. 5): the nprobe nearest coarse centroids, with term 2 = ||x - c||^2
+  KnnPlan plan;
+  if ((r = knn_run(xq, nq, ix->coarse.as<float>(), ix->nlist, ix->d, nprobe, GBK_METRIC_L2,
+                   clD.as<float>(), clI.as<int64_t>(), plan, st)) != GBK_OK)
+    return r;
+  const bool direct = !ix->use_precomputed;
+  if (!direct) {
+    if ((r = t3.alloc(sizeof(float) * (size_t)nq * ix->M * 256, st)) != GBK_OK) return r;
+    if ((r = term3_run(xq, nq, ix->pq.as<float>(), ix->d, ix->M, t3.as<float>(), st)) != GBK_OK)
+      return r;
+  }
+  return ivf_scan_run(ix->M, nq, nprobe, k, clI.as<int64_t>(), clD.as<float>(), ix->T.as<float>(),
+                      t3.as<float>(), xq, ix->coarse.as<float>(), ix->pq.as<float>(), ix->d,
+                      direct, ix->list_off.as<int64_t>(), ix->codes.as<uint8_t>(),
+                      ix->ids.as<int64_t>(), D, I, st);
+}
+
+gbk_status gbk_ivfpq_info(gbk_index* ix, int64_t* ntotal, int32_t* nlist, int32_t* d, int32_t* M,
+                          void* stream) {
+  clear_error();
+  GBK_REQUIRE(ix, "gbk_ivfpq_info: NULL index");
+  gbk_status r;
+  if (ix->trained && (r = finalize(ix, as_stream(stream))) != GBK_OK) return r;
+  if (ntotal) *ntotal = ix->n_staged;
+  if (nlist) *nlist = ix->nlist;
+  if (d) *d = ix->d;
+  if (M) *M = ix->M;
+  return GBK_OK;
+}
+
+gbk_status gbk_ivfpq_export(gbk_index* ix, float* coarse, float* pq, int64_t* list_off,
+                            uint8_t* codes, int64_t* ids, void* stream) {
+  clear_error();
+  GBK_REQUIRE(ix && ix->trained, "gbk_ivfpq_export: index missing or not trained");
+  cudaStream_t st = as_stream(stream);
+  gbk_status r;
+  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  if (coarse)
+    GBK_CUDA_CHECK(cudaMemcpyAsync(coarse, ix->coarse.p, ix->coarse.bytes, cudaMemcpyDefault, st));
+  if (pq) GBK_CUDA_CHECK(cudaMemcpyAsync(pq, ix->pq.p, ix->pq.bytes, cudaMemcpyDefault, st));
+  if (list_off)
+    GBK_CUDA_CHECK(cudaMemcpyAsync(list_off, ix->list_off.p, sizeof(int64_t) * (ix->nlist + 1),
+                                   cudaMemcpyDefault, st));
+  if (codes && ix->ntotal)
+    GBK_CUDA_CHECK(cudaMemcpyAsync(codes, ix->codes.p, (size_t)ix->ntotal * ix->M,
+                                   cudaMemcpyDefault, st));
+  if (ids && ix->ntotal)
+    GBK_CUDA_CHECK(cudaMemcpyAsync(ids, ix->ids.p, sizeof(int64_t) * ix->ntotal, cudaMemcpyDefault,
+                                   st));
+  return GBK_OK;
+}
+
+}  // extern "C"

@@ -2,8 +2,8 @@
 // pass over the input at memory bandwidth).
 //
 // One thread block per (row, segment).  Threads stream the segment with 16-byte
-// loads (cache-streaming), compare each value once against the block threshold and
-// append the rare survivors to a shared buffer (select_core.cuh).  Long rows are cut
+// loads (cache-streaming, eight in flight per thread), compare each value once against
+// the block threshold and append the rare survivors to a shared buffer (select_core.cuh).  Long rows are cut
 // into segments when there are too few rows to fill the GPU; each segment leaves its
 // k best composites in scratch and a merge kernel selects across segments - the
 // paper's two-pass k-selection (section 5.3, "Multi-pass kernels").  k = 1 is a plain
@@ -13,6 +13,7 @@
 #include "common.cuh"
 #include "kselect.cuh"
 #include "select_core.cuh"
+#include "sm100.cuh"
 
 namespace gbk {
 
@@ -20,40 +21,48 @@ namespace {
 
 template <int THREADS, int KP, int UNROLL, bool LARGEST>
 struct KselCfg {
-  static constexpr int CHUNK = THREADS * UNROLL * 4;
-  static constexpr int CAP = 2 * CHUNK;
+  static constexpr int PT = UNROLL * 4;          // floats per thread per iteration
+  static constexpr int CHUNK = THREADS * PT;     // floats per block iteration
+  static constexpr int CAP = 2048;               // candidate buffer
+  static_assert(PT <= 32, "one 32-bit mask per thread");
   using Sel = BlockSelect<THREADS, KP, CAP>;
-  static constexpr size_t SMEM = sizeof(typename Sel::Smem);
+  static constexpr size_t SMEM = 16 + sizeof(typename Sel::Smem);
 };
 
+// One block per work unit (a row, or a segment of one).  Every thread keeps UNROLL 16-byte
+// loads in flight per iteration (32 KB per block, ~128 KB per SM at four blocks), filters
+// them against the block threshold and appends survivors with one reservation per warp.
+// A reservation that does not fit the buffer is not written; that warp keeps its values in
+// registers and offers them again after the block compacts (block-uniform offer rounds),
+// so the buffer never needs room for a worst-case iteration.
 template <int THREADS, int KP, int UNROLL, bool LARGEST>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 4)
     kselect_rows_kernel(const float* __restrict__ vals, int64_t len, int k, int segs,
                         int64_t seg_len, float* __restrict__ outD, int64_t* __restrict__ outI,
                         uint64_t* __restrict__ part) {
   using C = KselCfg<THREADS, KP, UNROLL, LARGEST>;
   using Sel = typename C::Sel;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(smem_raw);
-  const int tid = threadIdx.x;
-  const int64_t row = blockIdx.x / segs;
-  const int seg = blockIdx.x % segs;
-  const float* rowp = vals + row * len;
+  int* overflow = reinterpret_cast<int*>(smem_raw);
+  int* n_ok = overflow + 1;
+  typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(smem_raw + 16);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t unit = blockIdx.x;
+  const int64_t row = unit / segs;
+  const int seg = (int)(unit % segs);
   const int64_t s0 = (int64_t)seg * seg_len;
-  const int64_t s1 = min(len, s0 + seg_len);
-  const int64_t n = s1 - s0;
+  const int64_t n = (len < s0 + seg_len ? len : s0 + seg_len) - s0;
+  const float* rowp = vals + row * len;
   const float* p = rowp + s0;
-
+  const int64_t he = (int64_t)(((16u - ((uintptr_t)p & 15u)) & 15u) / 4);
+  const int head = (int)(n < he ? n : he);
+  const int64_t n4 = (n - head) / 4;
+  const int tail = (int)(n - head - n4 * 4);
   Sel::init(s);
+  if (tid == 0) *overflow = 0;
   __syncthreads();
   ValueFilter f;
   f.set(NAN_KEY, LARGEST);
-
-  // scalar head (until 16-byte alignment) and tail
-  const int64_t head_e = (int64_t)(((16u - ((uintptr_t)p & 15u)) & 15u) / 4);
-  const int head = (int)(n < head_e ? n : head_e);
-  const int64_t n4 = (n - head) / 4;
-  const int tail = (int)(n - head - n4 * 4);
   {
     uint64_t c[1];
     uint32_t mask = 0;
@@ -61,7 +70,7 @@ __global__ void __launch_bounds__(THREADS)
     if (tid < head) e = tid;
     else if (tid >= 32 && tid < 32 + tail) e = head + n4 * 4 + (tid - 32);
     if (e >= 0) {
-      float v = p[e];
+      const float v = p[e];
       if (f.pass(v)) {
         c[0] = composite(ordered_key(v, LARGEST), (uint32_t)(s0 + e));
         mask = 1u;
@@ -69,48 +78,90 @@ __global__ void __launch_bounds__(THREADS)
     }
     Sel::template push<1>(s, mask, c);
   }
+  __syncthreads();
+  if (tid == 0) *n_ok = s.n_buf;
   const float4* p4 = reinterpret_cast<const float4*>(p + head);
   const uint32_t idx0 = (uint32_t)(s0 + head);
   for (int64_t base = 0; base < n4; base += (int64_t)THREADS * UNROLL) {
-    float4 v[UNROLL];
+    float v[C::PT];
 #pragma unroll
     for (int u = 0; u < UNROLL; u++) {
       const int64_t i = base + u * THREADS + tid;
-      if (i < n4) v[u] = __ldcs(p4 + i);
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < n4) x = __ldcs(p4 + i);
+      v[u * 4 + 0] = x.x;
+      v[u * 4 + 1] = x.y;
+      v[u * 4 + 2] = x.z;
+      v[u * 4 + 3] = x.w;
     }
-    uint64_t c[UNROLL * 4];
-    uint32_t mask = 0;
+    bool pending = true;
+    for (;;) {
+      uint32_t mask = 0;
+      if (pending) {
 #pragma unroll
-    for (int u = 0; u < UNROLL; u++) {
-      const int64_t i = base + u * THREADS + tid;
-      if (i < n4) {
-        const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+        for (int u = 0; u < UNROLL; u++) {
+          if (base + u * THREADS + tid < n4) {
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-          if (f.pass(x[j])) {
-            mask |= 1u << (u * 4 + j);
-            c[u * 4 + j] = composite(ordered_key(x[j], LARGEST), idx0 + (uint32_t)(i * 4 + j));
+            for (int j = 0; j < 4; j++) mask |= (f.pass(v[u * 4 + j]) ? 1u : 0u) << (u * 4 + j);
           }
         }
       }
-    }
-    Sel::template push<UNROLL * 4>(s, mask, c);
-    __syncthreads();
-    if (s.n_buf > C::CAP - C::CHUNK) {
+      bool retry = false;
+      if (__any_sync(FULL_MASK, mask != 0u)) {
+        const int cnt = __popc(mask);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(FULL_MASK, incl, o);
+          if (lane >= o) incl += t;
+        }
+        int wbase = 0;
+        if (lane == 31) wbase = atomicAdd(&s.n_buf, incl);
+        wbase = __shfl_sync(FULL_MASK, wbase, 31);
+        const int total = __shfl_sync(FULL_MASK, incl, 31);
+        if (wbase + total <= C::CAP) {
+          int pos = wbase + incl - cnt;
+#pragma unroll
+          for (int u = 0; u < UNROLL; u++) {
+            const uint32_t ib = idx0 + (uint32_t)((base + u * THREADS + tid) * 4);
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+              if (mask & (1u << (u * 4 + j)))
+                s.buf[pos++] = composite(ordered_key(v[u * 4 + j], LARGEST), ib + (uint32_t)j);
+          }
+          if (lane == 31) atomicAdd(n_ok, total);
+        } else {
+          retry = true;
+          if (lane == 31) *overflow = 1;
+        }
+      }
+      pending = retry;
+      __syncthreads();
+      const bool ovf = *overflow != 0;
+      if (!ovf) break;  // uniform: nobody writes the flag between the barriers
+      __syncthreads();  // all have read the flag before it is reset
+      if (tid == 0) {
+        s.n_buf = *n_ok;  // successful reservations form a prefix of the buffer
+        *overflow = 0;
+      }
+      __syncthreads();
       Sel::compact(s, k);
       f.set((uint32_t)(s.thr >> 32), LARGEST);
+      if (tid == 0) *n_ok = s.n_buf;
+      __syncthreads();
     }
   }
   Sel::finish(s, k);
   if (segs == 1) {
     for (int j = tid; j < k; j += THREADS) {
-      const uint64_t e = s.top[j];
-      const uint32_t idx = (uint32_t)e;
-      outD[row * k + j] = rowp[idx];
-      outI[row * k + j] = (int64_t)idx;
+      const uint32_t idx = (uint32_t)s.top[j];
+      if (idx < (uint32_t)len) {
+        outD[row * k + j] = rowp[idx];
+        outI[row * k + j] = (int64_t)idx;
+      }
     }
   } else {
-    uint64_t* dst = part + ((int64_t)row * segs + seg) * k;
+    uint64_t* dst = part + unit * k;
     for (int j = tid; j < k; j += THREADS) dst[j] = s.top[j];
   }
 }
@@ -199,7 +250,7 @@ __global__ void __launch_bounds__(THREADS)
                          int64_t* __restrict__ outI) {
   constexpr int CAP = 4096;
   using Sel = BlockSelect<THREADS, KP, CAP>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(smem_raw);
   const int64_t row = blockIdx.x;
   const uint64_t* src = part + row * nper;
@@ -231,22 +282,41 @@ __global__ void __launch_bounds__(THREADS)
   }
 }
 
-template <int THREADS, int KP, int UNROLL, bool LARGEST>
+template <int KP, int UNROLL, bool LARGEST>
 gbk_status launch_rows(const float* vals, int64_t rows, int64_t len, int k, int segs,
-                       int64_t seg_len, float* D, int64_t* I, uint64_t* part,
-                       cudaStream_t stream) {
+                       int64_t seg_len, float* D, int64_t* I, uint64_t* part, cudaStream_t stream) {
+  constexpr int THREADS = 256;
   using C = KselCfg<THREADS, KP, UNROLL, LARGEST>;
   auto kern = kselect_rows_kernel<THREADS, KP, UNROLL, LARGEST>;
   static bool attr_set = false;
   if (!attr_set) {
     GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)C::SMEM));
+    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared));
     attr_set = true;
   }
   kern<<<(unsigned)(rows * segs), THREADS, C::SMEM, stream>>>(vals, len, k, segs, seg_len, D, I,
                                                                 part);
   GBK_LAUNCH_CHECK();
   return GBK_OK;
+}
+
+template <bool LARGEST>
+gbk_status dispatch_rows(const float* vals, int64_t rows, int64_t len, int k, int segs,
+                         int64_t seg_len, float* D, int64_t* I, uint64_t* part,
+                         cudaStream_t st, const KselectTuning& tu) {
+  const bool wide = tu.unroll >= 8;
+#define GBK_ROWS(KP)                                                                         \
+  return wide ? launch_rows<KP, 8, LARGEST>(vals, rows, len, k, segs, seg_len, D, I, part, st) \
+              : launch_rows<KP, 4, LARGEST>(vals, rows, len, k, segs, seg_len, D, I, part, st)
+  if (k <= 32) GBK_ROWS(32);
+  if (k <= 64) GBK_ROWS(64);
+  if (k <= 128) GBK_ROWS(128);
+  if (k <= 256) GBK_ROWS(256);
+  if (k <= 512) GBK_ROWS(512);
+  GBK_ROWS(1024);
+#undef GBK_ROWS
 }
 
 template <int KP>
@@ -268,25 +338,6 @@ gbk_status launch_merge(const uint64_t* part, int64_t rows, int64_t nper, int k,
   return GBK_OK;
 }
 
-template <bool LARGEST>
-gbk_status dispatch_rows(const float* vals, int64_t rows, int64_t len, int k, int segs,
-                         int64_t seg_len, float* D, int64_t* I, uint64_t* part,
-                         cudaStream_t st, const KselectTuning& tu) {
-  const bool wide = tu.unroll >= 4;
-#define GBK_ROWS(KP)                                                                         \
-  return wide ? launch_rows<256, KP, 4, LARGEST>(vals, rows, len, k, segs, seg_len, D, I,  \
-                                                 part, st)                                  \
-              : launch_rows<256, KP, 2, LARGEST>(vals, rows, len, k, segs, seg_len, D, I,  \
-                                                 part, st)
-  if (k <= 32) GBK_ROWS(32);
-  if (k <= 64) GBK_ROWS(64);
-  if (k <= 128) GBK_ROWS(128);
-  if (k <= 256) GBK_ROWS(256);
-  if (k <= 512) GBK_ROWS(512);
-  GBK_ROWS(1024);
-#undef GBK_ROWS
-}
-
 gbk_status dispatch_merge(const uint64_t* part, int64_t rows, int64_t nper, int k,
                           const float* vals, int64_t len, float* D, int64_t* I,
                           cudaStream_t st) {
@@ -303,7 +354,7 @@ gbk_status dispatch_merge(const uint64_t* part, int64_t rows, int64_t nper, int 
 KselectTuning kselect_default_tuning(int64_t rows, int64_t len, int k) {
   KselectTuning t;
   const int sms = device_info().sm_count;
-  t.unroll = (k > 256) ? 4 : 2;
+  t.unroll = 8;
   // enough blocks to fill the GPU several times over; segments no shorter than 8K
   const int64_t target = 4ll * sms;
   int64_t segs = 1;
@@ -331,6 +382,7 @@ gbk_status kselect_run(const float* vals, int64_t rows, int64_t len, int k, bool
   }
   uint64_t* pp = part.as<uint64_t>();
   gbk_status r;
+  ProfScope prof(k == 1 ? "kselect_k1" : "kselect_rows", st);
   if (k == 1) {
     if (largest)
       kselect_k1_kernel<256, true><<<(unsigned)(rows * segs), 256, 0, st>>>(vals, len, (int)segs,

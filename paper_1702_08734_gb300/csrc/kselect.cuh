@@ -9,7 +9,7 @@ namespace gbk {
 
 struct KselectTuning {
   int segs = 1;    // segments per row (two-pass selection when > 1)
-  int unroll = 2;  // float4 loads per thread per iteration (2 or 4)
+  int unroll = 8;  // 16-byte loads in flight per thread per iteration (4 or 8)
 };
 
 KselectTuning kselect_default_tuning(int64_t rows, int64_t len, int k);

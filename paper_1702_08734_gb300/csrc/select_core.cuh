@@ -70,6 +70,16 @@ struct ValueFilter {
   }
 };
 
+// One shared atomic per warp: returns this lane's slot among the lanes with `want`.
+__device__ __forceinline__ int warp_reserve(int& counter, bool want) {
+  const int lane = threadIdx.x & 31;
+  const unsigned b = __ballot_sync(FULL_MASK, want);
+  int base = 0;
+  if (b && lane == __ffs(b) - 1) base = atomicAdd(&counter, __popc(b));
+  base = __shfl_sync(FULL_MASK, base, b ? __ffs(b) - 1 : 0);
+  return base + __popc(b & ((1u << lane) - 1u));
+}
+
 template <int THREADS, int KP, int CAP>
 struct BlockSelect {
   static_assert(THREADS % 32 == 0, "whole warps");
@@ -114,8 +124,9 @@ struct BlockSelect {
     }
   }
 
-  // Exact k best of top U buf; all threads call it after a __syncthreads().
-  __device__ static void compact(Smem& s, int k) {
+  // Exact k best of top U buf; all threads call it after a __syncthreads().  Kept out of
+  // line: it is the rare path and must not inflate the streaming loop's registers.
+  __device__ __noinline__ static void compact(Smem& s, int k) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int n_top = s.n_top, n_buf = s.n_buf;
     const int total = n_top + n_buf;
@@ -161,9 +172,17 @@ struct BlockSelect {
       const uint32_t dmask = (1u << w) - 1u;
       for (int i = tid; i < 256; i += THREADS) s.hist[i] = 0u;
       __syncthreads();
-      for (int i = tid; i < total; i += THREADS) {
-        uint64_t e = i < n_top ? s.top[i] : s.buf[i - n_top];
-        if (shr64(e, shift) == P) atomicAdd(&s.hist[(uint32_t)(e >> nshift) & dmask], 1u);
+      // warp-aggregated: one shared atomic per distinct digit per warp (the digits of
+      // surviving candidates are highly skewed, plain atomics would serialise)
+      for (int i0 = 0; i0 < total; i0 += THREADS) {
+        const int i = i0 + tid;
+        uint32_t bin = 0xffffffffu;
+        if (i < total) {
+          uint64_t e = i < n_top ? s.top[i] : s.buf[i - n_top];
+          if (shr64(e, shift) == P) bin = (uint32_t)(e >> nshift) & dmask;
+        }
+        const unsigned grp = __match_any_sync(FULL_MASK, bin);
+        if (bin != 0xffffffffu && lane == __ffs(grp) - 1) atomicAdd(&s.hist[bin], (uint32_t)__popc(grp));
       }
       __syncthreads();
       if (tid < 32) {
@@ -221,17 +240,20 @@ struct BlockSelect {
     uint64_t m = 0ull;
 #pragma unroll
     for (int j = 0; j < TPT; j++) {
-      int i = tid + j * THREADS;
-      if (i < n_top && shr64(mine[j], shift) <= P) {
-        int pos = atomicAdd(&s.cnt, 1);
+      const int i = tid + j * THREADS;
+      const bool keep = i < n_top && shr64(mine[j], shift) <= P;
+      const int pos = warp_reserve(s.cnt, keep);
+      if (keep) {
         s.top[pos] = mine[j];
         m = max(m, mine[j]);
       }
     }
-    for (int i = tid; i < n_buf; i += THREADS) {
-      uint64_t e = s.buf[i];
-      if (shr64(e, shift) <= P) {
-        int pos = atomicAdd(&s.cnt, 1);
+    for (int i0 = 0; i0 < n_buf; i0 += THREADS) {
+      const int i = i0 + tid;
+      uint64_t e = i < n_buf ? s.buf[i] : ~0ull;
+      const bool keep = i < n_buf && shr64(e, shift) <= P;
+      const int pos = warp_reserve(s.cnt, keep);
+      if (keep) {
         s.top[pos] = e;
         m = max(m, e);
       }
@@ -247,7 +269,7 @@ struct BlockSelect {
   }
 
   // Final compaction and ascending sort of the kept set into top[0..KP); padding ~0.
-  __device__ static void finish(Smem& s, int k) {
+  __device__ __noinline__ static void finish(Smem& s, int k) {
     __syncthreads();
     compact(s, k);
     const int n = s.n_top;

@@ -82,3 +82,12 @@ def test_invalid_arguments_raise(gbk):
     for k in (0, 11, 2000):
         with pytest.raises(gbk.GbkError):
             gbk.kselect(v, k)
+
+
+@pytest.mark.parametrize("unroll,segments", [(4, 1), (8, 1), (4, 3), (8, 7)])
+def test_launch_options_do_not_change_results(gbk, unroll, segments):
+    v = datagen.uniform_matrix(300 + unroll, 50, 30011)
+    Do, Io = oracle.kselect(v, 77)
+    D, I = gbk.kselect(torch.from_numpy(v).cuda(), 77, unroll=unroll, segments=segments)
+    np.testing.assert_array_equal(I.cpu().numpy(), Io)
+    np.testing.assert_array_equal(D.cpu().numpy(), Do)
