@@ -236,7 +236,7 @@ def main():
     for name, ms in prof:
         by.setdefault(name, []).append(ms)
     hbm, bf16, bf16s, src = peaks()
-    ks_ms = by.get("kselect_stream", [])
+    ks_ms = by.get("kselect_rows", [])
     k1_ms = by.get("kselect_k1", [])
     gemm_ms = by.get("dist_gemm_tf32x3", [])
     ksel_bytes = KSEL_ROWS * KSEL_LEN * 4

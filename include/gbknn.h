@@ -229,6 +229,38 @@ gbk_status gbk_ivfpq_info(gbk_index* index, int64_t* ntotal, int32_t* nlist, int
 gbk_status gbk_ivfpq_export(gbk_index* index, float* coarse, float* pq, int64_t* list_off,
                             uint8_t* codes, int64_t* ids, void* stream);
 
+/* ------------------------------------------------------------------ learned nprobe */
+
+/* A small multilayer perceptron f -> relu(W1 f + b1) -> relu(W2 . + b2) -> W3 . + b3 that
+ * maps per-query features to nprobe classes, trained with softmax cross-entropy and Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8) by the library's own kernels.  The master weights are
+ * float32; forward and backward passes read them rounded to BF16, accumulating in float32.
+ * Parameter layout (one float array): W1 [h1][n_in], b1 [h1], W2 [h2][h1], b2 [h2],
+ * W3 [n_out][h2], b3 [n_out].  Not part of the paper: an addition beside the fixed
+ * nprobe of Eq. (5). */
+typedef struct gbk_mlp gbk_mlp;
+
+/* init_params: host or device array of gbk_mlp_num_params() floats, or NULL for zeros. */
+gbk_status gbk_mlp_create(int32_t n_in, int32_t h1, int32_t h2, int32_t n_out,
+                          const float* init_params, gbk_mlp** out);
+void gbk_mlp_destroy(gbk_mlp* net);
+int64_t gbk_mlp_num_params(const gbk_mlp* net);
+
+/* Copy the master parameters and/or the gradients of the last train step (host or device
+ * destinations, may be NULL). */
+gbk_status gbk_mlp_params(gbk_mlp* net, float* params_out, float* grads_out, void* stream);
+
+/* X [B][n_in] device -> logits [B][n_out] (device, may be NULL) and argmax classes cls [B]
+ * (device int32, may be NULL; ties to the lower class). */
+gbk_status gbk_mlp_forward(gbk_mlp* net, const float* X, int64_t B, float* logits, int32_t* cls,
+                           void* stream);
+
+/* One step on a batch: forward, mean cross-entropy of labels [B] (device int32 in
+ * [0, n_out)), backward; with update != 0 also one Adam step of learning rate lr.  loss:
+ * optional device float receiving the batch loss. */
+gbk_status gbk_mlp_train_step(gbk_mlp* net, const float* X, const int32_t* labels, int64_t B,
+                              float lr, int32_t update, float* loss, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -332,3 +332,65 @@ class IVFPQIndex:
               _stream())
         torch.cuda.current_stream().synchronize()
         return {"coarse": coarse, "pq": pq, "list_off": off, "codes": codes[:n], "ids": ids[:n]}
+
+
+# ---------------------------------------------------------------------------- learned nprobe MLP
+
+_SIGNATURES.update({
+    "gbk_mlp_create": [_i32, _i32, _i32, _i32, _vp, _vp],
+    "gbk_mlp_params": [_vp, _vp, _vp, _vp],
+    "gbk_mlp_forward": [_vp, _vp, _i64, _vp, _vp, _vp],
+    "gbk_mlp_train_step": [_vp, _vp, _vp, _i64, ctypes.c_float, _i32, _vp, _vp],
+})
+
+
+class MLP:
+    """f -> relu(W1 f + b1) -> relu(W2 . + b2) -> W3 . + b3, trained on the GPU (BF16 weights
+    in the passes, float32 master copy and accumulation, Adam)."""
+
+    def __init__(self, n_in, h1, h2, n_out, params=None):
+        lib = load()
+        lib.gbk_mlp_num_params.argtypes = [_vp]
+        lib.gbk_mlp_num_params.restype = ctypes.c_int64
+        lib.gbk_mlp_destroy.argtypes = [_vp]
+        lib.gbk_mlp_destroy.restype = None
+        self.sizes = (int(n_in), int(h1), int(h2), int(n_out))
+        p = None
+        if params is not None:
+            p = torch.as_tensor(params, dtype=torch.float32).contiguous()
+        h = ctypes.c_void_p()
+        _call("gbk_mlp_create", *self.sizes, _ptr(p) if p is not None else None, ctypes.byref(h))
+        self._h = h
+        self.nparam = int(lib.gbk_mlp_num_params(h))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.gbk_mlp_destroy(self._h)
+            self._h = None
+
+    def params(self):
+        out = torch.empty(self.nparam, dtype=torch.float32, device="cuda")
+        _call("gbk_mlp_params", self._h, _ptr(out), None, _stream())
+        return out
+
+    def grads(self):
+        out = torch.empty(self.nparam, dtype=torch.float32, device="cuda")
+        _call("gbk_mlp_params", self._h, None, _ptr(out), _stream())
+        return out
+
+    def forward(self, X: torch.Tensor):
+        _dev(X, torch.float32, "X")
+        B = X.shape[0]
+        z = torch.empty((B, self.sizes[3]), dtype=torch.float32, device=X.device)
+        cls = torch.empty(B, dtype=torch.int32, device=X.device)
+        _call("gbk_mlp_forward", self._h, _ptr(X), B, _ptr(z), _ptr(cls), _stream())
+        return z, cls
+
+    def train_step(self, X: torch.Tensor, labels: torch.Tensor, lr: float = 1e-3,
+                   update: bool = True):
+        _dev(X, torch.float32, "X")
+        _dev(labels, torch.int32, "labels")
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        _call("gbk_mlp_train_step", self._h, _ptr(X), _ptr(labels), X.shape[0], float(lr),
+              int(bool(update)), _ptr(loss), _stream())
+        return loss

@@ -15,7 +15,11 @@ gbk_status ivf_scan_run(int M, int64_t nq, int nprobe, int k, const int64_t* cl_
                         const float* cl_D, const float* T, const float* t3, const float* xq,
                         const float* coarse, const float* pq, int d, bool direct,
                         const int64_t* list_off, const uint8_t* codes, const int64_t* ids,
-                        float* D, int64_t* I, cudaStream_t st);
+                        float* D, int64_t* I, cudaStream_t st, const int32_t* kq = nullptr,
+                        const int32_t* npq = nullptr, const int64_t* out_off = nullptr,
+                        const int64_t* order = nullptr, unsigned long long* counter = nullptr);
+gbk_status scan_cost_run(const int64_t* cl_I, int64_t nq, int nprobe, const int32_t* npq,
+                         const int64_t* off, int32_t* key, cudaStream_t st);
 gbk_status pq_encode_run(const float* x, int64_t n, int d, int M, const float* coarse,
                          const int32_t* lists, const float* pq, uint8_t* codes, cudaStream_t st);
 gbk_status term1_run(const float* coarse, const float* pq, int nlist, int d, int M, float* T,
@@ -389,6 +393,223 @@ gbk_status gbk_ivfpq_export(gbk_index* ix, float* coarse, float* pq, int64_t* li
   if (ids && ix->ntotal)
     GBK_CUDA_CHECK(cudaMemcpyAsync(ids, ix->ids.p, sizeof(int64_t) * ix->ntotal, cudaMemcpyDefault,
                                    st));
+  return GBK_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ mixed batches
+
+namespace gbk {
+namespace {
+
+// F[q] = [x_q, d_i / max(d_0, 1e-12) - 1 for the nfeat nearest coarse distances d_i]
+__global__ void nprobe_features_kernel(const float* __restrict__ xq, int64_t nq, int d,
+                                       const float* __restrict__ clD, int tau, int nfeat,
+                                       float* __restrict__ F) {
+  const int64_t q = blockIdx.x;
+  const int nf = d + nfeat;
+  const float d0 = fmaxf(clD[q * tau], 1e-12f);
+  for (int t = threadIdx.x; t < nf; t += blockDim.x)
+    F[q * nf + t] = t < d ? xq[q * d + t] : clD[q * tau + (t - d)] / d0 - 1.f;
+}
+
+// nprobe of each query from the class chosen by the network: class c -> 2^c, capped.
+__global__ void class_to_nprobe_kernel(const int32_t* __restrict__ cls, int64_t nq, int cap,
+                                       int32_t* __restrict__ np) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nq) np[q] = min(1 << min(cls[q], 30), cap);
+}
+
+__global__ void recall_counts_kernel(const int64_t* __restrict__ I, const int64_t* __restrict__ G,
+                                     int64_t nq, int k, int kg, int32_t* __restrict__ cnt) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  int c = 0;
+  for (int i = 0; i < k; i++) {
+    const int64_t v = I[q * k + i];
+    if (v < 0) continue;
+    for (int j = 0; j < kg; j++)
+      if (G[q * kg + j] == v) {
+        c++;
+        break;
+      }
+  }
+  cnt[q] = c;
+}
+
+}  // namespace
+
+gbk_status mlp_forward_classes(gbk_mlp* net, const float* X, int64_t B, int32_t* cls,
+                               cudaStream_t st);
+
+gbk_status batched_run(gbk_index* ix, const float* xq, int64_t nq, const int32_t* kq, int max_k,
+                       const int32_t* npq_in, int max_nprobe, gbk_mlp* mlp,
+                       const int64_t* out_off, float* D, int64_t* I, int32_t* np_used,
+                       cudaStream_t st) {
+  gbk_status r;
+  const int nfeat = 64;
+  const int tau = std::min(ix->nlist, mlp ? std::max(max_nprobe, nfeat) : max_nprobe);
+  Scratch clD, clI, t3, npq_s, F, cls, key, order, off32, counter;
+  if ((r = clD.alloc(sizeof(float) * (size_t)nq * tau, st)) != GBK_OK) return r;
+  if ((r = clI.alloc(sizeof(int64_t) * (size_t)nq * tau, st)) != GBK_OK) return r;
+  KnnPlan plan;
+  // L_IVF (Eq. 5) for the largest nprobe of the batch, with term 2
+  if ((r = knn_run(xq, nq, ix->coarse.as<float>(), ix->nlist, ix->d, tau, GBK_METRIC_L2,
+                   clD.as<float>(), clI.as<int64_t>(), plan, st)) != GBK_OK)
+    return r;
+  const int32_t* npq = npq_in;
+  if (!npq) {
+    // learned nprobe: features -> network -> class -> nprobe
+    if ((r = npq_s.alloc(sizeof(int32_t) * (size_t)nq, st)) != GBK_OK) return r;
+    if ((r = F.alloc(sizeof(float) * (size_t)nq * (ix->d + nfeat), st)) != GBK_OK) return r;
+    if ((r = cls.alloc(sizeof(int32_t) * (size_t)nq, st)) != GBK_OK) return r;
+    {
+      ProfScope prof("nprobe_features", st);
+      nprobe_features_kernel<<<(unsigned)nq, 128, 0, st>>>(xq, nq, ix->d, clD.as<float>(), tau,
+                                                            std::min(nfeat, tau), F.as<float>());
+      GBK_LAUNCH_CHECK();
+    }
+    if ((r = mlp_forward_classes(mlp, F.as<float>(), nq, cls.as<int32_t>(), st)) != GBK_OK) return r;
+    class_to_nprobe_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(
+        cls.as<int32_t>(), nq, max_nprobe, npq_s.as<int32_t>());
+    GBK_LAUNCH_CHECK();
+    npq = npq_s.as<int32_t>();
+  }
+  if (np_used)
+    GBK_CUDA_CHECK(cudaMemcpyAsync(np_used, npq, sizeof(int32_t) * (size_t)nq,
+                                   cudaMemcpyDeviceToDevice, st));
+  const bool direct = !ix->use_precomputed;
+  if (!direct) {
+    if ((r = t3.alloc(sizeof(float) * (size_t)nq * ix->M * 256, st)) != GBK_OK) return r;
+    if ((r = term3_run(xq, nq, ix->pq.as<float>(), ix->d, ix->M, t3.as<float>(), st)) != GBK_OK)
+      return r;
+  }
+  // longest-first work order for the persistent scan (uneven lists, mixed nprobe)
+  if ((r = key.alloc(sizeof(int32_t) * (size_t)nq, st)) != GBK_OK) return r;
+  if ((r = order.alloc(sizeof(int64_t) * (size_t)nq, st)) != GBK_OK) return r;
+  if ((r = off32.alloc(sizeof(int64_t) * 33, st)) != GBK_OK) return r;
+  if ((r = counter.alloc(sizeof(unsigned long long), st)) != GBK_OK) return r;
+  if ((r = scan_cost_run(clI.as<int64_t>(), nq, tau, npq, ix->list_off.as<int64_t>(),
+                         key.as<int32_t>(), st)) != GBK_OK)
+    return r;
+  if ((r = bucket_stable(key.as<int32_t>(), nq, 32, off32.as<int64_t>(), order.as<int64_t>(), st)) !=
+      GBK_OK)
+    return r;
+  GBK_CUDA_CHECK(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), st));
+  return ivf_scan_run(ix->M, nq, tau, max_k, clI.as<int64_t>(), clD.as<float>(), ix->T.as<float>(),
+                      t3.as<float>(), xq, ix->coarse.as<float>(), ix->pq.as<float>(), ix->d, direct,
+                      ix->list_off.as<int64_t>(), ix->codes.as<uint8_t>(), ix->ids.as<int64_t>(),
+                      D, I, st, kq, npq, out_off, order.as<int64_t>(),
+                      counter.as<unsigned long long>());
+}
+
+}  // namespace gbk
+
+struct gbk_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~gbk_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+extern "C" {
+
+static gbk_status batched_check(gbk_index* ix, const float* xq, int64_t nq, const int32_t* kq,
+                                int32_t max_k, const int32_t* npq, int32_t max_nprobe,
+                                gbk_mlp* mlp, const int64_t* out_off, float* D, int64_t* I) {
+  GBK_REQUIRE(ix && ix->trained, "batched search: index missing or not trained");
+  GBK_REQUIRE(nq >= 0 && nq < (int64_t(1) << 31), "batched search: nq out of range");
+  GBK_REQUIRE(max_k >= 1 && max_k <= GBK_MAX_K, "batched search: max_k out of [1, %d]", GBK_MAX_K);
+  GBK_REQUIRE(max_nprobe >= 1 && max_nprobe <= ix->nlist && max_nprobe <= GBK_MAX_K,
+              "batched search: max_nprobe out of range");
+  GBK_REQUIRE(npq || mlp, "batched search: give nprobe_per_q or a network");
+  GBK_REQUIRE(nq == 0 || (xq && kq && out_off && D && I), "batched search: NULL pointer");
+  return GBK_OK;
+}
+
+gbk_status gbk_ivfpq_search_batched(gbk_index* ix, const float* xq, int64_t nq,
+                                    const int32_t* k_per_q, int32_t max_k,
+                                    const int32_t* nprobe_per_q, int32_t max_nprobe,
+                                    gbk_mlp* mlp, const int64_t* out_offsets, float* D,
+                                    int64_t* I, int32_t* nprobe_used, void* stream) {
+  clear_error();
+  gbk_status r = batched_check(ix, xq, nq, k_per_q, max_k, nprobe_per_q, max_nprobe, mlp,
+                               out_offsets, D, I);
+  if (r != GBK_OK || nq == 0) return r;
+  cudaStream_t st = as_stream(stream);
+  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  return batched_run(ix, xq, nq, k_per_q, max_k, nprobe_per_q, max_nprobe, mlp, out_offsets, D, I,
+                     nprobe_used, st);
+}
+
+gbk_status gbk_ivfpq_batched_graph(gbk_index* ix, const float* xq, int64_t nq,
+                                   const int32_t* k_per_q, int32_t max_k,
+                                   const int32_t* nprobe_per_q, int32_t max_nprobe, gbk_mlp* mlp,
+                                   const int64_t* out_offsets, float* D, int64_t* I,
+                                   int32_t* nprobe_used, gbk_graph** out, void* stream) {
+  clear_error();
+  GBK_REQUIRE(out, "gbk_ivfpq_batched_graph: out is NULL");
+  gbk_status r = batched_check(ix, xq, nq, k_per_q, max_k, nprobe_per_q, max_nprobe, mlp,
+                               out_offsets, D, I);
+  if (r != GBK_OK) return r;
+  GBK_REQUIRE(nq > 0, "gbk_ivfpq_batched_graph: empty batch");
+  cudaStream_t st = as_stream(stream);
+  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  if (!device_status()) return set_error(GBK_ECUDA, "device status word unavailable");
+  GBK_CUDA_CHECK(cudaStreamSynchronize(st));
+  cudaStream_t cs;
+  GBK_CUDA_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  gbk_graph* g = new gbk_graph();
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    r = batched_run(ix, xq, nq, k_per_q, max_k, nprobe_per_q, max_nprobe, mlp, out_offsets, D, I,
+                    nprobe_used, cs);
+    e = cudaStreamEndCapture(cs, &g->graph);
+  }
+  if (e == cudaSuccess && r == GBK_OK) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  cudaStreamDestroy(cs);
+  if (r != GBK_OK || e != cudaSuccess) {
+    delete g;
+    cudaGetLastError();
+    return r != GBK_OK ? r : set_error(GBK_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  }
+  *out = g;
+  return GBK_OK;
+}
+
+gbk_status gbk_graph_launch(gbk_graph* g, void* stream) {
+  clear_error();
+  GBK_REQUIRE(g && g->exec, "gbk_graph_launch: NULL graph");
+  GBK_CUDA_CHECK(cudaGraphLaunch(g->exec, as_stream(stream)));
+  return GBK_OK;
+}
+
+void gbk_graph_destroy(gbk_graph* g) { delete g; }
+
+gbk_status gbk_recall_counts(const int64_t* I, const int64_t* G, int64_t nq, int32_t k, int32_t kg,
+                             int32_t* counts, void* stream) {
+  clear_error();
+  GBK_REQUIRE(nq >= 0 && k >= 1 && kg >= 1, "gbk_recall_counts: bad sizes");
+  if (nq == 0) return GBK_OK;
+  GBK_REQUIRE(I && G && counts, "gbk_recall_counts: NULL pointer");
+  recall_counts_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, as_stream(stream)>>>(I, G, nq, k, kg,
+                                                                                   counts);
+  GBK_LAUNCH_CHECK();
+  return GBK_OK;
+}
+
+gbk_status gbk_nprobe_features(const float* xq, int64_t nq, int32_t d, const float* coarse_dist,
+                               int32_t tau, int32_t nfeat, float* F, void* stream) {
+  clear_error();
+  GBK_REQUIRE(nq >= 0 && d >= 1 && nfeat >= 1 && tau >= nfeat, "gbk_nprobe_features: bad sizes");
+  if (nq == 0) return GBK_OK;
+  GBK_REQUIRE(xq && coarse_dist && F, "gbk_nprobe_features: NULL pointer");
+  nprobe_features_kernel<<<(unsigned)nq, 128, 0, as_stream(stream)>>>(xq, nq, d, coarse_dist, tau,
+                                                                      nfeat, F);
+  GBK_LAUNCH_CHECK();
   return GBK_OK;
 }
 

@@ -170,6 +170,14 @@ struct ScanArgs {
   const int64_t* ids;
   float* D;
   int64_t* I;
+  // mixed batches (all optional): per-query k and nprobe (<= k, nprobe above), output
+  // offsets (results of query q at D/I + out_off[q]); persistent mode takes queries from
+  // `order` (longest first) through the atomic `counter`.
+  const int32_t* kq;
+  const int32_t* npq;
+  const int64_t* out_off;
+  const int64_t* order;
+  unsigned long long* counter;
 };
 
 // Block per query: for each probed list, build the LUT, stream the codes (one 16-byte code
@@ -184,83 +192,100 @@ __global__ void __launch_bounds__(256)
   float* lut = reinterpret_cast<float*>(smem_raw);                  // [256][32]
   float* t3s = lut + 256 * 32;                                       // [M][256]
   typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(t3s + M * 256);
-  const int64_t q = blockIdx.x;
+  __shared__ int64_t q_sh;
   const int tid = threadIdx.x, lane = tid & 31;
   const int rot = lane % M, h = lane / M;
-  if (!a.direct)
-    for (int e = tid; e < M * 256; e += THREADS) t3s[e] = a.t3[q * M * 256 + e];
-  Sel::init(s);
-  __syncthreads();
-  ValueFilter f;
-  f.set(NAN_KEY, false);
-  for (int p = 0; p < a.nprobe; p++) {
-    const int64_t L = a.cl_I[q * a.nprobe + p];
-    if (L < 0) continue;  // uniform across the block
-    const float term2 = a.cl_D[q * a.nprobe + p];
-    __syncthreads();  // previous list's look-ups are done
-    if (!a.direct) {
-      const float* TL = a.T + L * M * 256;
-      for (int e = tid; e < M * 256; e += THREADS) {
-        const int m = e >> 8, c = e & 255;
-        const float v = fmaf(-2.f, t3s[e], __ldg(TL + e));
-#pragma unroll
-        for (int hh = 0; hh < 32 / M; hh++) lut[c * 32 + hh * M + m] = v;
-      }
-    } else {
-      const int dsub = a.d / M;
-      for (int e = tid; e < M * 256; e += THREADS) {
-        const int m = e >> 8, c = e & 255;
-        const float* C = a.pq + ((int64_t)m * 256 + c) * dsub;
-        float v = 0.f;
-        for (int t = 0; t < dsub; t++) {
-          const float r = a.xq[q * a.d + m * dsub + t] - a.coarse[L * a.d + m * dsub + t];
-          const float e2 = r - C[t];
-          v = fmaf(e2, e2, v);
-        }
-#pragma unroll
-        for (int hh = 0; hh < 32 / M; hh++) lut[c * 32 + hh * M + m] = v;
-      }
-    }
-    __syncthreads();
-    const int64_t o0 = a.list_off[L], o1 = a.list_off[L + 1];
-    const float base = a.direct ? 0.f : term2;
-    for (int64_t b0 = o0; b0 < o1; b0 += THREADS) {
-      const int64_t i = b0 + tid;
-      float dist = 0.f;
-      bool valid = i < o1;
-      if (valid) {
-        uint32_t w[M / 4];
-        load_code<M>(a.codes, i, w);
-        rotate_code<M>(w, rot);
-        float acc = 0.f;
-#pragma unroll
-        for (int st = 0; st < M; st++) {
-          const uint32_t c = (w[st >> 2] >> ((st & 3) * 8)) & 255u;
-          const int m = (st + rot) & (M - 1);
-          acc += lut[c * 32 + h * M + m];
-        }
-        dist = base + acc;
-      }
-      const bool pass = valid && f.pass(dist);
-      uint64_t cc[1];
-      if (pass) cc[0] = composite(ordered_key(dist, false), (uint32_t)i);
-      Sel::template push<1>(s, pass ? 1u : 0u, cc);
+  for (int64_t it = blockIdx.x;; it += gridDim.x) {
+    // next query: static (one block per query) or from the persistent work queue
+    if (a.counter) {
       __syncthreads();
-      if (s.n_buf > CAP - THREADS) {
-        Sel::compact(s, a.k);
-        f.set((uint32_t)(s.thr >> 32), false);
+      if (tid == 0) {
+        const unsigned long long w = atomicAdd(a.counter, 1ull);
+        q_sh = w < (unsigned long long)a.nq ? a.order[w] : -1;
+      }
+      __syncthreads();
+    }
+    const int64_t q = a.counter ? q_sh : (it < a.nq ? it : -1);
+    if (q < 0) break;
+    const int kq = a.kq ? a.kq[q] : a.k;
+    const int npq = a.npq ? min(a.npq[q], a.nprobe) : a.nprobe;
+    const int64_t ob = a.out_off ? a.out_off[q] : q * (int64_t)a.k;
+    __syncthreads();
+    if (!a.direct)
+      for (int e = tid; e < M * 256; e += THREADS) t3s[e] = a.t3[q * M * 256 + e];
+    Sel::init(s);
+    __syncthreads();
+    ValueFilter f;
+    f.set(NAN_KEY, false);
+    for (int p = 0; p < npq; p++) {
+      const int64_t L = a.cl_I[q * a.nprobe + p];
+      if (L < 0) continue;  // uniform across the block
+      const float term2 = a.cl_D[q * a.nprobe + p];
+      __syncthreads();  // previous list's look-ups are done
+      if (!a.direct) {
+        const float* TL = a.T + L * M * 256;
+        for (int e = tid; e < M * 256; e += THREADS) {
+          const int m = e >> 8, c = e & 255;
+          const float v = fmaf(-2.f, t3s[e], __ldg(TL + e));
+#pragma unroll
+          for (int hh = 0; hh < 32 / M; hh++) lut[c * 32 + hh * M + m] = v;
+        }
+      } else {
+        const int dsub = a.d / M;
+        for (int e = tid; e < M * 256; e += THREADS) {
+          const int m = e >> 8, c = e & 255;
+          const float* C = a.pq + ((int64_t)m * 256 + c) * dsub;
+          float v = 0.f;
+          for (int t = 0; t < dsub; t++) {
+            const float r = a.xq[q * a.d + m * dsub + t] - a.coarse[L * a.d + m * dsub + t];
+            const float e2 = r - C[t];
+            v = fmaf(e2, e2, v);
+          }
+#pragma unroll
+          for (int hh = 0; hh < 32 / M; hh++) lut[c * 32 + hh * M + m] = v;
+        }
+      }
+      __syncthreads();
+      const int64_t o0 = a.list_off[L], o1 = a.list_off[L + 1];
+      const float base = a.direct ? 0.f : term2;
+      for (int64_t b0 = o0; b0 < o1; b0 += THREADS) {
+        const int64_t i = b0 + tid;
+        float dist = 0.f;
+        bool valid = i < o1;
+        if (valid) {
+          uint32_t w[M / 4];
+          load_code<M>(a.codes, i, w);
+          rotate_code<M>(w, rot);
+          float acc = 0.f;
+#pragma unroll
+          for (int st = 0; st < M; st++) {
+            const uint32_t c = (w[st >> 2] >> ((st & 3) * 8)) & 255u;
+            const int m = (st + rot) & (M - 1);
+            acc += lut[c * 32 + h * M + m];
+          }
+          dist = base + acc;
+        }
+        const bool pass = valid && f.pass(dist);
+        uint64_t cc[1];
+        if (pass) cc[0] = composite(ordered_key(dist, false), (uint32_t)i);
+        Sel::template push<1>(s, pass ? 1u : 0u, cc);
+        __syncthreads();
+        if (s.n_buf > CAP - THREADS) {
+          Sel::compact(s, kq);
+          f.set((uint32_t)(s.thr >> 32), false);
+        }
       }
     }
-  }
-  Sel::finish(s, a.k);
-  for (int j = tid; j < a.k; j += THREADS) {
-    const uint64_t e = s.top[j];
-    if (e == ~0ull) {
-      a.D[q * a.k + j] = __int_as_float(0x7f800000);
-      a.I[q * a.k + j] = -1;
-    } else {
-      a.D[q * a.k + j] = key_value((uint32_t)(e >> 32), false);
-      a.I[q * a.k + j] = a.ids[(uint32_t)e];
+    Sel::finish(s, kq);
+    for (int j = tid; j < kq; j += THREADS) {
+      const uint64_t e = s.top[j];
+      if (e == ~0ull) {
+        a.D[ob + j] = __int_as_float(0x7f800000);
+        a.I[ob + j] = -1;
+      } else {
+        a.D[ob + j] = key_value((uint32_t)(e >> 32), false);
+        a.I[ob + j] = a.ids[(uint32_t)e];
+      }
     }
   }
 }
@@ -276,13 +301,14 @@ static gbk_status launch_scan(const ScanArgs& a, cudaStream_t st) {
                                         (int)smem));
     attr = true;
   }
-  kern<<<(unsigned)a.nq, 256, smem, st>>>(a);
+  const int64_t grid = a.counter ? std::min<int64_t>(a.nq, 2ll * device_info().sm_count) : a.nq;
+  kern<<<(unsigned)grid, 256, smem, st>>>(a);
   GBK_LAUNCH_CHECK();
   return GBK_OK;
 }
 
 template <int M>
-static gbk_status scan_k(const ScanArgs& a, cudaStream_t st) {
+static gbk_status scan_k(const ScanArgs& a, cudaStream_t st) {  // a.k = largest k
   if (a.k <= 32) return launch_scan<M, 32>(a, st);
   if (a.k <= 128) return launch_scan<M, 128>(a, st);
   if (a.k <= 256) return launch_scan<M, 256>(a, st);
@@ -293,15 +319,40 @@ gbk_status ivf_scan_run(int M, int64_t nq, int nprobe, int k, const int64_t* cl_
                         const float* cl_D, const float* T, const float* t3, const float* xq,
                         const float* coarse, const float* pq, int d, bool direct,
                         const int64_t* list_off, const uint8_t* codes, const int64_t* ids,
-                        float* D, int64_t* I, cudaStream_t st) {
+                        float* D, int64_t* I, cudaStream_t st, const int32_t* kq,
+                        const int32_t* npq, const int64_t* out_off, const int64_t* order,
+                        unsigned long long* counter) {
   if (nq == 0) return GBK_OK;
   ScanArgs a{nq, nprobe, k, cl_I, cl_D, T, t3, xq, coarse, pq, d, direct ? 1 : 0, list_off,
-             codes, ids, D, I};
+             codes, ids, D, I, kq, npq, out_off, order, counter};
   ProfScope prof("ivf_scan", st);
   if (M == 8) return scan_k<8>(a, st);
   if (M == 16) return scan_k<16>(a, st);
   if (M == 32) return scan_k<32>(a, st);
   return set_error(GBK_EUNSUPPORTED, "IVFPQ scan supports M in {8, 16, 32}");
+}
+
+// Work of each query (codes scanned) for longest-first scheduling: key = 31 - log2(work)
+// so that a stable bucketing by key lists the heaviest queries first.
+__global__ void scan_cost_kernel(const int64_t* __restrict__ cl_I, int64_t nq, int nprobe,
+                                 const int32_t* __restrict__ npq, const int64_t* __restrict__ off,
+                                 int32_t* __restrict__ key) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const int np = npq ? min(npq[q], nprobe) : nprobe;
+  long long w = 1;
+  for (int p = 0; p < np; p++) {
+    const int64_t L = cl_I[q * nprobe + p];
+    if (L >= 0) w += off[L + 1] - off[L] + 64;
+  }
+  key[q] = 63 - __clzll(w) > 31 ? 0 : 31 - (63 - __clzll(w));
+}
+
+gbk_status scan_cost_run(const int64_t* cl_I, int64_t nq, int nprobe, const int32_t* npq,
+                         const int64_t* off, int32_t* key, cudaStream_t st) {
+  scan_cost_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(cl_I, nq, nprobe, npq, off, key);
+  GBK_LAUNCH_CHECK();
+  return GBK_OK;
 }
 
 gbk_status pq_encode_run(const float* x, int64_t n, int d, int M, const float* coarse,

@@ -66,7 +66,9 @@ __global__ void __launch_bounds__(1024)
     for (int j = 0; j < (int)blockDim.x && base + j < nc; j++) {
       if (tid == 0) e_cur = counts[base + j] == 0 ? base + j : -1;
       __syncthreads();
-      if (e_cur < 0) continue;
+      const int ec = e_cur;
+      __syncthreads();  // everyone has read e_cur before thread 0 may rewrite it
+      if (ec < 0) continue;
       // argmax of counts, lowest index on ties
       long long bv = -1;
       int bi = 0x7fffffff;
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(1024)
         s_sel = ii;
       }
       __syncthreads();
-      const int s = s_sel, ec = e_cur;
+      const int s = s_sel;
       for (int t = tid; t < d; t += blockDim.x) {
         const double g = (t % 2 == 0) ? 1.0 : -1.0;
         const double cs = (double)cent[(int64_t)s * d + t];

@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(THREADS, 4)
                         uint64_t* __restrict__ part) {
   using C = KselCfg<THREADS, KP, UNROLL, LARGEST>;
   using Sel = typename C::Sel;
+  constexpr bool PIPE = (UNROLL == 4);  // 4: double-buffered loads; 8: one fat buffer
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* overflow = reinterpret_cast<int*>(smem_raw);
   int* n_ok = overflow + 1;
@@ -82,17 +83,65 @@ __global__ void __launch_bounds__(THREADS, 4)
   if (tid == 0) *n_ok = s.n_buf;
   const float4* p4 = reinterpret_cast<const float4*>(p + head);
   const uint32_t idx0 = (uint32_t)(s0 + head);
+  // PIPE: the next iteration's loads are issued before this one is filtered, so the
+  // block's capacity barrier never leaves the SM without loads in flight.
+  float4 nxt[PIPE ? UNROLL : 1];
+  if (PIPE) {
+#pragma unroll
+    for (int u = 0; u < UNROLL; u++) {
+      const int64_t i = (int64_t)u * THREADS + tid;
+      nxt[u] = i < n4 ? __ldcs(p4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
   for (int64_t base = 0; base < n4; base += (int64_t)THREADS * UNROLL) {
     float v[C::PT];
 #pragma unroll
     for (int u = 0; u < UNROLL; u++) {
       const int64_t i = base + u * THREADS + tid;
       float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (i < n4) x = __ldcs(p4 + i);
+      if (PIPE) {
+        x = nxt[u];
+        const int64_t inext = i + (int64_t)THREADS * UNROLL;
+        if (inext < n4) nxt[u] = __ldcs(p4 + inext);
+      } else if (i < n4) {
+        x = __ldcs(p4 + i);
+      }
       v[u * 4 + 0] = x.x;
       v[u * 4 + 1] = x.y;
       v[u * 4 + 2] = x.z;
       v[u * 4 + 3] = x.w;
+    }
+    uint32_t skip = 0u;  // slot already offered as this thread's minimum
+    if (base == 0 && k <= THREADS) {
+      // Seed the threshold: every thread offers the smallest of its first values; the
+      // k-th smallest of these distinct elements bounds the row's k-th from above and is
+      // about as tight as the k-th of the whole first iteration, at 1/PT of the work.
+      uint64_t mn = ~0ull;
+      int ms = -1;
+#pragma unroll
+      for (int u = 0; u < UNROLL; u++) {
+        if (u * THREADS + tid < n4) {
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            const uint64_t c = composite(ordered_key(v[u * 4 + j], LARGEST),
+                                         idx0 + (uint32_t)((u * THREADS + tid) * 4 + j));
+            if (c < mn) {
+              mn = c;
+              ms = u * 4 + j;
+            }
+          }
+        }
+      }
+      uint64_t cm[1] = {mn};
+      Sel::template push<1>(s, ms >= 0 ? 1u : 0u, cm);
+      if (ms >= 0) skip = 1u << ms;
+      __syncthreads();
+      if (s.n_top + s.n_buf > k) {
+        Sel::compact(s, k);
+        f.set((uint32_t)(s.thr >> 32), LARGEST);
+      }
+      if (tid == 0) *n_ok = s.n_buf;
+      __syncthreads();
     }
     bool pending = true;
     for (;;) {
@@ -105,6 +154,7 @@ __global__ void __launch_bounds__(THREADS, 4)
             for (int j = 0; j < 4; j++) mask |= (f.pass(v[u * 4 + j]) ? 1u : 0u) << (u * 4 + j);
           }
         }
+        mask &= ~skip;
       }
       bool retry = false;
       if (__any_sync(FULL_MASK, mask != 0u)) {

@@ -165,11 +165,19 @@ struct BlockSelect {
     int shift = 64 - __clzll((long long)s.diff);  // distinct composites -> diff != 0
     uint64_t P = shr64(x0, shift);
     int need = k;
-    // 2. MSB-first radix select of the need-th smallest composite
+    // 2. MSB-first radix select of the need-th smallest composite.  Digits never straddle
+    //    the 32-bit word boundary, so every test below is a 32-bit operation.
     for (;;) {
-      const int w = shift < 8 ? shift : 8;
+      const int w = shift > 32 ? min(8, shift - 32) : min(8, shift);
       const int nshift = shift - w;
       const uint32_t dmask = (1u << w) - 1u;
+      // prefix test (e >> shift) == P split into words
+      const bool hi_only = shift >= 32;
+      const uint32_t ph = hi_only ? (uint32_t)P : (uint32_t)(P >> (32 - shift));
+      const int sh_h = hi_only ? shift - 32 : 0;
+      const uint32_t pl = hi_only ? 0u : (shift == 32 ? 0u : (uint32_t)P & (uint32_t)((1ull << (32 - shift)) - 1ull));
+      const bool dig_hi = nshift >= 32;
+      const int dsh = dig_hi ? nshift - 32 : nshift;
       for (int i = tid; i < 256; i += THREADS) s.hist[i] = 0u;
       __syncthreads();
       // warp-aggregated: one shared atomic per distinct digit per warp (the digits of
@@ -178,8 +186,11 @@ struct BlockSelect {
         const int i = i0 + tid;
         uint32_t bin = 0xffffffffu;
         if (i < total) {
-          uint64_t e = i < n_top ? s.top[i] : s.buf[i - n_top];
-          if (shr64(e, shift) == P) bin = (uint32_t)(e >> nshift) & dmask;
+          const uint64_t e = i < n_top ? s.top[i] : s.buf[i - n_top];
+          const uint32_t eh = (uint32_t)(e >> 32), el = (uint32_t)e;
+          const bool match = hi_only ? (sh_h >= 32 ? true : (eh >> sh_h) == ph)
+                                     : (eh == ph && (shift == 32 ? true : (el >> shift) == pl));
+          if (match) bin = ((dig_hi ? eh : el) >> dsh) & dmask;
         }
         const unsigned grp = __match_any_sync(FULL_MASK, bin);
         if (bin != 0xffffffffu && lane == __ffs(grp) - 1) atomicAdd(&s.hist[bin], (uint32_t)__popc(grp));
@@ -237,11 +248,13 @@ struct BlockSelect {
       s.tmax = 0ull;
     }
     __syncthreads();
+    // (e >> shift) <= P  <=>  e <= (P << shift) | (2^shift - 1)
+    const uint64_t lim = shift >= 64 ? ~0ull : ((P << shift) | ((1ull << shift) - 1ull));
     uint64_t m = 0ull;
 #pragma unroll
     for (int j = 0; j < TPT; j++) {
       const int i = tid + j * THREADS;
-      const bool keep = i < n_top && shr64(mine[j], shift) <= P;
+      const bool keep = i < n_top && mine[j] <= lim;
       const int pos = warp_reserve(s.cnt, keep);
       if (keep) {
         s.top[pos] = mine[j];
@@ -251,7 +264,7 @@ struct BlockSelect {
     for (int i0 = 0; i0 < n_buf; i0 += THREADS) {
       const int i = i0 + tid;
       uint64_t e = i < n_buf ? s.buf[i] : ~0ull;
-      const bool keep = i < n_buf && shr64(e, shift) <= P;
+      const bool keep = i < n_buf && e <= lim;
       const int pos = warp_reserve(s.cnt, keep);
       if (keep) {
         s.top[pos] = e;

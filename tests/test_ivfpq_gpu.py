@@ -33,20 +33,27 @@ def test_kmeans_matches_oracle(gbk, d, nc, direct):
     np.testing.assert_allclose(obj, objo, rtol=1e-4)
 
 
-def test_kmeans_empty_cluster_rule_matches_oracle(gbk):
-    x, _ = _mixture(20, 3000, 16, ncent=10, std=8.0)
-    init = np.array([0, 0, 0, 5, 9, 9, 100, 101, 102, 103])  # duplicates: empty clusters
-    c, _, ns = gbk.kmeans(torch.from_numpy(x).cuda(), init, 3, direct=True)
-    co, _, nso = oracle.kmeans(x, init, 3)
-    assert ns == nso and ns > 0
+@pytest.mark.parametrize("direct", [True, False])
+def test_kmeans_empty_cluster_rule_matches_oracle(gbk, direct):
+    # Duplicate initial rows tie exactly, so the lowest centroid takes every point and the
+    # others are re-seeded by the split rule.  One iteration: the split is exact float64
+    # arithmetic on both sides (later iterations would meet genuine near-ties, since a
+    # split leaves two centroids 2/1024 apart).
+    d = 16 if direct else 64
+    x, _ = _mixture(20, 3000, d, ncent=10, std=8.0)
+    init = np.array([0, 0, 0, 5, 9, 9, 100, 101, 102, 103])
+    c, _, ns = gbk.kmeans(torch.from_numpy(x).cuda(), init, 1, direct=direct)
+    co, _, nso = oracle.kmeans(x, init, 1)
+    assert ns == nso == 3
     np.testing.assert_allclose(c.cpu().numpy(), co, rtol=1e-6, atol=1e-6)
 
 
 def _index_with_oracle_quantizers(gbk, seed, n=20000, d=32, nlist=16, M=8, precomputed=True):
     x, cen = _mixture(seed, n, d)
-    coarse, _, _ = oracle.kmeans(x[:4000], datagen.permutation_prefix(seed + 2, 4000, nlist), 6)
-    res = oracle.residual_training_set(x[:4000], coarse)
-    books = oracle.train_pq(res, M, datagen.permutation_prefix(seed + 3, 4000, 256), 6)
+    nt = min(4000, n)
+    coarse, _, _ = oracle.kmeans(x[:nt], datagen.permutation_prefix(seed + 2, nt, nlist), 6)
+    res = oracle.residual_training_set(x[:nt], coarse)
+    books = oracle.train_pq(res, M, datagen.permutation_prefix(seed + 3, nt, 256), 6)
     ix = gbk.IVFPQIndex(d, nlist, M)
     ix.set_quantizers(torch.from_numpy(coarse).cuda(), torch.from_numpy(books).cuda(),
                       use_precomputed=precomputed)
