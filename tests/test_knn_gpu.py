@@ -137,7 +137,8 @@ def test_low_precision_rerank_certified_queries_are_exact(gbk, prec, metric):
     if prec == "bf16":
         assert cert.mean() > 0.5, cert.mean()
     np.testing.assert_allclose(D[cert], Do[cert], rtol=1e-5, atol=1e-4)
-    assert (I[cert] == Io[cert]).mean() > 0.999
+    if cert.any():
+        assert (I[cert] == Io[cert]).mean() > 0.999
     assert np.all(eb.cpu().numpy() > 0)
 
 
