@@ -106,6 +106,28 @@ gbk_status gbk_kselect_ex(const float* vals, int64_t rows, int64_t len, int32_t 
                           void* stream);
 
 /*
+ * gbk_kselect for callers that cannot allocate device memory during the call (for
+ * example code being captured into a CUDA graph on a pool it does not own, latency-bound
+ * paths that forbid allocator calls after start-up, or hosts whose only allocator is
+ * their own).  The paper has no counterpart: this is a deployment variant of the
+ * row-split (two-pass) selection of gbk_kselect_ex.
+ *   Same arguments and results as gbk_kselect_ex with opts.segments = segments (0 = the
+ *   library's plan).  When the plan splits rows (segments > 1) the per-segment partial
+ *   results live in a fixed device array of 2^21 entries (16 MiB) that is part of the
+ *   library image, held on every GPU that loads the library until the process exits:
+ *   rows * segments * k must not exceed 2^21, else GBK_EINVAL and nothing is launched.
+ *   No cudaMalloc/cudaFree or other allocating call is made.
+ *   The first call on a device looks up the array's device address (once per device, with
+ *   that device current); make that first call before any stream capture.
+ *   Every call shares the array and it keeps the last call's contents (each call writes
+ *   all the partials it reads, so nothing needs clearing); calls whose executions overlap
+ *   on the GPU race on it and must be serialised by the caller.
+ */
+gbk_status gbk_kselect_static(const float* vals, int64_t rows, int64_t len, int32_t k,
+                              int32_t largest, int32_t segments, float* D, int64_t* I,
+                              void* stream);
+
+/*
  * Squared L2 norms of the rows of x (the precomputable terms of Eq. (2), section 2).
  *   x [n][d] float32 in, out [n] float32 out.  Errors: GBK_EINVAL, GBK_ECUDA.
  */

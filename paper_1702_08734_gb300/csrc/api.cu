@@ -282,6 +282,21 @@ gbk_status gbk_kmeans(const float* x, int64_t n, int32_t d, int32_t nc, int32_t 
   return r;
 }
 
+gbk_status gbk_kselect_static(const float* vals, int64_t rows, int64_t len, int32_t k,
+                              int32_t largest, int32_t segments, float* D, int64_t* I,
+                              void* stream) {
+  clear_error();
+  GBK_REQUIRE(rows >= 0, "gbk_kselect_static: rows < 0");
+  if (rows == 0) return GBK_OK;
+  GBK_REQUIRE(len >= 1 && len < (int64_t(1) << 31), "gbk_kselect_static: len out of [1, 2^31)");
+  GBK_REQUIRE(k >= 1 && k <= GBK_MAX_K && k <= len, "gbk_kselect_static: k=%d out of [1, min(len, %d)]",
+              k, GBK_MAX_K);
+  GBK_REQUIRE(vals && D && I, "gbk_kselect_static: NULL pointer");
+  GBK_REQUIRE(largest == 0 || largest == 1, "gbk_kselect_static: largest must be 0 or 1");
+  GBK_REQUIRE(segments >= 0, "gbk_kselect_static: segments < 0");
+  return kselect_static_run(vals, rows, len, k, largest != 0, segments, D, I, as_stream(stream));
+}
+
 gbk_status gbk_row_norms(const float* x, int64_t n, int32_t d, float* out, void* stream) {
   clear_error();
   GBK_REQUIRE(n >= 0 && d >= 1, "gbk_row_norms: bad sizes n=%lld d=%d", (long long)n, d);

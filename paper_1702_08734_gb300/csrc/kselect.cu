@@ -9,6 +9,7 @@
 // paper's two-pass k-selection (section 5.3, "Multi-pass kernels").  k = 1 is a plain
 // argmin/argmax reduction (section 6.2 notes that k = 1 needs no selection structure).
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "kselect.cuh"
@@ -417,20 +418,21 @@ KselectTuning kselect_default_tuning(int64_t rows, int64_t len, int k) {
   return t;
 }
 
-gbk_status kselect_run(const float* vals, int64_t rows, int64_t len, int k, bool largest,
-                       float* D, int64_t* I, cudaStream_t st, const KselectTuning* tuning) {
-  if (rows == 0) return GBK_OK;
-  KselectTuning tu = tuning ? *tuning : kselect_default_tuning(rows, len, k);
-  int64_t segs = std::max(1, tu.segs);
+namespace {
+
+// Segment length (a multiple of 4 floats) and the resulting segment count for a request.
+void plan_segments(int64_t len, int want, int64_t* segs_out, int64_t* seg_len_out) {
+  int64_t segs = std::max(1, want);
   int64_t seg_len = (len + segs - 1) / segs;
   seg_len = (seg_len + 3) & ~int64_t(3);
-  segs = (len + seg_len - 1) / seg_len;
-  Scratch part;
-  if (segs > 1) {
-    gbk_status r = part.alloc(sizeof(uint64_t) * (size_t)(rows * segs * k), st);
-    if (r != GBK_OK) return r;
-  }
-  uint64_t* pp = part.as<uint64_t>();
+  *seg_len_out = seg_len;
+  *segs_out = (len + seg_len - 1) / seg_len;
+}
+
+// Launches for a plan; `part` must hold rows * segs * k composites when segs > 1.
+gbk_status kselect_launch(const float* vals, int64_t rows, int64_t len, int k, bool largest,
+                          float* D, int64_t* I, cudaStream_t st, const KselectTuning& tu,
+                          int64_t segs, int64_t seg_len, uint64_t* pp) {
   gbk_status r;
   ProfScope prof(k == 1 ? "kselect_k1" : "kselect_rows", st);
   if (k == 1) {
@@ -449,6 +451,82 @@ gbk_status kselect_run(const float* vals, int64_t rows, int64_t len, int k, bool
   if (r != GBK_OK || segs == 1) return r;
   const int64_t nper = segs * (k == 1 ? 1 : k);
   return dispatch_merge(pp, rows, nper, k, vals, len, D, I, st);
+}
+
+}  // namespace
+
+gbk_status kselect_run(const float* vals, int64_t rows, int64_t len, int k, bool largest,
+                       float* D, int64_t* I, cudaStream_t st, const KselectTuning* tuning) {
+  if (rows == 0) return GBK_OK;
+  KselectTuning tu = tuning ? *tuning : kselect_default_tuning(rows, len, k);
+  int64_t segs, seg_len;
+  plan_segments(len, tu.segs, &segs, &seg_len);
+  Scratch part;
+  if (segs > 1) {
+    gbk_status r = part.alloc(sizeof(uint64_t) * (size_t)(rows * segs * k), st);
+    if (r != GBK_OK) return r;
+  }
+  return kselect_launch(vals, rows, len, k, largest, D, I, st, tu, segs, seg_len,
+                        part.as<uint64_t>());
+}
+
+// ------------------------------------------------------------------ no-allocation variant
+//
+// Some callers cannot allocate device memory at call time: code running while a CUDA graph
+// is being captured with a memory pool they do not own, real-time paths that forbid any
+// allocator call after start-up, and hosts whose only allocator is their own (a tensor
+// framework's caching allocator the library is not wired to).  For them the segmented
+// two-pass k-selection keeps its per-segment partial results in this fixed array instead
+// of scratch memory.  The array is part of the library image: every GPU that loads the
+// library holds it (16 MiB) until the process exits.  All calls share it and it keeps the
+// contents of the last call; each call fully writes the partials it then reads, so nothing
+// needs clearing, but calls whose executions overlap on the GPU (different streams, or
+// different host threads) race on it and must be serialised by the caller.
+constexpr int64_t STATIC_PART_ELEMS = (int64_t)2 << 20;  // composites (16 MiB)
+static __device__ __align__(256) uint64_t g_static_part[STATIC_PART_ELEMS];
+
+namespace {
+// Device address of g_static_part, looked up once per device with that device current
+// (in host code the symbol's name is only a host-side stand-in).
+uint64_t* static_part_address(gbk_status* st) {
+  static std::mutex mu;
+  static uint64_t* addr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    *st = set_error(GBK_ECUDA, "gbk_kselect_static: no current device");
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_part);
+    if (e != cudaSuccess) {
+      *st = set_error(GBK_ECUDA, "gbk_kselect_static: cudaGetSymbolAddress: %s",
+                      cudaGetErrorString(e));
+      return nullptr;
+    }
+    addr[dev] = static_cast<uint64_t*>(p);
+  }
+  return addr[dev];
+}
+}  // namespace
+
+gbk_status kselect_static_run(const float* vals, int64_t rows, int64_t len, int k, bool largest,
+                              int segments, float* D, int64_t* I, cudaStream_t st) {
+  if (rows == 0) return GBK_OK;
+  KselectTuning tu = kselect_default_tuning(rows, len, k);
+  if (segments > 0) tu.segs = segments;
+  int64_t segs, seg_len;
+  plan_segments(len, tu.segs, &segs, &seg_len);
+  if (segs > 1 && rows * segs * (int64_t)k > STATIC_PART_ELEMS)
+    return set_error(GBK_EINVAL,
+                     "gbk_kselect_static: rows*segments*k = %lld exceeds the fixed capacity of "
+                     "%lld partial results",
+                     (long long)(rows * segs * (int64_t)k), (long long)STATIC_PART_ELEMS);
+  gbk_status r = GBK_OK;
+  uint64_t* pp = segs > 1 ? static_part_address(&r) : nullptr;
+  if (segs > 1 && !pp) return r;
+  return kselect_launch(vals, rows, len, k, largest, D, I, st, tu, segs, seg_len, pp);
 }
 
 }  // namespace gbk

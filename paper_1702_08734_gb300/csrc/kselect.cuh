@@ -18,6 +18,10 @@ KselectTuning kselect_default_tuning(int64_t rows, int64_t len, int k);
 gbk_status kselect_run(const float* vals, int64_t rows, int64_t len, int k, bool largest,
                        float* D, int64_t* I, cudaStream_t stream, const KselectTuning* tuning);
 
+// Same selection with the segment partials in a fixed device array (no allocation).
+gbk_status kselect_static_run(const float* vals, int64_t rows, int64_t len, int k, bool largest,
+                              int segments, float* D, int64_t* I, cudaStream_t stream);
+
 gbk_status row_norms_run(const float* x, int64_t n, int d, float* out, cudaStream_t stream);
 
 }  // namespace gbk
