@@ -153,6 +153,166 @@ def cpu_baseline_oracle():
             "sample": "exact L2 k=10 for %d queries (16 per call) against the full 1M x 128 database, %.1f s" % (n, el)}
 
 
+def recall_stats(g, I, Igt, k=10):
+    """1-R@k (true nearest in the top k) and k-R@k (overlap of the top k sets)."""
+    import torch
+    nq = I.shape[0]
+    Ik = I[:, :k].contiguous()
+    cnt = torch.empty(nq, dtype=torch.int32, device=I.device)
+    g.recall_counts(Ik, Igt[:, :k].contiguous(), cnt)
+    one = torch.empty(nq, dtype=torch.int32, device=I.device)
+    g.recall_counts(Ik, Igt[:, :1].contiguous(), one)
+    return float(one.float().mean().item()), float(cnt.float().mean().item()) / k
+
+
+def build_ivfadc_index(g, datagen, n):
+    """The IVFADC workload's index: 10M x 128 Gaussian mixture (4,096 centres N(0,4I), noise
+    N(0,I)), nlist 4,096, PQ 16 x 256 trained on 256K points of the same mixture."""
+    import torch
+    d, nlist, M = 128, 4096, 16
+    t = {}
+    t0 = time.perf_counter()
+    cen = datagen.mixture_centres(301, 4096, d)
+    xt = datagen.mixture_points_cuda(cen, 303, 262144)
+    xb = datagen.mixture_points_cuda(cen, 302, n)
+    torch.cuda.synchronize()
+    t["gen_s"] = time.perf_counter() - t0
+    ix = g.IVFPQIndex(d, nlist, M)
+    t0 = time.perf_counter()
+    ix.train(xt, niter=20, coarse_init=datagen.permutation_prefix(305, 262144, nlist),
+             pq_init=datagen.permutation_prefix(306, 262144, 256))
+    torch.cuda.synchronize()
+    t["train_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ix.add(xb)
+    assert ix.ntotal == n
+    torch.cuda.synchronize()
+    t["add_s"] = time.perf_counter() - t0
+    return ix, cen, xb, t
+
+
+def time_search(g, fn, steps):
+    import torch
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, out
+
+
+def run_ivfadc(args):
+    """IVFADC workload, k = 100, nprobe in {1,4,16,64,256}, 10K queries from the mixture;
+    ground truth by exact search; reports q/s with 1-R@10 and 10-R@10."""
+    import torch
+
+    import paper_1702_08734_gb300 as g
+    from paper_1702_08734_gb300 import datagen
+    g.load()
+    nq, k = 10000, 100
+    ix, cen, xb, t = build_ivfadc_index(g, datagen, args.ivf_n)
+    xq = datagen.mixture_points_cuda(cen, 304, nq)
+    t0 = time.perf_counter()
+    _, Igt = g.knn_brute(xq, xb, k)
+    torch.cuda.synchronize()
+    t["groundtruth_s"] = time.perf_counter() - t0
+    rows = []
+    for nprobe in (1, 4, 16, 64, 256):
+        g.profile_enable(True)
+        ms, (D, I) = time_search(g, lambda: ix.search(xq, k, nprobe), args.steps)
+        g.profile_enable(False)
+        prof = g.profile_read()
+        scan = [tt for nm, tt in prof if nm == "ivf_scan"]
+        r1, r10 = recall_stats(g, I, Igt)
+        rows.append({"nprobe": nprobe, "ms": ms, "qps": nq / (ms / 1e3), "R1@10": r1,
+                     "R10@10": r10, "scan_ms": sum(scan) / max(1, len(scan))})
+    print(json.dumps({"workload": "ivfadc nb=%d d=128 nlist=4096 M=16 nq=1e4 k=100" % args.ivf_n,
+                      **t, "results": rows}), flush=True)
+
+
+def run_learned(args):
+    """Learned nprobe: labels = smallest nprobe in {1,..,256} whose 10-R@10 reaches
+    min(10/10, the query's 10-R@10 at 256), for 200K training queries; the network (query +
+    64 coarse-distance features -> 256 -> 256 -> 9 classes) is trained with the library's
+    kernels; learned routing vs fixed nprobe on the 10K evaluation queries, k = 10."""
+    import numpy as np
+    import torch
+
+    import paper_1702_08734_gb300 as g
+    from paper_1702_08734_gb300 import datagen
+    from oracle import mlp as omlp  # seeded initial weights only (uniform draws)
+    g.load()
+    ix, cen, xb, t = build_ivfadc_index(g, datagen, args.ivf_n)
+    coarse = torch.from_numpy(ix.export()["coarse"]).cuda()
+    ntr, nq, chunk = args.learn_n, 10000, 20000
+    taus = [1 << c for c in range(9)]
+    F_all, y_all = [], []
+    t0 = time.perf_counter()
+    for q0 in range(0, ntr, chunk):
+        xq = datagen.mixture_points_cuda(cen, 501, min(chunk, ntr - q0), row0=q0)
+        _, Igt = g.knn_brute(xq, xb, 10)
+        cnts = []
+        for tau in taus:
+            _, I = ix.search(xq, 10, tau)
+            c = torch.empty(xq.shape[0], dtype=torch.int32, device="cuda")
+            g.recall_counts(I, Igt, c)
+            cnts.append(c)
+        C = torch.stack(cnts, 1)                    # [q][9] overlap counts out of 10
+        target = torch.clamp(C[:, -1:], max=10)     # min(10/10, recall at 256)
+        y = torch.argmax((C >= target).to(torch.int32), dim=1).to(torch.int32)
+        clD, _ = g.knn_brute(xq, coarse, 64)
+        F_all.append(g.nprobe_features(xq, clD))
+        y_all.append(y)
+    F = torch.cat(F_all)
+    y = torch.cat(y_all)
+    t["labels_s"] = time.perf_counter() - t0
+    hist = torch.bincount(y.long(), minlength=9).cpu().tolist()
+    nparam = 256 * 192 + 256 + 256 * 256 + 256 + 9 * 256 + 9
+    p = omlp.init_params((192, 256, 256, 9), datagen.uniform24(502, 0, nparam).astype(np.float64))
+    net = g.MLP(192, 256, 256, 9,
+                params=np.concatenate([p[kk].ravel() for kk in omlp.PARAM_NAMES]).astype(np.float32))
+    t0 = time.perf_counter()
+    perm_seed = 503
+    bs = 4096
+    losses = []
+    for ep in range(args.learn_epochs):
+        perm = torch.from_numpy(np.argsort(datagen.hash_u64(perm_seed + ep, 0, F.shape[0]))).cuda()
+        for b0 in range(0, F.shape[0] - bs + 1, bs):
+            idx = perm[b0:b0 + bs]
+            l = net.train_step(F[idx].contiguous(), y[idx].contiguous(), lr=1e-3)
+        losses.append(float(l.item()))
+    torch.cuda.synchronize()
+    t["mlp_train_s"] = time.perf_counter() - t0
+    # evaluation queries
+    xq = datagen.mixture_points_cuda(cen, 304, nq)
+    _, Igt = g.knn_brute(xq, xb, 10)
+    fixed = []
+    for tau in taus:
+        ms, (D, I) = time_search(g, lambda: ix.search(xq, 10, tau), args.steps)
+        _, r10 = recall_stats(g, I, Igt)
+        fixed.append({"nprobe": tau, "qps": nq / (ms / 1e3), "R10@10": r10})
+    kq = torch.full((nq,), 10, dtype=torch.int32, device="cuda")
+    ms, (D, I, off, used) = time_search(
+        g, lambda: g.ivfpq_search_batched(ix, xq, kq, 10, None, 256, mlp=net), args.steps)
+    _, r10 = recall_stats(g, I.view(nq, 10), Igt)
+    learned = {"qps": nq / (ms / 1e3), "R10@10": r10,
+               "mean_nprobe": float(used.float().mean().item())}
+    # fixed-nprobe q/s at the learned recall (log-linear interpolation between neighbours)
+    eq = None
+    for a, b in zip(fixed, fixed[1:]):
+        if a["R10@10"] <= r10 <= b["R10@10"] and b["R10@10"] > a["R10@10"]:
+            w = (r10 - a["R10@10"]) / (b["R10@10"] - a["R10@10"])
+            eq = float(np.exp(np.log(a["qps"]) * (1 - w) + np.log(b["qps"]) * w))
+    print(json.dumps({"workload": "learned nprobe, nb=%d, %d training queries" % (args.ivf_n, ntr),
+                      **t, "label_hist": hist, "loss_per_epoch": losses, "fixed": fixed,
+                      "learned": learned, "fixed_qps_at_learned_recall": eq,
+                      "speedup_at_equal_recall": learned["qps"] / eq if eq else None}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -160,7 +320,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="exact", choices=["exact", "ivfadc", "learned"])
+    ap.add_argument("--ivf-n", type=int, default=10000000)
+    ap.add_argument("--learn-n", type=int, default=200000)
+    ap.add_argument("--learn-epochs", type=int, default=15)
     args = ap.parse_args()
+    if args.workload == "ivfadc" and args.impl == "ours":
+        run_ivfadc(args)
+        return
+    if args.workload == "learned" and args.impl == "ours":
+        run_learned(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

@@ -136,7 +136,7 @@ gbk_status gbk_row_norms(const float* x, int64_t n, int32_t d, float* out, void*
 /* Options of gbk_knn_brute (NULL = defaults). */
 typedef struct gbk_knn_opts {
   int32_t precision; /* GBK_PREC_FP32 (default), GBK_PREC_BF16 or GBK_PREC_FP8          */
-  int32_t kprime;    /* BF16/FP8: candidates re-ranked in float32 (0 = 4k, >= k, <= 1024) */
+  int32_t kprime;    /* BF16/FP8: candidates re-ranked in float32 (0 = min(4k, max(2k, 64)), >= k, <= 1024) */
   int32_t chunks;    /* database chunks of the work decomposition (0 = planned)          */
   int32_t* certified; /* BF16/FP8, optional device [nq]: 1 if the result provably equals
                          the float32 top-k (see gbk_knn_brute), else 0                  */
@@ -156,7 +156,7 @@ typedef struct gbk_knn_opts {
  * keep the best k.  A query is certified when the k'-th low-precision distance minus
  * the error bound exceeds the k-th re-ranked distance (plus, for inner product), which
  * proves no other database row belongs to the top k.
- * Limits: nb, nq < 2^31; d <= 128 for k <= 256 (larger k tiles the distance matrix over
+ * Limits: nb, nq < 2^31; d <= 128 for k <= 512 (larger k tiles the distance matrix over
  * queries and allows d <= 160).  Errors: GBK_EINVAL, GBK_EUNSUPPORTED (d too large),
  * GBK_ENOMEM, GBK_ECUDA.  Inputs must be finite.
  */
@@ -282,6 +282,58 @@ gbk_status gbk_mlp_forward(gbk_mlp* net, const float* X, int64_t B, float* logit
  * optional device float receiving the batch loss. */
 gbk_status gbk_mlp_train_step(gbk_mlp* net, const float* X, const int32_t* labels, int64_t B,
                               float lr, int32_t update, float* loss, void* stream);
+
+/* ------------------------------------------------------------------ batched serving */
+
+/* A mixed batch in one call: query q asks for its own k_per_q[q] (1..max_k) neighbours from
+ * its own nprobe_per_q[q] (1..max_nprobe) lists; otherwise the same search as
+ * gbk_ivfpq_search (Algorithm 4, Eq. 5-6, 10-11), and query q's results equal those of a
+ * plain search with that k and nprobe.  One coarse k-NN for max_nprobe serves every query
+ * (the lists of a smaller nprobe are a prefix).  The scan is one persistent launch that
+ * takes queries longest-first from an atomic counter, so uneven lists and mixed nprobe
+ * keep every SM busy.  All arrays are device memory:
+ *   k_per_q [nq] int32; nprobe_per_q [nq] int32, or NULL to have `mlp` choose it;
+ *   out_offsets [nq+1] int64 prefix sums of k_per_q (results of q at
+ *   [out_offsets[q], out_offsets[q+1]) of D float32 / I int64);
+ *   nprobe_used [nq] int32 (may be NULL): the nprobe each query was searched with.
+ * mlp (NULL unless nprobe_per_q is NULL): a network with d + 64 inputs whose class c gives
+ * nprobe 2^c (capped at max_nprobe); its features are the query and its 64 smallest coarse
+ * distances relative to the smallest (gbk_nprobe_features).  Needs nlist >= 64.  Learned
+ * nprobe is not part of the paper.  GBK_EINVAL on bad sizes or a NULL pointer. */
+gbk_status gbk_ivfpq_search_batched(gbk_index* index, const float* xq, int64_t nq,
+                                    const int32_t* k_per_q, int32_t max_k,
+                                    const int32_t* nprobe_per_q, int32_t max_nprobe,
+                                    gbk_mlp* mlp, const int64_t* out_offsets, float* D,
+                                    int64_t* I, int32_t* nprobe_used, void* stream);
+
+/* The launches of gbk_ivfpq_search_batched captured once into a CUDA graph on a private
+ * stream (the index must not change afterwards; `stream` is synchronised before capture).
+ * The graph reads the buffers given here on every replay: refill xq (and k_per_q,
+ * nprobe_per_q, out_offsets) in place and call gbk_graph_launch.  Temporary buffers of
+ * the capture stay owned by the graph.  nq > 0.  *out receives the graph; free it with
+ * gbk_graph_destroy.  Not part of the paper: serving machinery. */
+typedef struct gbk_graph gbk_graph;
+gbk_status gbk_ivfpq_batched_graph(gbk_index* index, const float* xq, int64_t nq,
+                                   const int32_t* k_per_q, int32_t max_k,
+                                   const int32_t* nprobe_per_q, int32_t max_nprobe,
+                                   gbk_mlp* mlp, const int64_t* out_offsets, float* D,
+                                   int64_t* I, int32_t* nprobe_used, gbk_graph** out,
+                                   void* stream);
+gbk_status gbk_graph_launch(gbk_graph* graph, void* stream);
+void gbk_graph_destroy(gbk_graph* graph);
+
+/* R@k counting (the evaluation measure of section 6): counts[q] = how many of the k ids
+ * I [nq][k] (entries < 0 ignored) appear among the kg ground-truth ids G [nq][kg].  Device
+ * arrays. */
+gbk_status gbk_recall_counts(const int64_t* I, const int64_t* G, int64_t nq, int32_t k,
+                             int32_t kg, int32_t* counts, void* stream);
+
+/* Features of the learned-nprobe network: F [nq][d + nfeat] = the query xq [nq][d], then
+ * coarse_dist[q][j] / max(coarse_dist[q][0], 1e-12) - 1 for j < nfeat, where coarse_dist
+ * [nq][tau] holds each query's ascending squared distances to its tau >= nfeat nearest
+ * coarse centroids.  Device arrays.  Not part of the paper. */
+gbk_status gbk_nprobe_features(const float* xq, int64_t nq, int32_t d, const float* coarse_dist,
+                               int32_t tau, int32_t nfeat, float* F, void* stream);
 
 #ifdef __cplusplus
 }

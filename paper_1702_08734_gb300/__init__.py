@@ -394,3 +394,83 @@ class MLP:
         _call("gbk_mlp_train_step", self._h, _ptr(X), _ptr(labels), X.shape[0], float(lr),
               int(bool(update)), _ptr(loss), _stream())
         return loss
+
+
+_SIGNATURES.update({
+    "gbk_recall_counts": [_vp, _vp, _i64, _i32, _i32, _vp, _vp],
+    "gbk_nprobe_features": [_vp, _i64, _i32, _vp, _i32, _i32, _vp, _vp],
+    "gbk_ivfpq_search_batched": [_vp, _vp, _i64, _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp,
+                                 _vp],
+    "gbk_ivfpq_batched_graph": [_vp, _vp, _i64, _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp,
+                                _vp, _vp],
+    "gbk_graph_launch": [_vp, _vp],
+})
+
+
+def recall_counts(I: torch.Tensor, G: torch.Tensor, out: torch.Tensor):
+    """out[q] = |{I[q][i]} intersect {G[q][j]}| (ids; -1 entries ignored)."""
+    _dev(I, torch.int64, "I")
+    _dev(G, torch.int64, "G")
+    _call("gbk_recall_counts", _ptr(I), _ptr(G), I.shape[0], I.shape[1], G.shape[1], _ptr(out),
+          _stream())
+    return out
+
+
+def nprobe_features(xq: torch.Tensor, coarse_dist: torch.Tensor, nfeat: int = 64):
+    """[x, d_i / d_0 - 1 for the nfeat nearest coarse distances] per query."""
+    nq, d = xq.shape
+    F = torch.empty((nq, d + nfeat), dtype=torch.float32, device=xq.device)
+    _call("gbk_nprobe_features", _ptr(xq), nq, int(d), _ptr(coarse_dist),
+          coarse_dist.shape[1], int(nfeat), _ptr(F), _stream())
+    return F
+
+
+def _batched_args(index, xq, k_per_q, max_k, nprobe_per_q, max_nprobe, mlp):
+    nq = xq.shape[0]
+    k_per_q = k_per_q.to(torch.int32).contiguous()
+    off = torch.zeros(nq + 1, dtype=torch.int64, device=xq.device)
+    off[1:] = torch.cumsum(k_per_q.to(torch.int64), 0)
+    total = int(off[-1].item())
+    D = torch.empty(total, dtype=torch.float32, device=xq.device)
+    I = torch.empty(total, dtype=torch.int64, device=xq.device)
+    used = torch.empty(nq, dtype=torch.int32, device=xq.device)
+    npq = nprobe_per_q.to(torch.int32).contiguous() if nprobe_per_q is not None else None
+    return nq, k_per_q, off, D, I, used, npq
+
+
+def ivfpq_search_batched(index, xq, k_per_q, max_k, nprobe_per_q=None, max_nprobe=256, mlp=None):
+    """Mixed batch: per-query k (and nprobe, or nprobe chosen by a trained MLP).  Returns
+    (D, I, offsets, nprobe_used): results of query q are D/I[offsets[q]:offsets[q+1]]."""
+    nq, kq, off, D, I, used, npq = _batched_args(index, xq, k_per_q, max_k, nprobe_per_q,
+                                                 max_nprobe, mlp)
+    _call("gbk_ivfpq_search_batched", index._h, _ptr(xq), nq, _ptr(kq), int(max_k), _ptr(npq),
+          int(max_nprobe), mlp._h if mlp is not None else None, _ptr(off), _ptr(D), _ptr(I),
+          _ptr(used), _stream())
+    return D, I, off, used
+
+
+class BatchedGraph:
+    """A captured CUDA graph of one mixed-batch search over fixed buffers; launch() replays
+    it (new query contents may be written into `xq` between launches)."""
+
+    def __init__(self, index, xq, k_per_q, max_k, nprobe_per_q=None, max_nprobe=256, mlp=None):
+        lib = load()
+        lib.gbk_graph_destroy.argtypes = [_vp]
+        lib.gbk_graph_destroy.restype = None
+        nq, kq, off, D, I, used, npq = _batched_args(index, xq, k_per_q, max_k, nprobe_per_q,
+                                                     max_nprobe, mlp)
+        self._keep = (index, xq, kq, off, npq, mlp)
+        self.D, self.I, self.offsets, self.nprobe_used = D, I, off, used
+        h = ctypes.c_void_p()
+        _call("gbk_ivfpq_batched_graph", index._h, _ptr(xq), nq, _ptr(kq), int(max_k), _ptr(npq),
+              int(max_nprobe), mlp._h if mlp is not None else None, _ptr(off), _ptr(D), _ptr(I),
+              _ptr(used), ctypes.byref(h), _stream())
+        self._h = h
+
+    def launch(self):
+        _call("gbk_graph_launch", self._h, _stream())
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.gbk_graph_destroy(self._h)
+            self._h = None

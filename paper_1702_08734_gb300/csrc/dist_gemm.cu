@@ -175,7 +175,8 @@ gbk_status knn_merge(const uint64_t* part, int64_t nq, int chunks, int kp, int k
   if (k <= 32) return launch_knn_merge<32>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);
   if (k <= 64) return launch_knn_merge<64>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);
   if (k <= 128) return launch_knn_merge<128>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);
-  return launch_knn_merge<256>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);
+  if (k <= 256) return launch_knn_merge<256>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);
+  return launch_knn_merge<512>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);
 }
 
 // ------------------------------------------------------------------ TMA descriptors
@@ -302,7 +303,8 @@ gbk_status gemm_launch(int mode, int kpr, bool largest, const PreparedOperand& Q
   }
   const DeviceInfo& di = device_info();
   const bool queues = mode == MODE_SELECT && kpr > 0;
-  const GemmSmemLayout l0 = gemm_smem_layout(pieces, Q.nkb, 0, queues);
+  const int epi = gemm_epi(prec);
+  const GemmSmemLayout l0 = gemm_smem_layout(pieces, Q.nkb, 0, queues, epi);
   const int64_t avail = (int64_t)di.smem_optin - 1024 - l0.total;
   const int64_t stage_bytes = (int64_t)pieces * GEMM_TILE_BYTES + 16;
   int stages = (int)std::min<int64_t>(8, avail / stage_bytes);
@@ -311,7 +313,7 @@ gbk_status gemm_launch(int mode, int kpr, bool largest, const PreparedOperand& Q
   a.stages = stages;
   a.nkb = Q.nkb;
   // at least half the SM's shared memory, so one CTA per SM owns the TMEM it allocates
-  const size_t smem = std::max<size_t>(gemm_smem_layout(pieces, Q.nkb, stages, queues).total + 1024,
+  const size_t smem = std::max<size_t>(gemm_smem_layout(pieces, Q.nkb, stages, queues, epi).total + 1024,
                                        di.smem_optin / 2 + 1024);
   const int nitems = a.nqt * a.chunks;
   const int grid = std::min(nitems, di.sm_count);
@@ -354,7 +356,7 @@ static gbk_status select_run(const float* xq, const PreparedOperand& Q, const Pr
                              float* D, int64_t* I, cudaStream_t st) {
   gbk_status r;
   const int ntiles = (int)((nb + GEMM_BN - 1) / GEMM_BN);
-  if (k > 256) {
+  if (k > 512) {
     // Large k: distance blocks of t_q queries x nb (section 5.1 tiling over queries), each
     // followed by a row-wise k-selection of the full distances.
     const int64_t budget = (int64_t)1 << 31;  // bytes of distance block
@@ -388,16 +390,16 @@ static gbk_status select_run(const float* xq, const PreparedOperand& Q, const Pr
   a.ynorm = B.norms.as<float>();
   a.qscale = Q.scale.as<float>();
   a.bscale = B.scale.as<float>();
+  const int lists = a.chunks * gemm_epi(Q.prec);  // candidate lists per query
   Scratch part, thr;
-  if ((r = part.alloc(sizeof(uint64_t) * (size_t)nq * a.chunks * a.kp, st)) != GBK_OK) return r;
+  if ((r = part.alloc(sizeof(uint64_t) * (size_t)nq * lists * a.kp, st)) != GBK_OK) return r;
   if ((r = thr.alloc(sizeof(uint32_t) * (size_t)nq, st)) != GBK_OK) return r;
   GBK_CUDA_CHECK(cudaMemsetAsync(thr.p, 0xff, sizeof(uint32_t) * (size_t)nq, st));
   a.part = part.as<uint64_t>();
   a.thr_key = thr.as<uint32_t>();
   const int kpr = k == 1 ? 0 : a.kp / 32;
   if ((r = gemm_launch(MODE_SELECT, kpr, ip, Q, B, a, st)) != GBK_OK) return r;
-  return knn_merge(a.part, nq, a.chunks, a.kp, k, ip ? nullptr : Q.norms.as<float>(), ip, D, I,
-                   st);
+  return knn_merge(a.part, nq, lists, a.kp, k, ip ? nullptr : Q.norms.as<float>(), ip, D, I, st);
 }
 
 gbk_status knn_run(const float* xq, int64_t nq, const float* xb, int64_t nb, int d, int k,
@@ -413,7 +415,10 @@ gbk_status knn_run(const float* xq, int64_t nq, const float* xb, int64_t nb, int
     return r;
   if (plan.prec == GBK_PREC_FP32) return select_run(xq, Q, B, nq, nb, d, k, ip, plan.chunks, D, I, st);
   // low precision: over-fetch k' candidates, then exact float32 re-rank + certificate
-  int kp = plan.kprime > 0 ? plan.kprime : std::min(4 * k, GBK_MAX_K);
+  // default over-fetch: 4k for small k, 2k (at least 64) once k is large enough that the
+  // candidates' rank statistics concentrate
+  int kp = plan.kprime > 0 ? plan.kprime : std::min(4 * k, std::max(2 * k, 64));
+  kp = std::min(kp, GBK_MAX_K);
   kp = (int)std::min<int64_t>(std::max(kp, k), nb);
   Scratch Dc, Ic;
   if ((r = Dc.alloc(sizeof(float) * (size_t)nq * kp, st)) != GBK_OK) return r;

@@ -41,28 +41,32 @@ enum GemmMode : int { MODE_SELECT = 0, MODE_STORE = 1 };
 
 constexpr int GEMM_BM = 128;          // queries per tile (TMEM lanes)
 constexpr int GEMM_BN = 128;          // database rows per tile (TMEM columns per buffer)
-constexpr int GEMM_THREADS = 192;
 constexpr int GEMM_QCAP = 24;         // queued candidates per query before a merge
 constexpr int GEMM_QSTRIDE = GEMM_QCAP + 1;
 constexpr uint32_t GEMM_TILE_BYTES = 128u * 128u;  // one 128-row x 128-byte box
 
 template <int KIND>
 struct KindTraits;
+// EPI: epilogue warpgroups.  The one-pass kinds finish a tile's MMAs three times faster,
+// so two warpgroups (each owning half of the tile's columns, with separate candidate
+// lists) keep the selection ahead of the tensor core; TF32X3 has no shared memory to spare.
 template <>
 struct KindTraits<KIND_TF32X3> {
-  static constexpr int ELEM = 4, PIECES = 2;
+  static constexpr int ELEM = 4, PIECES = 2, EPI = 1;
   static constexpr uint32_t FMT = sm100::FMT_TF32;
 };
 template <>
 struct KindTraits<KIND_BF16> {
-  static constexpr int ELEM = 2, PIECES = 1;
+  static constexpr int ELEM = 2, PIECES = 1, EPI = 2;
   static constexpr uint32_t FMT = sm100::FMT_BF16;
 };
 template <>
 struct KindTraits<KIND_FP8> {
-  static constexpr int ELEM = 1, PIECES = 1;
+  static constexpr int ELEM = 1, PIECES = 1, EPI = 2;
   static constexpr uint32_t FMT = sm100::FMT_E4M3;
 };
+__host__ __device__ constexpr int gemm_threads(int epi) { return 64 + 128 * epi; }
+__host__ __device__ constexpr int gemm_epi(int prec) { return prec == 0 ? 1 : 2; }
 
 struct GemmArgs {
   int nq, nb;            // queries, database rows
@@ -75,7 +79,7 @@ struct GemmArgs {
   const float* xnorm;    // STORE: [nq] ||x||^2 added (and the sum clamped at 0), or null
   const float* qscale;   // [nq] per-query dequantisation scale (FP8), else null
   const float* bscale;   // [ntiles*128] per-row database scale (FP8), else null
-  uint64_t* part;        // SELECT: [nq][chunks][kp] sorted composite lists
+  uint64_t* part;        // SELECT: [nq][chunks * EPI][kp] sorted composite lists
   uint32_t* thr_key;     // SELECT: [nq] global threshold keys (init 0xffffffff)
   float* out;            // STORE: [nq][ldo] partial distances
   int64_t ldo;

@@ -14,7 +14,7 @@ static gbk_status go(const CUtensorMap* m, const GemmArgs& a, int grid, size_t s
                                         (int)device_info().smem_optin));
     attr = true;
   }
-  kern<<<grid, GEMM_THREADS, smem, st>>>(m[0], m[1], m[2], m[3], a);
+  kern<<<grid, gemm_threads(KindTraits<KIND_BF16>::EPI), smem, st>>>(m[0], m[1], m[2], m[3], a);
   GBK_LAUNCH_CHECK();
   return GBK_OK;
 }
@@ -29,7 +29,8 @@ static gbk_status pick(int mode, int kpr, const CUtensorMap* m, const GemmArgs& 
     case 2: return go<MODE_SELECT, 2, LG>(m, a, grid, smem, st);
     case 4: return go<MODE_SELECT, 4, LG>(m, a, grid, smem, st);
     case 8: return go<MODE_SELECT, 8, LG>(m, a, grid, smem, st);
-    default: return set_error(GBK_EUNSUPPORTED, "fused selection supports k <= 256");
+    case 16: return go<MODE_SELECT, 16, LG>(m, a, grid, smem, st);
+    default: return set_error(GBK_EUNSUPPORTED, "fused selection supports k <= 512");
   }
 }
 

@@ -442,6 +442,7 @@ __global__ void recall_counts_kernel(const int64_t* __restrict__ I, const int64_
 
 gbk_status mlp_forward_classes(gbk_mlp* net, const float* X, int64_t B, int32_t* cls,
                                cudaStream_t st);
+int mlp_inputs(const gbk_mlp* n);
 
 gbk_status batched_run(gbk_index* ix, const float* xq, int64_t nq, const int32_t* kq, int max_k,
                        const int32_t* npq_in, int max_nprobe, gbk_mlp* mlp,
@@ -526,6 +527,11 @@ static gbk_status batched_check(gbk_index* ix, const float* xq, int64_t nq, cons
   GBK_REQUIRE(max_nprobe >= 1 && max_nprobe <= ix->nlist && max_nprobe <= GBK_MAX_K,
               "batched search: max_nprobe out of range");
   GBK_REQUIRE(npq || mlp, "batched search: give nprobe_per_q or a network");
+  if (!npq) {
+    GBK_REQUIRE(ix->nlist >= 64, "learned nprobe needs nlist >= 64 (64 coarse-distance features)");
+    GBK_REQUIRE(gbk::mlp_inputs(mlp) == ix->d + 64,
+                "learned nprobe: network inputs must be d + 64 = %d", ix->d + 64);
+  }
   GBK_REQUIRE(nq == 0 || (xq && kq && out_off && D && I), "batched search: NULL pointer");
   return GBK_OK;
 }

@@ -231,6 +231,9 @@ gbk_status mlp_grad(gbk_mlp* n, const float* X, const int32_t* y, int64_t B, flo
 }  // namespace
 
 namespace gbk {
+int mlp_inputs(const gbk_mlp* n) { return n ? n->n_in : 0; }
+int mlp_outputs(const gbk_mlp* n) { return n ? n->n_out : 0; }
+
 gbk_status mlp_forward_classes(gbk_mlp* n, const float* X, int64_t B, int32_t* cls,
                                cudaStream_t st) {
   ProfScope prof("mlp_forward", st);

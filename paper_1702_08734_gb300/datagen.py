@@ -146,3 +146,78 @@ def permutation_prefix(seed: int, n: int, m: int) -> np.ndarray:
     h = hash_u64(seed, 0, n, stream=7)
     order = np.lexsort((np.arange(n), h))
     return order[:m].astype(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# The same generator evaluated on a CUDA device (torch), for workloads too large to
+# generate on the host.  Integer hashing is bit-identical to the numpy version (int64
+# arithmetic wraps mod 2**64; right shifts are masked to be logical); Box-Muller runs in
+# float64 on the device, whose log/cos may differ from the host's in the last double ulp,
+# so an N(0,1) value can differ by one float32 ulp in rare (~1e-8) cases.
+# ---------------------------------------------------------------------------
+
+def _t_signed(v: int) -> int:
+    v &= _M64
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _t_shr(z, s):
+    import torch
+    return (z >> s) & torch.tensor(_t_signed((1 << (64 - s)) - 1), dtype=torch.int64,
+                                   device=z.device)
+
+
+def _t_mix64(z):
+    z = z ^ _t_shr(z, 30)
+    z = z * _t_signed(0xBF58476D1CE4E5B9)
+    z = z ^ _t_shr(z, 27)
+    z = z * _t_signed(0x94D049BB133111EB)
+    z = z ^ _t_shr(z, 31)
+    return z
+
+
+def hash_u64_cuda(seed: int, start: int, count: int, stream: int = 0, device="cuda"):
+    """h(key(seed, stream), i) as int64 bit patterns on the device."""
+    import torch
+    key = _t_signed(stream_key(seed, stream))
+    i = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+    return _t_mix64(key + i * _t_signed(0x9E3779B97F4A7C15))
+
+
+def normal_cuda(seed: int, start: int, count: int, stream: int = 0, device="cuda"):
+    import torch
+    h = hash_u64_cuda(seed, 2 * start, 2 * count, stream, device)
+    u1 = (_t_shr(h[0::2], 11).to(torch.float64) + 1.0) * 2.0 ** -53
+    u2 = _t_shr(h[1::2], 11).to(torch.float64) * 2.0 ** -53
+    return (torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * np.pi * u2)).to(torch.float32)
+
+
+def randint_cuda(seed: int, start: int, count: int, n: int, stream: int = 0, device="cuda"):
+    """h mod n for n a power of two (the only case the workloads use)."""
+    assert n & (n - 1) == 0
+    return hash_u64_cuda(seed, start, count, stream, device) & (n - 1)
+
+
+def gaussian_matrix_cuda(seed: int, n: int, d: int, row0: int = 0, device="cuda"):
+    import torch
+    out = torch.empty((n, d), dtype=torch.float32, device=device)
+    step = max(1, (1 << 24) // d)
+    for r in range(0, n, step):
+        c = min(step, n - r)
+        out[r:r + c] = normal_cuda(seed, (row0 + r) * d, c * d, device=device).view(c, d)
+    return out
+
+
+def mixture_points_cuda(centres, seed: int, n: int, row0: int = 0, device="cuda"):
+    """Device version of mixture_points (centres: host or device float32 [nc][d])."""
+    import torch
+    cen = torch.as_tensor(centres, device=device)
+    nc, d = cen.shape
+    out = torch.empty((n, d), dtype=torch.float32, device=device)
+    step = max(1, (1 << 24) // d)
+    for r in range(0, n, step):
+        c = min(step, n - r)
+        u = randint_cuda(seed, row0 + r, c, nc, stream=0, device=device)
+        noise = normal_cuda(seed, (row0 + r) * d, c * d, stream=1, device=device).view(c, d)
+        out[r:r + c] = cen[u] + noise
+    return out
