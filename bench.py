@@ -324,7 +324,13 @@ def main():
     ap.add_argument("--ivf-n", type=int, default=10000000)
     ap.add_argument("--learn-n", type=int, default=200000)
     ap.add_argument("--learn-epochs", type=int, default=15)
+    ap.add_argument("--small", action="store_true",
+                    help="profiling case of the exact workload: nq=2000, nb=400000, 2000 "
+                         "k-select rows (inputs still larger than L2); not a bench line")
     args = ap.parse_args()
+    global NQ, NB, KSEL_ROWS
+    if args.small:
+        NQ, NB, KSEL_ROWS = 2000, 400000, 2000
     if args.workload == "ivfadc" and args.impl == "ours":
         run_ivfadc(args)
         return
@@ -458,7 +464,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded N(0,1) database/queries, U[0,1) k-select rows)",
-            "config": {"workload": "exact k-NN nb=1e6 nq=1e4 d=128 k in {10,100} (TF32x3, float32-accurate) + k-select 1e4 x 65536 k in {1,32,256,1024}",
+            "config": {"workload": "exact k-NN nb=%d nq=%d d=%d k in {10,100} (TF32x3, float32-accurate) + k-select %d x %d k in {1,32,256,1024}" % (NB, NQ, D, KSEL_ROWS, KSEL_LEN),
                        "l2_flush": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU",
                        "knn_ms_per_step": knn_ms / args.steps, "kselect_ms_per_step": ksel_ms / args.steps},
             "roofline": roof, "kselect": kselect_obj, "cpu_baseline": cpu, "e2e": e2e,

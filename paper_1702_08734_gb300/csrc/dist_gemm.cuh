@@ -4,17 +4,20 @@
 // selection and writes D' once, section 5.1; on sm_103a the accumulator tile can be
 // filtered straight out of tensor memory).
 //
-// CTA = 192 threads, one per SM (persistent):
+// CTA = 64 + 128 * EPI threads, one per SM (persistent):
 //   warp 0      TMA producer: the 128-query A tile (all of d, resident for a work item)
 //               and a ring of 128-row database B k-blocks (128 bytes of K per row,
 //               SWIZZLE_128B boxes);
 //   warp 1      TMEM allocator + single-thread MMA issuer: 128x128 tiles, K = 32 bytes
-//               per instruction, double-buffered accumulators (2 x 128 TMEM columns);
-//   warps 2..5  epilogue: thread t of quarter q owns query row 32q+t (its TMEM lane),
-//               reads 16 accumulator columns at a time, forms ||y||^2 - 2<x,y> (or <x,y>
-//               for inner product), filters against its query's threshold and queues
-//               survivors; full queues are merged by the whole warp into the query's
-//               sorted candidate list (bitonic network over shuffles).
+//               per instruction, GEMM_NACC accumulator buffers of 128 TMEM columns, so
+//               the MMAs run several tiles ahead of the epilogue;
+//   warps 2..   epilogue, EPI warpgroups each owning 128 / EPI columns of every tile:
+//               thread t of quarter q owns query row 32q+t (its TMEM lane), reads 32
+//               accumulator columns at a time, forms ||y||^2 - 2<x,y> (or <x,y> for
+//               inner product), and tests the batch's best value against its query's
+//               threshold; only batches holding a survivor queue their survivors, and
+//               full queues are merged by the whole warp into the query's sorted
+//               candidate list (bitonic network over shuffles).
 // Work item = (query tile, database chunk); items are chunk-major so all CTAs sweep
 // the database in near lockstep and each B tile is fetched from HBM about once.  A
 // global per-query threshold (ordered key, atomicMin) carries the k-th distance of
@@ -41,6 +44,7 @@ enum GemmMode : int { MODE_SELECT = 0, MODE_STORE = 1 };
 
 constexpr int GEMM_BM = 128;          // queries per tile (TMEM lanes)
 constexpr int GEMM_BN = 128;          // database rows per tile (TMEM columns per buffer)
+constexpr int GEMM_NACC = 4;          // TMEM accumulator buffers (4 x 128 columns = all 512)
 constexpr int GEMM_QCAP = 24;         // queued candidates per query before a merge
 constexpr int GEMM_QSTRIDE = GEMM_QCAP + 1;
 constexpr uint32_t GEMM_TILE_BYTES = 128u * 128u;  // one 128-row x 128-byte box
@@ -120,8 +124,10 @@ __device__ __forceinline__ void warp_merge_list(uint64_t (&L)[KPR], uint64_t q_s
   const int lane = threadIdx.x & 31;
   const uint64_t qrev = shfl64(q_sorted, 31 - lane);
   L[KPR - 1] = min(L[KPR - 1], qrev);
+  constexpr int LOGK = KPR >= 16 ? 4 : KPR >= 8 ? 3 : KPR >= 4 ? 2 : KPR >= 2 ? 1 : 0;
 #pragma unroll
-  for (int s = KPR / 2; s >= 1; s >>= 1) {  // strides >= 32: within a lane
+  for (int ls = LOGK - 1; ls >= 0; ls--) {  // strides >= 32: within a lane
+    const int s = 1 << ls;
 #pragma unroll
     for (int r = 0; r < KPR; r++) {
       if ((r & s) == 0) {

@@ -20,8 +20,87 @@ __host__ __device__ inline GemmSmemLayout gemm_smem_layout(int pieces, int nkb, 
   const uint32_t qbytes = queues ? (uint32_t)(epi * GEMM_BM * GEMM_QSTRIDE * 8) : 0u;
   L.y_off = (L.q_off + qbytes + 15u) & ~15u;
   L.bar_off = (L.y_off + (uint32_t)(epi * 4 * 1024) + 63u) & ~63u;
-  L.total = L.bar_off + 8u * (2u + 2u * (uint32_t)stages + 4u) + 16u;
+  L.total = L.bar_off + 8u * (2u + 2u * (uint32_t)stages + 2u * GEMM_NACC) + 16u;
   return L;
+}
+
+// Three-input min / max (sm_100 family); as with the two-input forms a NaN input is
+// ignored unless every input is NaN.
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Best (smallest, or largest for LARGEST) of 32 values as a depth-4 tree; NaN only when
+// all 32 are NaN.
+template <bool LARGEST>
+__device__ __forceinline__ float batch_best32(const float (&v)[32]) {
+  float a[12];
+#pragma unroll
+  for (int i = 0; i < 10; i++)
+    a[i] = LARGEST ? max3f(v[3 * i], v[3 * i + 1], v[3 * i + 2])
+                   : min3f(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+  a[10] = v[30];
+  a[11] = v[31];
+  float b[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+    b[i] = LARGEST ? max3f(a[3 * i], a[3 * i + 1], a[3 * i + 2])
+                   : min3f(a[3 * i], a[3 * i + 1], a[3 * i + 2]);
+  const float c = LARGEST ? max3f(b[0], b[1], b[2]) : min3f(b[0], b[1], b[2]);
+  return LARGEST ? fmaxf(c, b[3]) : fminf(c, b[3]);
+}
+
+// Warp-cooperative merge of every lane's candidate queue holding more than `limit`
+// entries into that lane's sorted list (queue of lane l: sQ[l * GEMM_QSTRIDE ...] as
+// {value bits, column}; list of lane l at part + l * rowstride, KPR*32 composites).  The
+// merging lane's threshold becomes its list's k-th value.
+template <int KPR, bool LARGEST>
+__device__ __forceinline__ void merge_queues(int limit, int& cnt, float& thr, const uint2* sQ,
+                                             uint64_t* part, int64_t rowstride, int k,
+                                             int quarter, int lane) {
+  if constexpr (KPR == 0) return;  // k = 1 keeps no lists
+  constexpr int KR = KPR > 0 ? KPR : 1;
+  unsigned m = __ballot_sync(FULL_MASK, cnt > limit);
+  if (!m) return;
+  __syncwarp();  // other lanes' queue writes are visible
+  while (m) {
+    const int l = __ffs(m) - 1;
+    m &= m - 1;
+    const int n = __shfl_sync(FULL_MASK, cnt, l);
+    uint64_t v = ~0ull;
+    if (lane < n) {
+      const uint2 e = sQ[l * GEMM_QSTRIDE + lane];
+      v = composite(ordered_key(__uint_as_float(e.x), LARGEST), e.y);
+    }
+    v = warp_sort32(v);
+    uint64_t* Lg = part + (int64_t)l * rowstride;
+    uint64_t L[KR];
+#pragma unroll
+    for (int r = 0; r < KR; r++) L[r] = Lg[r * 32 + lane];
+    warp_merge_list<KR>(L, v);
+#pragma unroll
+    for (int r = 0; r < KR; r++) Lg[r * 32 + lane] = L[r];
+    // new threshold: element k-1 of the list
+    const int kk = k - 1;
+    uint64_t tk = 0;
+#pragma unroll
+    for (int r = 0; r < KR; r++)  // masked OR, not an indexed read (keeps L in registers)
+      tk |= L[r] & (0ull - (uint64_t)(r == (kk >> 5)));
+    tk = shfl64(tk, kk & 31);
+    if (lane == l) {
+      cnt = 0;
+      if (tk != ~0ull) thr = key_value((uint32_t)(tk >> 32), LARGEST);
+    }
+  }
+  __syncwarp();
+  (void)quarter;
 }
 
 // KPR: candidate list length / 32 (SELECT with k > 1); KPR == 0 with MODE_SELECT is the
@@ -50,8 +129,8 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
   uint64_t* b_full = bars + 2;
   uint64_t* b_empty = b_full + args.stages;
   uint64_t* acc_full = b_empty + args.stages;
-  uint64_t* acc_empty = acc_full + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* acc_empty = acc_full + GEMM_NACC;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + GEMM_NACC);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -64,7 +143,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       sm100::mbar_init(&b_full[i], 1);
       sm100::mbar_init(&b_empty[i], 1);
     }
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < GEMM_NACC; i++) {
       sm100::mbar_init(&acc_full[i], 1);
       sm100::mbar_init(&acc_empty[i], 4 * EPI);
     }
@@ -72,7 +151,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
     sm100::fence_mbar_init();
   }
   if (warp == 1) {
-    sm100::tmem_alloc(tmem_slot, 2 * GEMM_BN);
+    sm100::tmem_alloc(tmem_slot, GEMM_NACC * GEMM_BN);
     sm100::tmem_relinquish();
   }
   sm100::tc_fence_before();
@@ -136,8 +215,8 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
         sm100::tc_fence_after();
         const uint32_t a_base = sm100::smem_u32(sA);
         for (int t = t0; t < t1 && ok; t++, gtile++) {
-          const int acc = (int)(gtile & 1u);
-          ok = sm100::mbar_wait(&acc_empty[acc], ((gtile >> 1) & 1u) ^ 1u, args.status,
+          const int acc = (int)(gtile % GEMM_NACC);
+          ok = sm100::mbar_wait(&acc_empty[acc], ((gtile / GEMM_NACC) & 1u) ^ 1u, args.status,
                                 abort_flag);
           if (!ok) break;
           sm100::tc_fence_after();
@@ -222,76 +301,44 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           __syncwarp();
         }
       }
-      // warp-cooperative merge of every queue holding more than `limit` entries
-      auto merge_queues = [&](int limit) {
-        if constexpr (QUEUES) {
-          unsigned m = __ballot_sync(FULL_MASK, cnt > limit);
-          if (m) __syncwarp();  // other lanes' queue writes are visible
-          while (m) {
-            const int l = __ffs(m) - 1;
-            m &= m - 1;
-            const int n = __shfl_sync(FULL_MASK, cnt, l);
-            const int ql = quarter * 32 + l;
-            const int qq = qt * GEMM_BM + ql;
-            uint64_t v = lane < n ? sQ[(half * GEMM_BM + ql) * GEMM_QSTRIDE + lane] : ~0ull;
-            v = warp_sort32(v);
-            uint64_t* Lg = args.part + ((int64_t)qq * lists + ch * EPI + half) * args.kp;
-            uint64_t L[KPR];
-#pragma unroll
-            for (int r = 0; r < KPR; r++) L[r] = Lg[r * 32 + lane];
-            warp_merge_list<KPR>(L, v);
-#pragma unroll
-            for (int r = 0; r < KPR; r++) Lg[r * 32 + lane] = L[r];
-            // new threshold: element k-1 of the list
-            const int kk = args.k - 1;
-            uint64_t tk = 0;
-#pragma unroll
-            for (int r = 0; r < KPR; r++)
-              if (r == (kk >> 5)) tk = L[r];
-            tk = shfl64(tk, kk & 31);
-            if (lane == l) {
-              cnt = 0;
-              if (tk != ~0ull) thr = key_value((uint32_t)(tk >> 32), LARGEST);
-            }
-          }
-          __syncwarp();
-        }
-      };
-      for (int t = t0; t < t1; t++, gtile++) {
-        const int acc = (int)(gtile & 1u);
-        const int col0 = t * GEMM_BN + co;  // first column of this warp's part
-        // stage this part's database norms (and FP8 scales) while the MMAs run
-        __syncwarp();
+      // lists of this warp's 32 queries (lane l: pbase + l * rowstride) and their queues
+      const int64_t rowstride = (int64_t)lists * args.kp;
+      uint64_t* pbase =
+          QUEUES ? args.part + ((int64_t)(qt * GEMM_BM + quarter * 32) * lists + ch * EPI + half) *
+                                   args.kp
+                 : nullptr;
+      const uint2* sQh = reinterpret_cast<const uint2*>(sQ + (half * GEMM_BM + quarter * 32) * GEMM_QSTRIDE);
+      // Database norms (and FP8 scales) of this warp's part of a tile, fetched one tile
+      // ahead into registers so the global-load latency hides behind a tile of work, then
+      // staged in shared memory (the values are the same for the warp's 32 rows).
+      float4 pre_y = make_float4(0.f, 0.f, 0.f, 0.f), pre_s = pre_y;
+      auto prefetch = [&](int t) {
         if (lane < CW / 4) {
           if (!LARGEST)
-            reinterpret_cast<float4*>(sY)[lane] =
-                __ldg(reinterpret_cast<const float4*>(args.ynorm + col0) + lane);
-          if (KIND == KIND_FP8)  // shared by the warp's rows: the row scale is applied below
-            reinterpret_cast<float4*>(sY + 128)[lane] =
-                __ldg(reinterpret_cast<const float4*>(args.bscale + col0) + lane);
+            pre_y = __ldg(reinterpret_cast<const float4*>(args.ynorm + t * GEMM_BN + co) + lane);
+          if (KIND == KIND_FP8)  // the row scale is applied below
+            pre_s = __ldg(reinterpret_cast<const float4*>(args.bscale + t * GEMM_BN + co) + lane);
+        }
+      };
+      if (t0 < t1) prefetch(t0);
+      for (int t = t0; t < t1; t++, gtile++) {
+        const int acc = (int)(gtile % GEMM_NACC);
+        const int col0 = t * GEMM_BN + co;  // first column of this warp's part
+        __syncwarp();
+        if (lane < CW / 4) {
+          if (!LARGEST) reinterpret_cast<float4*>(sY)[lane] = pre_y;
+          if (KIND == KIND_FP8) reinterpret_cast<float4*>(sY + 128)[lane] = pre_s;
         }
         __syncwarp();
-        ok = sm100::mbar_wait(&acc_full[acc], (gtile >> 1) & 1u, args.status, abort_flag);
+        if (t + 1 < t1) prefetch(t + 1);
+        ok = sm100::mbar_wait(&acc_full[acc], (gtile / GEMM_NACC) & 1u, args.status, abort_flag);
         if (!ok) break;
         sm100::tc_fence_after();
-        const int lim = args.nb - col0;  // valid columns in this part
+        const int lim = args.nb - col0;  // valid columns in this part (warp-uniform)
         const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * GEMM_BN + co);
-        uint32_t rb[32];
-        sm100::tmem_ld_x32(taddr, rb);
-#pragma unroll 1
-        for (int b = 0; b < CW / 32; b++) {
-          sm100::tmem_wait_ld();
-          float dist[32];
-#pragma unroll
-          for (int j = 0; j < 32; j++) dist[j] = __uint_as_float(rb[j]);
-          if (b + 1 < CW / 32) {
-            sm100::tmem_ld_x32(taddr + (uint32_t)((b + 1) * 32), rb);  // next batch in flight
-          } else {
-            sm100::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) sm100::mbar_arrive(&acc_empty[acc]);
-          }
-          const int cb = b * 32;
+        // One batch = 32 accumulator columns of this lane's row, already in registers.
+        auto batch = [&](float (&dist)[32], const int cb) {
+          const int cbase = col0 + cb;  // database row of dist[0]
           if (KIND == KIND_FP8) {
             const float4* bs4 = reinterpret_cast<const float4*>(sY + 128 + cb);
 #pragma unroll
@@ -317,50 +364,104 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
 #pragma unroll
             for (int j = 0; j < 32; j++) dist[j] *= qs;
           }
-          const uint32_t vm = lim >= cb + 32 ? 0xffffffffu : (lim <= cb ? 0u : ((1u << (lim - cb)) - 1u));
+          const bool ragged = lim < cb + 32;  // columns past nb in this batch (last tile only)
           if (MODE == MODE_STORE) {
             if (qvalid) {
 #pragma unroll
               for (int j = 0; j < 32; j++)
-                if ((vm >> j) & 1u)
-                  args.out[(int64_t)q * args.ldo + col0 + cb + j] =
+                if (!ragged || cb + j < lim)
+                  args.out[(int64_t)q * args.ldo + cbase + j] =
                       xn_store >= 0.f ? fmaxf(dist[j] + xn_store, 0.f) : dist[j];
             }
-          } else if (!QUEUES) {
+            return;
+          }
+          if (ragged) {  // past-the-end columns become NaN: they pass no threshold
 #pragma unroll
-            for (int j = 0; j < 32; j++) {
-              const bool better = LARGEST ? dist[j] > bestd : dist[j] < bestd;
-              if (better && ((vm >> j) & 1u)) {
-                bestd = dist[j];
-                besti = col0 + cb + j;
-              }
+            for (int j = 0; j < 32; j++)
+              if (cb + j >= lim) dist[j] = __int_as_float(0x7fc00000);
+          }
+          // Fast path: the batch's best value (NaN ignored) decides whether any of its 32
+          // values can enter; most batches end here once the threshold has settled.
+          const float bm = batch_best32<LARGEST>(dist);
+          if (!QUEUES) {
+            const bool imp = LARGEST ? bm > bestd : bm < bestd;  // strict: earlier column wins ties
+            if (__any_sync(FULL_MASK, imp) && imp) {
+              int jj = 31;
+#pragma unroll
+              for (int j = 31; j >= 0; j--)
+                if (dist[j] == bm) jj = j;  // lowest column holding the best value
+              bestd = bm;
+              besti = cbase + jj;
             }
           } else {
+            const bool any = LARGEST ? bm >= thr : bm <= thr;
+            if (__any_sync(FULL_MASK, any)) {
+              uint2* q2 = reinterpret_cast<uint2*>(myQ);
 #pragma unroll
-            for (int hf = 0; hf < 2; hf++) {
-              uint32_t m = 0;
+              for (int hf = 0; hf < 2; hf++) {
+                if (any) {
 #pragma unroll
-              for (int jj = 0; jj < 16; jj++) {
-                const float dv = dist[hf * 16 + jj];
-                m |= ((LARGEST ? dv >= thr : dv <= thr) ? 1u : 0u) << jj;
+                  for (int jj = 0; jj < 16; jj++) {
+                    const float dv = dist[hf * 16 + jj];
+                    if (LARGEST ? dv >= thr : dv <= thr)
+                      q2[cnt++] = make_uint2(__float_as_uint(dv), (uint32_t)(cbase + hf * 16 + jj));
+                  }
+                }
+                merge_queues<KPR, LARGEST>(GEMM_QCAP - 16, cnt, thr, sQh, pbase, rowstride,
+                                           args.k, quarter, lane);
               }
-              m &= (vm >> (hf * 16)) & 0xffffu;
-              if (m) {
-#pragma unroll
-                for (int jj = 0; jj < 16; jj++)
-                  if (m & (1u << jj))
-                    myQ[cnt++] = composite(ordered_key(dist[hf * 16 + jj], LARGEST),
-                                           (uint32_t)(col0 + cb + hf * 16 + jj));
-              }
-              merge_queues(GEMM_QCAP - 16);
             }
           }
+        };
+        if constexpr (QUEUES) {
+          // one batch at a time (the merge code stays out of line of a second copy), the
+          // next batch's TMEM load in flight while this one is filtered
+          uint32_t rb[32];
+          sm100::tmem_ld_x32(taddr, rb);
+#pragma unroll 1
+          for (int b = 0; b < CW / 32; b++) {
+            sm100::tmem_wait_ld();
+            float d[32];
+#pragma unroll
+            for (int j = 0; j < 32; j++) d[j] = __uint_as_float(rb[j]);
+            if (b + 1 < CW / 32) {
+              sm100::tmem_ld_x32(taddr + (uint32_t)((b + 1) * 32), rb);
+            } else {
+              sm100::tc_fence_before();
+              __syncwarp();
+              if (lane == 0) sm100::mbar_arrive(&acc_empty[acc]);
+            }
+            batch(d, b * 32);
+          }
+        } else {
+        // Two batches per TMEM wait; the accumulator buffer is handed back to the MMA warp
+        // as soon as its last columns are in registers.
+#pragma unroll 1
+        for (int b = 0; b < CW / 64; b++) {
+          uint32_t r0[32], r1[32];
+          sm100::tmem_ld_x32(taddr + (uint32_t)(b * 64), r0);
+          sm100::tmem_ld_x32(taddr + (uint32_t)(b * 64 + 32), r1);
+          sm100::tmem_wait_ld();
+          if (b + 1 == CW / 64) {
+            sm100::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) sm100::mbar_arrive(&acc_empty[acc]);
+          }
+          float d0[32], d1[32];
+#pragma unroll
+          for (int j = 0; j < 32; j++) {
+            d0[j] = __uint_as_float(r0[j]);
+            d1[j] = __uint_as_float(r1[j]);
+          }
+          batch(d0, b * 64);
+          batch(d1, b * 64 + 32);
+        }
         }
       }
       if (!ok) break;
       if (MODE == MODE_SELECT) {
         if (QUEUES) {
-          merge_queues(0);
+          merge_queues<KPR, LARGEST>(0, cnt, thr, sQh, pbase, rowstride, args.k, quarter, lane);
           // publish this chunk's k-th distance as an upper bound for later chunks
           if (qvalid) {
             const uint64_t* Lg = args.part + ((int64_t)q * lists + ch * EPI + half) * args.kp;
@@ -379,7 +480,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
   __syncthreads();
   if (warp == 1) {
     sm100::tc_fence_after();
-    sm100::tmem_dealloc(tmem_base, 2 * GEMM_BN);
+    sm100::tmem_dealloc(tmem_base, GEMM_NACC * GEMM_BN);
   }
 }
 

@@ -108,6 +108,28 @@ def test_knn_integer_lattice_bit_exact(gbk):
         np.testing.assert_array_equal(D.cpu().numpy(), Do.astype(np.float32))
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+@pytest.mark.parametrize("k", [1, 10])
+def test_knn_nan_rows_rank_last(gbk, prec, metric, k):
+    # NaN database rows give NaN distances, which rank after every number (the oracle's
+    # order): they never displace a finite neighbour, whatever batch they fall in
+    xq = datagen.gaussian_matrix(61, 100, 64)
+    xb = datagen.gaussian_matrix(62, 6000, 64)
+    bad = np.unique(datagen.randint(63, 0, 300, 6000))
+    xb[bad, 5] = np.nan
+    D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), k,
+                         metric=metric, precision=prec)
+    I = I.cpu().numpy()
+    assert not np.isin(I, bad).any()
+    good = np.setdiff1d(np.arange(6000), bad)
+    Do, Io = oracle.knn(xq, xb[good], k, metric=metric)
+    if prec == "fp32":
+        _check_knn(xq, xb[good], D, torch.from_numpy(np.searchsorted(good, I)), k, metric)
+    else:
+        assert (np.searchsorted(good, I) == Io).mean() > 0.95
+
+
 @pytest.mark.parametrize("k", [300, 1024])
 def test_knn_large_k_path(gbk, k):
     xq = datagen.gaussian_matrix(41, 50, 64)
