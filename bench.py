@@ -296,11 +296,18 @@ def run_learned(args):
         _, r10 = recall_stats(g, I, Igt)
         fixed.append({"nprobe": tau, "qps": nq / (ms / 1e3), "R10@10": r10})
     kq = torch.full((nq,), 10, dtype=torch.int32, device="cuda")
+    cap = 64  # nprobe cap of the learned routing: the 64 coarse distances of the features
+    g.profile_enable(True)
     ms, (D, I, off, used) = time_search(
-        g, lambda: g.ivfpq_search_batched(ix, xq, kq, 10, None, 256, mlp=net), args.steps)
+        g, lambda: g.ivfpq_search_batched(ix, xq, kq, 10, None, cap, mlp=net), args.steps)
+    g.profile_enable(False)
+    by = {}
+    for nm, tt in g.profile_read():
+        by.setdefault(nm, []).append(tt)
     _, r10 = recall_stats(g, I.view(nq, 10), Igt)
-    learned = {"qps": nq / (ms / 1e3), "R10@10": r10,
-               "mean_nprobe": float(used.float().mean().item())}
+    learned = {"qps": nq / (ms / 1e3), "R10@10": r10, "nprobe_cap": cap,
+               "mean_nprobe": float(used.float().mean().item()),
+               "kernel_ms": {kk: sum(v) / len(v) for kk, v in by.items()}}
     # fixed-nprobe q/s at the learned recall (log-linear interpolation between neighbours)
     eq = None
     for a, b in zip(fixed, fixed[1:]):

@@ -101,6 +101,13 @@ namespace {
 
 // ------------------------------------------------------------------ cross-chunk merge
 
+// D[q][j] <- max(0, D[q][j] + ||x_q||^2): the query norm added to selected L2 values.
+__global__ void add_norm_clamp_kernel(float* __restrict__ D, int64_t nq, int k,
+                                      const float* __restrict__ xnorm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nq * k) D[i] = fmaxf(D[i] + xnorm[i / k], 0.f);
+}
+
 template <int KP>
 __global__ void __launch_bounds__(256)
     knn_merge_kernel(const uint64_t* __restrict__ part, int chunks, int kp, int k,
@@ -285,17 +292,24 @@ int plan_chunks(int nqt, int ntiles, int grid_cap) {
   return best;
 }
 
+// Q rows [q0, q0 + qn) (all rows when qn < 0) against all of B.
 gbk_status gemm_launch(int mode, int kpr, bool largest, const PreparedOperand& Q,
-                       const PreparedOperand& B, GemmArgs a, cudaStream_t st) {
+                       const PreparedOperand& B, GemmArgs a, cudaStream_t st, int64_t q0 = 0,
+                       int64_t qn = -1) {
   const int prec = Q.prec;
   const int pieces = pieces_of(prec);
   const int eb = elem_bytes_of(prec);
   CUtensorMap maps[4];
   gbk_status r;
-  if ((r = make_operand_map(&maps[0], Q.piece[0], Q.n, Q.dpad, eb)) != GBK_OK) return r;
+  if (qn < 0) qn = Q.n - q0;
+  const size_t qoff = (size_t)q0 * Q.dpad * eb;  // a multiple of 128 bytes
+  if ((r = make_operand_map(&maps[0], (const char*)Q.piece[0] + qoff, qn, Q.dpad, eb)) != GBK_OK)
+    return r;
   if ((r = make_operand_map(&maps[2], B.piece[0], B.n, B.dpad, eb)) != GBK_OK) return r;
   if (pieces > 1) {
-    if ((r = make_operand_map(&maps[1], Q.piece[1], Q.n, Q.dpad, eb)) != GBK_OK) return r;
+    if ((r = make_operand_map(&maps[1], (const char*)Q.piece[1] + qoff, qn, Q.dpad, eb)) !=
+        GBK_OK)
+      return r;
     if ((r = make_operand_map(&maps[3], B.piece[1], B.n, B.dpad, eb)) != GBK_OK) return r;
   } else {
     maps[1] = maps[0];
@@ -328,25 +342,27 @@ gbk_status gemm_launch(int mode, int kpr, bool largest, const PreparedOperand& Q
   return launch_dist_gemm_fp8(mode, kpr, largest, maps, a, grid, smem, st);
 }
 
-// Distances of every (query, database) pair: max(0, ||x||^2 + ||y||^2 - 2<x,y>) for L2,
-// <x,y> for inner product.
+// Distances of every (query, database) pair: max(0, ||x||^2 + ||y||^2 - 2<x,y>) for L2
+// (||y||^2 - 2<x,y> without the query norm when add_xnorm is false), <x,y> for inner
+// product.  Query rows [q0, q0 + qn) of Q (all when qn < 0); out row 0 is query q0.
 gbk_status pairwise_run(const PreparedOperand& Q, const PreparedOperand& B, bool ip, float* out,
-                        int64_t ldo, cudaStream_t st) {
+                        int64_t ldo, cudaStream_t st, int64_t q0, int64_t qn, bool add_xnorm) {
+  if (qn < 0) qn = Q.n - q0;
   GemmArgs a = {};
-  a.nq = (int)Q.n;
+  a.nq = (int)qn;
   a.nb = (int)B.n;
-  a.nqt = (int)((Q.n + GEMM_BM - 1) / GEMM_BM);
+  a.nqt = (int)((qn + GEMM_BM - 1) / GEMM_BM);
   a.ntiles = (int)((B.n + GEMM_BN - 1) / GEMM_BN);
   a.chunks = plan_chunks(a.nqt, a.ntiles, device_info().sm_count);
   a.tpc = (a.ntiles + a.chunks - 1) / a.chunks;
   a.chunks = (a.ntiles + a.tpc - 1) / a.tpc;
   a.ynorm = B.norms.as<float>();
-  a.xnorm = ip ? nullptr : Q.norms.as<float>();
-  a.qscale = Q.scale.as<float>();
+  a.xnorm = ip || !add_xnorm ? nullptr : Q.norms.as<float>() + q0;
+  a.qscale = Q.scale.p ? Q.scale.as<float>() + q0 : nullptr;
   a.bscale = B.scale.as<float>();
   a.out = out;
   a.ldo = ldo;
-  return gemm_launch(MODE_STORE, 0, ip, Q, B, a, st);
+  return gemm_launch(MODE_STORE, 0, ip, Q, B, a, st, q0, qn);
 }
 
 // Top-k (ascending distance / descending inner product) of prepared operands in their
@@ -356,9 +372,12 @@ static gbk_status select_run(const float* xq, const PreparedOperand& Q, const Pr
                              float* D, int64_t* I, cudaStream_t st) {
   gbk_status r;
   const int ntiles = (int)((nb + GEMM_BN - 1) / GEMM_BN);
-  if (k > 512) {
-    // Large k: distance blocks of t_q queries x nb (section 5.1 tiling over queries), each
-    // followed by a row-wise k-selection of the full distances.
+  if (k > 512 || (k > 1 && nb <= 65536)) {
+    // Large k, or k > 1 against a short database (a coarse quantizer): distance blocks
+    // of t_q queries x nb (section 5.1 tiling over queries), each followed by a row-wise
+    // k-selection.  The blocks hold ||y||^2 - 2<x,y> (<x,y> for inner product), the values
+    // the fused path ranks, so both routes select the same neighbours; the query norm is
+    // added to the k winners afterwards.
     const int64_t budget = (int64_t)1 << 31;  // bytes of distance block
     int64_t tq = std::max<int64_t>(GEMM_BM, budget / (4 * nb) / GEMM_BM * GEMM_BM);
     tq = std::min(tq, nq);
@@ -366,13 +385,16 @@ static gbk_status select_run(const float* xq, const PreparedOperand& Q, const Pr
     if ((r = blk.alloc(sizeof(float) * (size_t)(tq * nb), st)) != GBK_OK) return r;
     for (int64_t q0 = 0; q0 < nq; q0 += tq) {
       const int64_t nqb = std::min(tq, nq - q0);
-      PreparedOperand Qb;
-      if ((r = prepare_operand(xq + q0 * d, nqb, d, Q.prec, nqb, 0.f, &Qb, st)) != GBK_OK)
+      if ((r = pairwise_run(Q, B, ip, blk.as<float>(), nb, st, q0, nqb, false)) != GBK_OK)
         return r;
-      if ((r = pairwise_run(Qb, B, ip, blk.as<float>(), nb, st)) != GBK_OK) return r;
       if ((r = kselect_run(blk.as<float>(), nqb, nb, k, ip, D + q0 * k, I + q0 * k, st,
                            nullptr)) != GBK_OK)
         return r;
+    }
+    if (!ip) {
+      add_norm_clamp_kernel<<<(unsigned)((nq * k + 255) / 256), 256, 0, st>>>(
+          D, nq, k, Q.norms.as<float>());
+      GBK_LAUNCH_CHECK();
     }
     return GBK_OK;
   }

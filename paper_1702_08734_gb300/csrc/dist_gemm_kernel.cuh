@@ -265,6 +265,8 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
     uint64_t* myQ = sQ + (half * GEMM_BM + qrow) * GEMM_QSTRIDE;
     float* sY = reinterpret_cast<float*>(smem + lay.y_off) + (warp - 2) * 256;  // norms, scales
     const int lists = args.chunks * EPI;   // candidate lists per query
+    const bool vec_out = MODE == MODE_STORE && (args.ldo & 3) == 0 &&
+                         (reinterpret_cast<uintptr_t>(args.out) & 15) == 0;
     uint32_t gtile = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
@@ -367,11 +369,21 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           const bool ragged = lim < cb + 32;  // columns past nb in this batch (last tile only)
           if (MODE == MODE_STORE) {
             if (qvalid) {
+              if (xn_store >= 0.f) {
 #pragma unroll
-              for (int j = 0; j < 32; j++)
-                if (!ragged || cb + j < lim)
-                  args.out[(int64_t)q * args.ldo + cbase + j] =
-                      xn_store >= 0.f ? fmaxf(dist[j] + xn_store, 0.f) : dist[j];
+                for (int j = 0; j < 32; j++) dist[j] = fmaxf(dist[j] + xn_store, 0.f);
+              }
+              float* orow = args.out + (int64_t)q * args.ldo + cbase;
+              if (!ragged && vec_out) {  // 16-byte stores: 8 per batch instead of 32
+#pragma unroll
+                for (int j4 = 0; j4 < 8; j4++)
+                  reinterpret_cast<float4*>(orow)[j4] =
+                      make_float4(dist[4 * j4], dist[4 * j4 + 1], dist[4 * j4 + 2], dist[4 * j4 + 3]);
+              } else {
+#pragma unroll
+                for (int j = 0; j < 32; j++)
+                  if (!ragged || cb + j < lim) orow[j] = dist[j];
+              }
             }
             return;
           }

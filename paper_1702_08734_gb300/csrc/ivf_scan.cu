@@ -17,6 +17,7 @@
 #include "common.cuh"
 #include "ivf.cuh"
 #include "select_core.cuh"
+#include "sm100.cuh"
 
 namespace gbk {
 
@@ -64,13 +65,14 @@ __global__ void __launch_bounds__(256)
   codes[v * M + m] = (uint8_t)bc;
 }
 
-// T[L][m][c] = ||C_m[c]||^2 + 2 <c_L^m, C_m[c]>  (block per list, thread per (m, c)).
+// T[L][c][m] = ||C_m[c]||^2 + 2 <c_L^m, C_m[c]>  (block per list, thread per (c, m)); the
+// c-major layout makes one list's table a contiguous block whose rows the scan reads whole.
 __global__ void term1_kernel(const float* __restrict__ coarse, const float* __restrict__ pq, int d,
                              int M, float* __restrict__ T) {
   const int L = blockIdx.x;
   const int dsub = d / M;
-  for (int e = threadIdx.x; e < M * 256; e += blockDim.x) {
-    const int m = e / 256, c = e % 256;
+  for (int e = threadIdx.x; e < M * 256; e += blockDim.x) {  // e = c * M + m
+    const int m = e % M, c = e / M;
     const float* C = pq + ((int64_t)m * 256 + c) * dsub;
     const float* cl = coarse + (int64_t)L * d + m * dsub;
     float nn = 0.f, ip = 0.f;
@@ -82,20 +84,33 @@ __global__ void term1_kernel(const float* __restrict__ coarse, const float* __re
   }
 }
 
-// term3[q][m][c] = <x^m, C_m[c]>  (block per query).
-__global__ void term3_kernel(const float* __restrict__ xq, const float* __restrict__ pq, int d,
-                             int M, float* __restrict__ t3) {
-  const int64_t q = blockIdx.x;
+// term3[q][c][m] = <x^m, C_m[c]>.  A block serves T3_QB queries so each codebook row is
+// read once per block (into registers) instead of once per query; thread per (c, m) with m
+// fastest, so the output rows are written contiguously.
+constexpr int T3_QB = 16;
+__global__ void __launch_bounds__(256)
+    term3_kernel(const float* __restrict__ xq, int64_t nq, const float* __restrict__ pq, int d,
+                 int M, float* __restrict__ t3) {
+  const int64_t q0 = (int64_t)blockIdx.x * T3_QB;
+  const int nqb = nq - q0 < T3_QB ? (int)(nq - q0) : T3_QB;
   const int dsub = d / M;
-  __shared__ float xs[1024];
-  for (int t = threadIdx.x; t < d; t += blockDim.x) xs[t] = xq[q * d + t];
+  extern __shared__ float xs[];  // [T3_QB][d]
+  for (int i = threadIdx.x; i < nqb * d; i += blockDim.x) xs[i] = xq[q0 * d + i];
   __syncthreads();
-  for (int e = threadIdx.x; e < M * 256; e += blockDim.x) {
-    const int m = e / 256, c = e % 256;
+  for (int e = threadIdx.x; e < M * 256; e += blockDim.x) {  // e = c * M + m
+    const int m = e % M, c = e / M;
     const float* C = pq + ((int64_t)m * 256 + c) * dsub;
-    float ip = 0.f;
-    for (int t = 0; t < dsub; t++) ip = fmaf(xs[m * dsub + t], C[t], ip);
-    t3[q * M * 256 + e] = ip;
+    float cr[32];
+#pragma unroll
+    for (int t = 0; t < 32; t++) cr[t] = t < dsub ? __ldg(C + t) : 0.f;
+    for (int j = 0; j < nqb; j++) {
+      const float* x = xs + j * d + m * dsub;
+      float ip = 0.f;
+#pragma unroll
+      for (int t = 0; t < 32; t++)
+        if (t < dsub) ip = fmaf(x[t], cr[t], ip);
+      t3[(q0 + j) * M * 256 + e] = ip;
+    }
   }
 }
 
@@ -158,8 +173,8 @@ struct ScanArgs {
   int nprobe, k;
   const int64_t* cl_I;   // [nq][nprobe] probed lists, nearest first (-1 = none)
   const float* cl_D;     // [nq][nprobe] term 2 = ||x - c_L||^2
-  const float* T;        // [nlist][M][256] term 1 (precomputed tables)
-  const float* t3;       // [nq][M][256] term 3
+  const float* T;        // [nlist][256][M] term 1 (precomputed tables)
+  const float* t3;       // [nq][256][M] term 3
   const float* xq;       // direct tables: queries
   const float* coarse;   // direct tables: coarse centroids
   const float* pq;       // direct tables: codebooks [M][256][dsub]
@@ -178,6 +193,7 @@ struct ScanArgs {
   const int64_t* out_off;
   const int64_t* order;
   unsigned long long* counter;
+  uint32_t* status;      // device status word (bounded waits record a timeout here)
 };
 
 // Block per query: for each probed list, build the LUT, stream the codes (one 16-byte code
@@ -190,11 +206,30 @@ __global__ void __launch_bounds__(256)
   using Sel = BlockSelect<THREADS, KP, CAP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* lut = reinterpret_cast<float*>(smem_raw);                  // [256][32]
-  float* t3s = lut + 256 * 32;                                       // [M][256]
-  typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(t3s + M * 256);
+  float* t3s = lut + 256 * 32;                                       // [256][M]
+  float* tst = t3s + M * 256;                                        // [256][M] term 1 of a list
+  typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(tst + M * 256);
   __shared__ int64_t q_sh;
-  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ uint64_t t_bar;  // completion of the term-1 bulk copy
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rot = lane % M, h = lane / M;
+  constexpr uint32_t TBYTES = M * 256 * sizeof(float);
+  uint32_t t_phase = 0;
+  if (tid == 0) {
+    sm100::mbar_init(&t_bar, 1);
+    abort_flag = 0;
+    sm100::fence_mbar_init();
+  }
+  __syncthreads();
+  // one thread starts the copy of list L's term-1 table into tst
+  auto copy_T = [&](int64_t L) {
+    if (tid == 0) {
+      sm100::fence_proxy_async_smem();
+      sm100::mbar_arrive_expect_tx(&t_bar, TBYTES);
+      sm100::bulk_load(tst, a.T + L * M * 256, TBYTES, &t_bar);
+    }
+  };
   for (int64_t it = blockIdx.x;; it += gridDim.x) {
     // next query: static (one block per query) or from the persistent work queue
     if (a.counter) {
@@ -217,60 +252,104 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     ValueFilter f;
     f.set(NAN_KEY, false);
-    for (int p = 0; p < npq; p++) {
-      const int64_t L = a.cl_I[q * a.nprobe + p];
-      if (L < 0) continue;  // uniform across the block
-      const float term2 = a.cl_D[q * a.nprobe + p];
-      __syncthreads();  // previous list's look-ups are done
-      if (!a.direct) {
-        const float* TL = a.T + L * M * 256;
-        for (int e = tid; e < M * 256; e += THREADS) {
-          const int m = e >> 8, c = e & 255;
-          const float v = fmaf(-2.f, t3s[e], __ldg(TL + e));
-#pragma unroll
-          for (int hh = 0; hh < 32 / M; hh++) lut[c * 32 + hh * M + m] = v;
-        }
+    // Software pipeline across the probed lists: the term-1 table of list p+1 is copied
+    // into shared memory (bulk copy) and the first codes of each list are loaded into
+    // registers while earlier work proceeds, so no global-memory latency is exposed once
+    // per list.
+    int64_t Lc = -1, o0c = 0, o1c = 0;  // current list
+    auto fetch_list = [&](int p, int64_t& L, int64_t& o0, int64_t& o1) {
+      L = p < npq ? a.cl_I[q * a.nprobe + p] : -1;
+      if (L >= 0) {
+        o0 = a.list_off[L];
+        o1 = a.list_off[L + 1];
       } else {
-        const int dsub = a.d / M;
-        for (int e = tid; e < M * 256; e += THREADS) {
-          const int m = e >> 8, c = e & 255;
-          const float* C = a.pq + ((int64_t)m * 256 + c) * dsub;
-          float v = 0.f;
-          for (int t = 0; t < dsub; t++) {
-            const float r = a.xq[q * a.d + m * dsub + t] - a.coarse[L * a.d + m * dsub + t];
-            const float e2 = r - C[t];
-            v = fmaf(e2, e2, v);
-          }
+        o0 = o1 = 0;
+      }
+    };
+    constexpr int U = 4;                 // codes per thread per step
+    constexpr int STEP = THREADS * U;
+    uint32_t wn[U][M / 4];               // codes of the next step, in flight
+    auto fetch_codes = [&](int64_t b0, int64_t o1) {
 #pragma unroll
-          for (int hh = 0; hh < 32 / M; hh++) lut[c * 32 + hh * M + m] = v;
+      for (int u = 0; u < U; u++) {
+        const int64_t i = b0 + u * THREADS + tid;
+        if (i < o1) load_code<M>(a.codes, i, wn[u]);
+      }
+    };
+    fetch_list(0, Lc, o0c, o1c);
+    if (Lc >= 0 && !a.direct) copy_T(Lc);
+    bool ok = true;
+    for (int p = 0; p < npq && ok; p++) {
+      const int64_t L = Lc, o0 = o0c, o1 = o1c;
+      if (L >= 0) fetch_codes(o0, o1);
+      __syncthreads();  // previous list's look-ups are done
+      if (L >= 0) {
+        // LUT[c][h*M + m] = T[L][c][m] - 2 term3[c][m]: warp w fills rows c of its 32; lane l
+        // writes word c*32 + l (copy h = l / M of sub-table m = l % M): conflict-free.
+        if (!a.direct) {
+          ok = sm100::mbar_wait(&t_bar, t_phase, a.status, (volatile int*)&abort_flag);
+          t_phase ^= 1u;
+          if (ok) {
+#pragma unroll 4
+            for (int i = 0; i < 32; i++) {
+              const int c = warp * 32 + i;
+              const int e = c * M + rot;
+              lut[c * 32 + lane] = fmaf(-2.f, t3s[e], tst[e]);
+            }
+          }
+        } else {
+          const int dsub = a.d / M;
+          for (int i = 0; i < 32; i++) {
+            const int c = warp * 32 + i, m = rot;
+            const float* C = a.pq + ((int64_t)m * 256 + c) * dsub;
+            float v = 0.f;
+            for (int t = 0; t < dsub; t++) {
+              const float r = a.xq[q * a.d + m * dsub + t] - a.coarse[L * a.d + m * dsub + t];
+              const float e2 = r - C[t];
+              v = fmaf(e2, e2, v);
+            }
+            lut[c * 32 + lane] = v;
+          }
         }
       }
-      __syncthreads();
-      const int64_t o0 = a.list_off[L], o1 = a.list_off[L + 1];
+      const float term2 = L >= 0 ? a.cl_D[q * a.nprobe + p] : 0.f;
+      fetch_list(p + 1, Lc, o0c, o1c);  // next list's extent
+      __syncthreads();                   // LUT complete, tst consumed
+      if (Lc >= 0 && !a.direct && ok) copy_T(Lc);
+      if (L < 0 || !ok) continue;        // uniform across the block
       const float base = a.direct ? 0.f : term2;
-      for (int64_t b0 = o0; b0 < o1; b0 += THREADS) {
-        const int64_t i = b0 + tid;
-        float dist = 0.f;
-        bool valid = i < o1;
-        if (valid) {
-          uint32_t w[M / 4];
-          load_code<M>(a.codes, i, w);
-          rotate_code<M>(w, rot);
-          float acc = 0.f;
+      for (int64_t b0 = o0; b0 < o1; b0 += STEP) {
+        uint32_t w[U][M / 4];
 #pragma unroll
-          for (int st = 0; st < M; st++) {
-            const uint32_t c = (w[st >> 2] >> ((st & 3) * 8)) & 255u;
-            const int m = (st + rot) & (M - 1);
-            acc += lut[c * 32 + h * M + m];
+        for (int u = 0; u < U; u++)
+#pragma unroll
+          for (int j = 0; j < M / 4; j++) w[u][j] = wn[u][j];
+        if (b0 + STEP < o1) fetch_codes(b0 + STEP, o1);
+        uint32_t mask = 0;
+        uint64_t cc[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int64_t i = b0 + u * THREADS + tid;
+          cc[u] = ~0ull;
+          if (i < o1) {
+            rotate_code<M>(w[u], rot);
+            float acc = 0.f;
+#pragma unroll
+            for (int st = 0; st < M; st++) {
+              const uint32_t c = (w[u][st >> 2] >> ((st & 3) * 8)) & 255u;
+              const int m = (st + rot) & (M - 1);
+              acc += lut[c * 32 + h * M + m];
+            }
+            const float dist = base + acc;
+            if (f.pass(dist)) {
+              mask |= 1u << u;
+              cc[u] = composite(ordered_key(dist, false), (uint32_t)i);
+            }
           }
-          dist = base + acc;
         }
-        const bool pass = valid && f.pass(dist);
-        uint64_t cc[1];
-        if (pass) cc[0] = composite(ordered_key(dist, false), (uint32_t)i);
-        Sel::template push<1>(s, pass ? 1u : 0u, cc);
+        Sel::template push<U>(s, mask, cc);
         __syncthreads();
-        if (s.n_buf > CAP - THREADS) {
+        if (s.n_buf > CAP - STEP) {
           Sel::compact(s, kq);
           f.set((uint32_t)(s.thr >> 32), false);
         }
@@ -293,7 +372,7 @@ __global__ void __launch_bounds__(256)
 template <int M, int KP>
 static gbk_status launch_scan(const ScanArgs& a, cudaStream_t st) {
   using Sel = BlockSelect<256, KP, 4096>;
-  const size_t smem = sizeof(float) * (256 * 32 + M * 256) + sizeof(typename Sel::Smem);
+  const size_t smem = sizeof(float) * (256 * 32 + 2 * M * 256) + sizeof(typename Sel::Smem);
   auto kern = ivf_scan_kernel<M, KP>;
   static bool attr = false;
   if (!attr) {
@@ -324,7 +403,8 @@ gbk_status ivf_scan_run(int M, int64_t nq, int nprobe, int k, const int64_t* cl_
                         unsigned long long* counter) {
   if (nq == 0) return GBK_OK;
   ScanArgs a{nq, nprobe, k, cl_I, cl_D, T, t3, xq, coarse, pq, d, direct ? 1 : 0, list_off,
-             codes, ids, D, I, kq, npq, out_off, order, counter};
+             codes, ids, D, I, kq, npq, out_off, order, counter, device_status()};
+  if (!a.status) return set_error(GBK_ECUDA, "device status word unavailable");
   ProfScope prof("ivf_scan", st);
   if (M == 8) return scan_k<8>(a, st);
   if (M == 16) return scan_k<16>(a, st);
@@ -390,7 +470,14 @@ gbk_status term3_run(const float* xq, int64_t nq, const float* pq, int d, int M,
   if (nq == 0) return GBK_OK;
   if (d > 1024) return set_error(GBK_EUNSUPPORTED, "term 3 supports d <= 1024");
   ProfScope prof("term3", st);
-  term3_kernel<<<(unsigned)nq, 256, 0, st>>>(xq, pq, d, M, t3);
+  const size_t smem = sizeof(float) * T3_QB * d;  // <= 64 KB
+  static bool attr = false;
+  if (!attr) {
+    GBK_CUDA_CHECK(cudaFuncSetAttribute(term3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(float) * T3_QB * 1024)));
+    attr = true;
+  }
+  term3_kernel<<<(unsigned)((nq + T3_QB - 1) / T3_QB), 256, smem, st>>>(xq, nq, pq, d, M, t3);
   GBK_LAUNCH_CHECK();
   return GBK_OK;
 }

@@ -29,9 +29,12 @@ struct KnnPlan {
 gbk_status prepare_operand(const float* x, int64_t n, int d, int prec, int64_t nrows_pad,
                            float pad_norm, PreparedOperand* out, cudaStream_t st);
 
-// Full pairwise squared L2 distances (clamped at 0) or inner products, out[q*ldo + i].
+// Full pairwise squared L2 distances (clamped at 0) or inner products, out[q*ldo + i],
+// for query rows [q0, q0 + qn) (all rows when qn < 0).  add_xnorm = false leaves out the
+// query norm (and the clamp): ||y||^2 - 2<x,y>.
 gbk_status pairwise_run(const PreparedOperand& Q, const PreparedOperand& B, bool ip, float* out,
-                        int64_t ldo, cudaStream_t st);
+                        int64_t ldo, cudaStream_t st, int64_t q0 = 0, int64_t qn = -1,
+                        bool add_xnorm = true);
 
 // Exact k-NN (arguments validated by the caller).
 gbk_status knn_run(const float* xq, int64_t nq, const float* xb, int64_t nb, int d, int k,
