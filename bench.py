@@ -305,7 +305,12 @@ def run_learned(args):
     for nm, tt in g.profile_read():
         by.setdefault(nm, []).append(tt)
     _, r10 = recall_stats(g, I.view(nq, 10), Igt)
-    learned = {"qps": nq / (ms / 1e3), "R10@10": r10, "nprobe_cap": cap,
+    # the same search captured once as a CUDA graph and replayed (serving form)
+    gr = g.BatchedGraph(ix, xq, kq, 10, None, cap, mlp=net)
+    ms_graph, _ = time_search(g, gr.launch, args.steps)
+    assert torch.equal(gr.I, I)
+    learned = {"qps": nq / (ms_graph / 1e3), "qps_eager": nq / (ms / 1e3), "R10@10": r10,
+               "nprobe_cap": cap,
                "mean_nprobe": float(used.float().mean().item()),
                "kernel_ms": {kk: sum(v) / len(v) for kk, v in by.items()}}
     # fixed-nprobe q/s at the learned recall (log-linear interpolation between neighbours)

@@ -87,14 +87,14 @@ __global__ void term1_kernel(const float* __restrict__ coarse, const float* __re
 // term3[q][c][m] = <x^m, C_m[c]>.  A block serves T3_QB queries so each codebook row is
 // read once per block (into registers) instead of once per query; thread per (c, m) with m
 // fastest, so the output rows are written contiguously.
-constexpr int T3_QB = 16;
+constexpr int T3_QB = 8;
 __global__ void __launch_bounds__(256)
     term3_kernel(const float* __restrict__ xq, int64_t nq, const float* __restrict__ pq, int d,
                  int M, float* __restrict__ t3) {
   const int64_t q0 = (int64_t)blockIdx.x * T3_QB;
   const int nqb = nq - q0 < T3_QB ? (int)(nq - q0) : T3_QB;
   const int dsub = d / M;
-  extern __shared__ float xs[];  // [T3_QB][d]
+  extern __shared__ __align__(16) float xs[];  // [T3_QB][d]
   for (int i = threadIdx.x; i < nqb * d; i += blockDim.x) xs[i] = xq[q0 * d + i];
   __syncthreads();
   for (int e = threadIdx.x; e < M * 256; e += blockDim.x) {  // e = c * M + m
@@ -103,12 +103,26 @@ __global__ void __launch_bounds__(256)
     float cr[32];
 #pragma unroll
     for (int t = 0; t < 32; t++) cr[t] = t < dsub ? __ldg(C + t) : 0.f;
+    const bool v4 = (dsub & 3) == 0 && (d & 3) == 0;  // 16-byte reads of the sub-vector
     for (int j = 0; j < nqb; j++) {
       const float* x = xs + j * d + m * dsub;
       float ip = 0.f;
+      if (v4) {
 #pragma unroll
-      for (int t = 0; t < 32; t++)
-        if (t < dsub) ip = fmaf(x[t], cr[t], ip);
+        for (int t4 = 0; t4 < 8; t4++) {
+          if (4 * t4 < dsub) {
+            const float4 xv = reinterpret_cast<const float4*>(x)[t4];
+            ip = fmaf(xv.x, cr[4 * t4], ip);
+            ip = fmaf(xv.y, cr[4 * t4 + 1], ip);
+            ip = fmaf(xv.z, cr[4 * t4 + 2], ip);
+            ip = fmaf(xv.w, cr[4 * t4 + 3], ip);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 32; t++)
+          if (t < dsub) ip = fmaf(x[t], cr[t], ip);
+      }
       t3[(q0 + j) * M * 256 + e] = ip;
     }
   }

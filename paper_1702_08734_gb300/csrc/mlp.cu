@@ -20,47 +20,8 @@ namespace gbk {
 
 namespace {
 
-constexpr int TILE = 16;
-
 __device__ __forceinline__ float bf16r(float x) {
   return __bfloat162float(__float2bfloat16_rn(x));
-}
-
-// C[M][N] = sum_k A(m, k) * B(k, n) (+ bias[n]) (relu optional); accumulate into C when acc.
-// A(m,k) = TA ? A[k*lda + m] : A[m*lda + k];  B(k,n) = TB ? B[n*ldb + k] : B[k*ldb + n].
-// RB: round B elements to BF16 (weights).  Fixed summation order over k.
-template <bool TA, bool TB, bool RB>
-__global__ void gemm16(int M, int N, int K, const float* __restrict__ A, int lda,
-                       const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
-                       const float* __restrict__ bias, int relu, int acc) {
-  __shared__ float As[TILE][TILE + 1];
-  __shared__ float Bs[TILE][TILE + 1];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int m = blockIdx.y * TILE + ty, n = blockIdx.x * TILE + tx;
-  float s = 0.f;
-  for (int k0 = 0; k0 < K; k0 += TILE) {
-    {
-      const int mm = blockIdx.y * TILE + ty, kk = k0 + tx;
-      As[ty][tx] = (mm < M && kk < K) ? (TA ? A[(int64_t)kk * lda + mm] : A[(int64_t)mm * lda + kk])
-                                      : 0.f;
-    }
-    {
-      const int kk = k0 + ty, nn = blockIdx.x * TILE + tx;
-      float b = (kk < K && nn < N) ? (TB ? B[(int64_t)nn * ldb + kk] : B[(int64_t)kk * ldb + nn])
-                                   : 0.f;
-      Bs[ty][tx] = RB ? bf16r(b) : b;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < TILE; t++) s = fmaf(As[ty][t], Bs[t][tx], s);
-    __syncthreads();
-  }
-  if (m < M && n < N) {
-    if (bias) s += bias[n];
-    if (relu) s = fmaxf(s, 0.f);
-    float* c = C + (int64_t)m * ldc + n;
-    *c = acc ? *c + s : s;
-  }
 }
 
 // Row-wise softmax cross-entropy: dz = (softmax(z) - onehot(y)) / B; loss_row out.
@@ -137,11 +98,71 @@ __global__ void loss_sum_kernel(const float* __restrict__ lr, int64_t B, float* 
 
 int grid1(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
 
+// C[M][N] = sum_k A(m, k) * B(k, n) (+ bias[n]) (relu optional); accumulate into C when acc.
+// A(m,k) = TA ? A[k*lda + m] : A[m*lda + k];  B(k,n) = TB ? B[n*ldb + k] : B[k*ldb + n].
+// RB: round B elements to BF16 (weights).  Each output is summed over k in increasing
+// order with fmaf (a fixed order).  64 x 64 block tiles, 4 x 4 outputs per thread: 16 FMAs
+// per pair of 16-byte shared-memory reads.
+constexpr int BT = 64, BK = 16;
+template <bool TA, bool TB, bool RB>
+__global__ void __launch_bounds__(256)
+    gemm64(int M, int N, int K, const float* __restrict__ A, int lda, const float* __restrict__ B,
+           int ldb, float* __restrict__ C, int ldc, const float* __restrict__ bias, int relu,
+           int acc) {
+  __shared__ __align__(16) float As[BK][BT + 4];
+  __shared__ __align__(16) float Bs[BK][BT + 4];
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int m0 = blockIdx.y * BT, n0 = blockIdx.x * BT;
+  float s[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const int i = t + 256 * r;
+      const int km = TA ? i / BT : i % BK, mm = TA ? i % BT : i / BK;
+      const int gm = m0 + mm, gk = k0 + km;
+      As[km][mm] = (gm < M && gk < K) ? (TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk])
+                                      : 0.f;
+      const int kn = TB ? i % BK : i / BT, nn = TB ? i / BK : i % BT;
+      const int gn = n0 + nn, gk2 = k0 + kn;
+      const float b = (gn < N && gk2 < K) ? (TB ? B[(int64_t)gn * ldb + gk2] : B[(int64_t)gk2 * ldb + gn])
+                                          : 0.f;
+      Bs[kn][nn] = RB ? bf16r(b) : b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; kk++) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) s[i][j] = fmaf(av[i], bv[j], s[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const int m = m0 + ty * 4 + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int n = n0 + tx * 4 + j;
+      if (n >= N) continue;
+      float v = s[i][j];
+      if (bias) v += bias[n];
+      if (relu) v = fmaxf(v, 0.f);
+      float* c = C + (int64_t)m * ldc + n;
+      *c = acc ? *c + v : v;
+    }
+  }
+}
+
 template <bool TA, bool TB, bool RB>
 void mm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
         const float* bias, bool relu, bool acc, cudaStream_t st) {
-  dim3 blk(TILE, TILE), grd((N + TILE - 1) / TILE, (M + TILE - 1) / TILE);
-  gemm16<TA, TB, RB><<<grd, blk, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu ? 1 : 0,
+  dim3 grd((N + BT - 1) / BT, (M + BT - 1) / BT);
+  gemm64<TA, TB, RB><<<grd, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu ? 1 : 0,
                                           acc ? 1 : 0);
 }
 
