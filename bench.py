@@ -313,6 +313,25 @@ def run_learned(args):
                "nprobe_cap": cap,
                "mean_nprobe": float(used.float().mean().item()),
                "kernel_ms": {kk: sum(v) / len(v) for kk, v in by.items()}}
+    # k-NN graph over all indexed vectors (section 6.5), k = 10, learned route and fixed
+    # nprobe 1; 10-R@10 on 10,000 sampled nodes against exact search (self excluded)
+    samp = torch.from_numpy(np.unique(datagen.randint(505, 0, 10000, xb.shape[0]))).cuda()
+    _, Ie = g.knn_brute(xb[samp].contiguous(), xb, 11)
+    Ie = Ie.cpu().numpy()
+    sid = samp.cpu().numpy()
+    gt = np.stack([np.concatenate([r[r != s_], r[r == s_]])[:10] for r, s_ in zip(Ie, sid)])
+    gt = torch.from_numpy(gt).cuda()
+    graph = {}
+    for name, kw in (("learned", {"mlp": net}), ("fixed_nprobe1", {})):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, G = g.knn_graph(ix, xb, 10, cap if kw else 1, distances=False, **kw)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        c = torch.empty(samp.shape[0], dtype=torch.int32, device="cuda")
+        g.recall_counts(G[samp].contiguous(), gt, c)
+        graph[name] = {"seconds": el, "nodes": int(xb.shape[0]),
+                       "R10@10_sampled": float(c.float().mean().item()) / 10}
     # fixed-nprobe q/s at the learned recall (log-linear interpolation between neighbours)
     eq = None
     for a, b in zip(fixed, fixed[1:]):
@@ -321,7 +340,8 @@ def run_learned(args):
             eq = float(np.exp(np.log(a["qps"]) * (1 - w) + np.log(b["qps"]) * w))
     print(json.dumps({"workload": "learned nprobe, nb=%d, %d training queries" % (args.ivf_n, ntr),
                       **t, "label_hist": hist, "loss_per_epoch": losses, "fixed": fixed,
-                      "learned": learned, "fixed_qps_at_learned_recall": eq,
+                      "learned": learned, "knn_graph_k10": graph,
+                      "fixed_qps_at_learned_recall": eq,
                       "speedup_at_equal_recall": learned["qps"] / eq if eq else None}), flush=True)
 
 

@@ -335,6 +335,21 @@ gbk_status gbk_recall_counts(const int64_t* I, const int64_t* G, int64_t nq, int
 gbk_status gbk_nprobe_features(const float* xq, int64_t nq, int32_t d, const float* coarse_dist,
                                int32_t tau, int32_t nfeat, float* F, void* stream);
 
+/* ------------------------------------------------------------------ k-NN graph */
+
+/* The k-NN graph of section 6.5: every one of the n vectors x [n][d] (device, normally the
+ * indexed vectors) is searched in the index for k + 1 neighbours with IVFADC (fixed nprobe,
+ * or with `mlp` non-NULL the learned per-query nprobe capped at `nprobe`, as in
+ * gbk_ivfpq_search_batched), and its own id is dropped: the first occurrence of
+ * self_ids[i] (device int64 [n], or NULL for running numbers 0..n-1) in row i is removed;
+ * if absent, the first k entries are kept.  Another vector with equal coordinates but a
+ * different id stays a neighbour.  G [n][k] int64 neighbour ids, GD [n][k] squared ADC
+ * distances (may be NULL), ascending.  Queries are processed `batch` at a time (<= 0:
+ * 2^20); scratch is batch * (k + 1) * 12 bytes.  1 <= k < GBK_MAX_K. */
+gbk_status gbk_ivfpq_knn_graph(gbk_index* index, const float* x, int64_t n,
+                               const int64_t* self_ids, int32_t k, int32_t nprobe, gbk_mlp* mlp,
+                               int64_t batch, float* GD, int64_t* G, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

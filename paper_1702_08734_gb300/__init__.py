@@ -404,6 +404,7 @@ _SIGNATURES.update({
     "gbk_ivfpq_batched_graph": [_vp, _vp, _i64, _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp,
                                 _vp, _vp],
     "gbk_graph_launch": [_vp, _vp],
+    "gbk_ivfpq_knn_graph": [_vp, _vp, _i64, _vp, _i32, _i32, _vp, _i64, _vp, _vp, _vp],
 })
 
 
@@ -447,6 +448,19 @@ def ivfpq_search_batched(index, xq, k_per_q, max_k, nprobe_per_q=None, max_nprob
           int(max_nprobe), mlp._h if mlp is not None else None, _ptr(off), _ptr(D), _ptr(I),
           _ptr(used), _stream())
     return D, I, off, used
+
+
+def knn_graph(index, x, k, nprobe, mlp=None, self_ids=None, batch=0, distances=True):
+    """k-NN graph (section 6.5): each row of x searched for k+1 neighbours, its own id
+    (self_ids[i], default i) removed.  Returns (GD, G) [n][k] (GD None if not requested)."""
+    _dev(x, torch.float32, "x")
+    n = x.shape[0]
+    G = torch.empty((n, k), dtype=torch.int64, device=x.device)
+    GD = torch.empty((n, k), dtype=torch.float32, device=x.device) if distances else None
+    sid = self_ids.to(torch.int64).contiguous() if self_ids is not None else None
+    _call("gbk_ivfpq_knn_graph", index._h, _ptr(x), n, _ptr(sid), int(k), int(nprobe),
+          mlp._h if mlp is not None else None, int(batch), _ptr(GD), _ptr(G), _stream())
+    return GD, G
 
 
 class BatchedGraph:

@@ -98,6 +98,10 @@ struct gbk_index {
 
 namespace gbk {
 
+// Algorithm 4 for a validated, finalized index (below).
+gbk_status search_run(gbk_index* ix, const float* xq, int64_t nq, int k, int nprobe, float* D,
+                      int64_t* I, cudaStream_t st);
+
 namespace {
 
 __global__ void residual_kernel(const float* __restrict__ x, int64_t n, int d,
@@ -341,6 +345,16 @@ gbk_status gbk_ivfpq_search(gbk_index* ix, const float* xq, int64_t nq, int32_t 
   cudaStream_t st = as_stream(stream);
   gbk_status r;
   if ((r = finalize(ix, st)) != GBK_OK) return r;
+  return gbk::search_run(ix, xq, nq, k, nprobe, D, I, st);
+}
+
+}  // extern "C"
+
+namespace gbk {
+// Algorithm 4 for a validated, finalized index.
+gbk_status search_run(gbk_index* ix, const float* xq, int64_t nq, int k, int nprobe, float* D,
+                      int64_t* I, cudaStream_t st) {
+  gbk_status r;
   Scratch clD, clI, t3;
   if ((r = clD.alloc(sizeof(float) * (size_t)nq * nprobe, st)) != GBK_OK) return r;
   if ((r = clI.alloc(sizeof(int64_t) * (size_t)nq * nprobe, st)) != GBK_OK) return r;
@@ -360,6 +374,8 @@ gbk_status gbk_ivfpq_search(gbk_index* ix, const float* xq, int64_t nq, int32_t 
                       direct, ix->list_off.as<int64_t>(), ix->codes.as<uint8_t>(),
                       ix->ids.as<int64_t>(), D, I, st);
 }
+}  // namespace gbk
+extern "C" {
 
 gbk_status gbk_ivfpq_info(gbk_index* ix, int64_t* ntotal, int32_t* nlist, int32_t* d, int32_t* M,
                           void* stream) {
@@ -616,6 +632,98 @@ gbk_status gbk_nprobe_features(const float* xq, int64_t nq, int32_t d, const flo
   nprobe_features_kernel<<<(unsigned)nq, 128, 0, as_stream(stream)>>>(xq, nq, d, coarse_dist, tau,
                                                                       nfeat, F);
   GBK_LAUNCH_CHECK();
+  return GBK_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ k-NN graph (section 6.5)
+
+namespace gbk {
+namespace {
+
+// Row r of the (k+1)-NN lists without the query's own id: the first occurrence of `self`
+// is dropped (a duplicate vector with another id stays a neighbour); when the row does not
+// contain it, its first k entries are kept.
+__global__ void drop_self_kernel(const float* __restrict__ D1, const int64_t* __restrict__ I1,
+                                 int64_t n, int k, const int64_t* __restrict__ self_ids,
+                                 int64_t id0, float* __restrict__ GD, int64_t* __restrict__ G) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int64_t self = self_ids ? self_ids[r] : id0 + r;
+  const float* d = D1 + r * (k + 1);
+  const int64_t* id = I1 + r * (k + 1);
+  bool dropped = false;
+  int j = 0;
+  for (int i = 0; i <= k && j < k; i++) {
+    if (!dropped && id[i] == self) {
+      dropped = true;
+      continue;
+    }
+    if (GD) GD[r * k + j] = d[i];
+    G[r * k + j] = id[i];
+    j++;
+  }
+}
+
+__global__ void fill_graph_args_kernel(int64_t n, int kk, int32_t* kq, int64_t* off) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) kq[i] = kk;
+  if (i <= n) off[i] = i * kk;
+}
+
+}  // namespace
+}  // namespace gbk
+
+extern "C" {
+
+gbk_status gbk_ivfpq_knn_graph(gbk_index* ix, const float* x, int64_t n, const int64_t* self_ids,
+                               int32_t k, int32_t nprobe, gbk_mlp* mlp, int64_t batch,
+                               float* GD, int64_t* G, void* stream) {
+  clear_error();
+  GBK_REQUIRE(ix && ix->trained, "gbk_ivfpq_knn_graph: index missing or not trained");
+  GBK_REQUIRE(k >= 1 && k < GBK_MAX_K, "gbk_ivfpq_knn_graph: k out of [1, %d)", GBK_MAX_K);
+  GBK_REQUIRE(nprobe >= 1 && nprobe <= ix->nlist && nprobe <= GBK_MAX_K,
+              "gbk_ivfpq_knn_graph: nprobe out of range");
+  GBK_REQUIRE(n >= 0, "gbk_ivfpq_knn_graph: n < 0");
+  if (n == 0) return GBK_OK;
+  GBK_REQUIRE(x && G, "gbk_ivfpq_knn_graph: NULL pointer");
+  if (mlp) {
+    GBK_REQUIRE(ix->nlist >= 64, "learned nprobe needs nlist >= 64 (64 coarse-distance features)");
+    GBK_REQUIRE(gbk::mlp_inputs(mlp) == ix->d + 64,
+                "learned nprobe: network inputs must be d + 64 = %d", ix->d + 64);
+  }
+  if (batch <= 0) batch = int64_t(1) << 20;
+  batch = std::min<int64_t>(batch, std::min<int64_t>(n, (int64_t(1) << 31) / (k + 1) - 1));
+  cudaStream_t st = as_stream(stream);
+  gbk_status r;
+  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  const int kk = k + 1;
+  Scratch D1, I1, kq, off;
+  if ((r = D1.alloc(sizeof(float) * (size_t)batch * kk, st)) != GBK_OK) return r;
+  if ((r = I1.alloc(sizeof(int64_t) * (size_t)batch * kk, st)) != GBK_OK) return r;
+  if (mlp) {
+    if ((r = kq.alloc(sizeof(int32_t) * (size_t)batch, st)) != GBK_OK) return r;
+    if ((r = off.alloc(sizeof(int64_t) * (size_t)(batch + 1), st)) != GBK_OK) return r;
+    gbk::fill_graph_args_kernel<<<(unsigned)((batch + 256) / 256), 256, 0, st>>>(
+        batch, kk, kq.as<int32_t>(), off.as<int64_t>());
+    GBK_LAUNCH_CHECK();
+  }
+  ProfScope prof("knn_graph", st);
+  for (int64_t b0 = 0; b0 < n; b0 += batch) {
+    const int64_t nb = std::min(batch, n - b0);
+    const float* xb = x + b0 * ix->d;
+    if (mlp)
+      r = gbk::batched_run(ix, xb, nb, kq.as<int32_t>(), kk, nullptr, nprobe, mlp,
+                           off.as<int64_t>(), D1.as<float>(), I1.as<int64_t>(), nullptr, st);
+    else
+      r = gbk::search_run(ix, xb, nb, kk, nprobe, D1.as<float>(), I1.as<int64_t>(), st);
+    if (r != GBK_OK) return r;
+    gbk::drop_self_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(
+        D1.as<float>(), I1.as<int64_t>(), nb, k, self_ids ? self_ids + b0 : nullptr, b0,
+        GD ? GD + b0 * k : nullptr, G + b0 * k);
+    GBK_LAUNCH_CHECK();
+  }
   return GBK_OK;
 }
 
