@@ -335,6 +335,27 @@ gbk_status gbk_recall_counts(const int64_t* I, const int64_t* G, int64_t nq, int
 gbk_status gbk_nprobe_features(const float* xq, int64_t nq, int32_t d, const float* coarse_dist,
                                int32_t tau, int32_t nfeat, float* F, void* stream);
 
+/* ------------------------------------------------------------------ scan autotuning */
+
+/* Launch shape of the list scan (results never depend on it): codes each thread loads per
+ * step (2, 4 or 8; default 4) and resident blocks per SM in the persistent mixed-batch mode
+ * (1..8; default 2).  GBK_EINVAL outside those sets. */
+gbk_status gbk_ivfpq_set_tuning(gbk_index* index, int32_t codes_per_thread,
+                                int32_t blocks_per_sm);
+gbk_status gbk_ivfpq_get_tuning(const gbk_index* index, int32_t* codes_per_thread,
+                                int32_t* blocks_per_sm);
+
+/* Times gbk_ivfpq_search_batched on this batch (arguments as there) for every codes per
+ * thread in {2, 4, 8} x blocks per SM in {1..4}: one untimed run, then `reps` (< 1: 3) runs
+ * timed with CUDA events on `stream`, and keeps the fastest shape in the index.  D and I
+ * hold the batch's results afterwards.  Synchronises `stream`.  *best_ms (host, may be
+ * NULL): mean milliseconds per batch of the chosen shape.  Not part of the paper. */
+gbk_status gbk_ivfpq_autotune(gbk_index* index, const float* xq, int64_t nq,
+                              const int32_t* k_per_q, int32_t max_k,
+                              const int32_t* nprobe_per_q, int32_t max_nprobe, gbk_mlp* mlp,
+                              const int64_t* out_offsets, float* D, int64_t* I, int32_t reps,
+                              float* best_ms, void* stream);
+
 /* ------------------------------------------------------------------ k-NN graph */
 
 /* The k-NN graph of section 6.5: every one of the n vectors x [n][d] (device, normally the

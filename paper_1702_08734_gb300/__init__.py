@@ -405,7 +405,34 @@ _SIGNATURES.update({
                                 _vp, _vp],
     "gbk_graph_launch": [_vp, _vp],
     "gbk_ivfpq_knn_graph": [_vp, _vp, _i64, _vp, _i32, _i32, _vp, _i64, _vp, _vp, _vp],
+    "gbk_ivfpq_set_tuning": [_vp, _i32, _i32],
+    "gbk_ivfpq_get_tuning": [_vp, _vp, _vp],
+    "gbk_ivfpq_autotune": [_vp, _vp, _i64, _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _i32, _vp,
+                           _vp],
 })
+
+
+def ivfpq_set_tuning(index, codes_per_thread: int, blocks_per_sm: int):
+    _call("gbk_ivfpq_set_tuning", index._h, int(codes_per_thread), int(blocks_per_sm))
+
+
+def ivfpq_get_tuning(index):
+    u, b = ctypes.c_int32(), ctypes.c_int32()
+    _call("gbk_ivfpq_get_tuning", index._h, ctypes.byref(u), ctypes.byref(b))
+    return u.value, b.value
+
+
+def ivfpq_autotune(index, xq, k_per_q, max_k, nprobe_per_q=None, max_nprobe=256, mlp=None,
+                   reps=3):
+    """Time the mixed-batch search over the scan's launch shapes and keep the fastest in the
+    index.  Returns ((codes_per_thread, blocks_per_sm), ms per batch)."""
+    nq, kq, off, D, I, used, npq = _batched_args(index, xq, k_per_q, max_k, nprobe_per_q,
+                                                 max_nprobe, mlp)
+    ms = ctypes.c_float()
+    _call("gbk_ivfpq_autotune", index._h, _ptr(xq), nq, _ptr(kq), int(max_k), _ptr(npq),
+          int(max_nprobe), mlp._h if mlp is not None else None, _ptr(off), _ptr(D), _ptr(I),
+          int(reps), ctypes.byref(ms), _stream())
+    return ivfpq_get_tuning(index), ms.value
 
 
 def recall_counts(I: torch.Tensor, G: torch.Tensor, out: torch.Tensor):

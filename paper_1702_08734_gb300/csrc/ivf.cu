@@ -17,7 +17,8 @@ gbk_status ivf_scan_run(int M, int64_t nq, int nprobe, int k, const int64_t* cl_
                         const int64_t* list_off, const uint8_t* codes, const int64_t* ids,
                         float* D, int64_t* I, cudaStream_t st, const int32_t* kq = nullptr,
                         const int32_t* npq = nullptr, const int64_t* out_off = nullptr,
-                        const int64_t* order = nullptr, unsigned long long* counter = nullptr);
+                        const int64_t* order = nullptr, unsigned long long* counter = nullptr,
+                        ScanTuning tun = ScanTuning());
 gbk_status scan_cost_run(const int64_t* cl_I, int64_t nq, int nprobe, const int32_t* npq,
                          const int64_t* off, int32_t* key, cudaStream_t st);
 gbk_status pq_encode_run(const float* x, int64_t n, int d, int M, const float* coarse,
@@ -83,6 +84,7 @@ struct gbk_index {
   int64_t ntotal = 0;
   bool dirty = true;
   int64_t max_list = 0;
+  gbk::ScanTuning tuning;  // list-scan launch shape (gbk_ivfpq_autotune / set_tuning)
   ~gbk_index() {
     coarse.release();
     pq.release();
@@ -372,7 +374,8 @@ gbk_status search_run(gbk_index* ix, const float* xq, int64_t nq, int k, int npr
   return ivf_scan_run(ix->M, nq, nprobe, k, clI.as<int64_t>(), clD.as<float>(), ix->T.as<float>(),
                       t3.as<float>(), xq, ix->coarse.as<float>(), ix->pq.as<float>(), ix->d,
                       direct, ix->list_off.as<int64_t>(), ix->codes.as<uint8_t>(),
-                      ix->ids.as<int64_t>(), D, I, st);
+                      ix->ids.as<int64_t>(), D, I, st, nullptr, nullptr, nullptr, nullptr,
+                      nullptr, ix->tuning);
 }
 }  // namespace gbk
 extern "C" {
@@ -518,7 +521,7 @@ gbk_status batched_run(gbk_index* ix, const float* xq, int64_t nq, const int32_t
                       t3.as<float>(), xq, ix->coarse.as<float>(), ix->pq.as<float>(), ix->d, direct,
                       ix->list_off.as<int64_t>(), ix->codes.as<uint8_t>(), ix->ids.as<int64_t>(),
                       D, I, st, kq, npq, out_off, order.as<int64_t>(),
-                      counter.as<unsigned long long>());
+                      counter.as<unsigned long long>(), ix->tuning);
 }
 
 }  // namespace gbk
@@ -728,3 +731,89 @@ gbk_status gbk_ivfpq_knn_graph(gbk_index* ix, const float* x, int64_t n, const i
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ scan autotuning
+
+extern "C" {
+
+gbk_status gbk_ivfpq_set_tuning(gbk_index* ix, int32_t codes_per_thread, int32_t blocks_per_sm) {
+  clear_error();
+  GBK_REQUIRE(ix, "gbk_ivfpq_set_tuning: NULL index");
+  GBK_REQUIRE(codes_per_thread == 2 || codes_per_thread == 4 || codes_per_thread == 8,
+              "gbk_ivfpq_set_tuning: codes per thread must be 2, 4 or 8");
+  GBK_REQUIRE(blocks_per_sm >= 1 && blocks_per_sm <= 8,
+              "gbk_ivfpq_set_tuning: blocks per SM must be in [1, 8]");
+  ix->tuning.codes_per_thread = codes_per_thread;
+  ix->tuning.blocks_per_sm = blocks_per_sm;
+  return GBK_OK;
+}
+
+gbk_status gbk_ivfpq_get_tuning(const gbk_index* ix, int32_t* codes_per_thread,
+                                int32_t* blocks_per_sm) {
+  clear_error();
+  GBK_REQUIRE(ix, "gbk_ivfpq_get_tuning: NULL index");
+  if (codes_per_thread) *codes_per_thread = ix->tuning.codes_per_thread;
+  if (blocks_per_sm) *blocks_per_sm = ix->tuning.blocks_per_sm;
+  return GBK_OK;
+}
+
+gbk_status gbk_ivfpq_autotune(gbk_index* ix, const float* xq, int64_t nq, const int32_t* k_per_q,
+                              int32_t max_k, const int32_t* nprobe_per_q, int32_t max_nprobe,
+                              gbk_mlp* mlp, const int64_t* out_offsets, float* D, int64_t* I,
+                              int32_t reps, float* best_ms, void* stream) {
+  clear_error();
+  gbk_status r = batched_check(ix, xq, nq, k_per_q, max_k, nprobe_per_q, max_nprobe, mlp,
+                               out_offsets, D, I);
+  if (r != GBK_OK) return r;
+  GBK_REQUIRE(nq > 0, "gbk_ivfpq_autotune: empty batch");
+  if (reps < 1) reps = 3;
+  cudaStream_t st = as_stream(stream);
+  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  cudaEvent_t e0, e1;
+  GBK_CUDA_CHECK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return set_error(GBK_ECUDA, "gbk_ivfpq_autotune: cudaEventCreate failed");
+  }
+  const gbk::ScanTuning keep = ix->tuning;
+  gbk::ScanTuning best = keep;
+  float best_t = -1.f;
+  static const int U[3] = {2, 4, 8};
+  for (int ui = 0; ui < 3 && r == GBK_OK; ui++) {
+    for (int bps = 1; bps <= 4 && r == GBK_OK; bps++) {
+      ix->tuning.codes_per_thread = U[ui];
+      ix->tuning.blocks_per_sm = bps;
+      // one untimed run (first-use set-up), then `reps` timed runs of the whole batch
+      r = gbk::batched_run(ix, xq, nq, k_per_q, max_k, nprobe_per_q, max_nprobe, mlp,
+                           out_offsets, D, I, nullptr, st);
+      if (r != GBK_OK) break;
+      if (cudaEventRecord(e0, st) != cudaSuccess) {
+        r = set_error(GBK_ECUDA, "gbk_ivfpq_autotune: event record failed");
+        break;
+      }
+      for (int i = 0; i < reps && r == GBK_OK; i++)
+        r = gbk::batched_run(ix, xq, nq, k_per_q, max_k, nprobe_per_q, max_nprobe, mlp,
+                             out_offsets, D, I, nullptr, st);
+      if (r != GBK_OK) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        r = set_error(GBK_ECUDA, "gbk_ivfpq_autotune: event timing failed");
+        break;
+      }
+      ms /= (float)reps;
+      if (best_t < 0.f || ms < best_t) {
+        best_t = ms;
+        best = ix->tuning;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ix->tuning = r == GBK_OK ? best : keep;
+  if (r == GBK_OK && best_ms) *best_ms = best_t;
+  return r;
+}
+
+}  // extern "C"
+

@@ -7,6 +7,14 @@
 
 namespace gbk {
 
+// Launch shape of the IVFADC list scan, chosen by gbk_ivfpq_autotune or set by the caller:
+// codes each thread loads per step (2, 4 or 8) and, in the persistent mixed-batch mode,
+// resident blocks per SM (1..8).  Results do not depend on it.
+struct ScanTuning {
+  int codes_per_thread = 4;
+  int blocks_per_sm = 2;
+};
+
 // Stable counting sort by key in [0, nb): offsets[nb+1], order[n] (positions grouped by
 // key, ascending within a key).  n < 2^31.
 gbk_status bucket_stable(const int32_t* keys, int64_t n, int nb, int64_t* offsets, int64_t* order,

@@ -210,10 +210,10 @@ struct ScanArgs {
   uint32_t* status;      // device status word (bounded waits record a timeout here)
 };
 
-// Block per query: for each probed list, build the LUT, stream the codes (one 16-byte code
-// per thread), form the distance and keep the k best (block selection, section 4 goal of a
-// single pass); ids are looked up only for the winners (section 5.3).
-template <int M, int KP>
+// Block per query: for each probed list, build the LUT, stream the codes (U 16-byte codes
+// per thread per step), form the distance and keep the k best (block selection, section 4
+// goal of a single pass); ids are looked up only for the winners (section 5.3).
+template <int M, int KP, int U>
 __global__ void __launch_bounds__(256)
     ivf_scan_kernel(const ScanArgs a) {
   constexpr int THREADS = 256, CAP = 4096;
@@ -280,7 +280,6 @@ __global__ void __launch_bounds__(256)
         o0 = o1 = 0;
       }
     };
-    constexpr int U = 4;                 // codes per thread per step
     constexpr int STEP = THREADS * U;
     uint32_t wn[U][M / 4];               // codes of the next step, in flight
     auto fetch_codes = [&](int64_t b0, int64_t o1) {
@@ -383,29 +382,42 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <int M, int KP>
-static gbk_status launch_scan(const ScanArgs& a, cudaStream_t st) {
+template <int M, int KP, int U>
+static gbk_status launch_scan(const ScanArgs& a, const ScanTuning& tun, cudaStream_t st) {
   using Sel = BlockSelect<256, KP, 4096>;
   const size_t smem = sizeof(float) * (256 * 32 + 2 * M * 256) + sizeof(typename Sel::Smem);
-  auto kern = ivf_scan_kernel<M, KP>;
+  auto kern = ivf_scan_kernel<M, KP, U>;
   static bool attr = false;
   if (!attr) {
     GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
     attr = true;
   }
-  const int64_t grid = a.counter ? std::min<int64_t>(a.nq, 2ll * device_info().sm_count) : a.nq;
+  // persistent mode: blocks_per_sm resident blocks per SM pull queries from the counter
+  const int64_t grid =
+      a.counter ? std::min<int64_t>(a.nq, (int64_t)tun.blocks_per_sm * device_info().sm_count)
+                : a.nq;
   kern<<<(unsigned)grid, 256, smem, st>>>(a);
   GBK_LAUNCH_CHECK();
   return GBK_OK;
 }
 
+template <int M, int KP>
+static gbk_status scan_u(const ScanArgs& a, const ScanTuning& tun, cudaStream_t st) {
+  switch (tun.codes_per_thread) {
+    case 2: return launch_scan<M, KP, 2>(a, tun, st);
+    case 4: return launch_scan<M, KP, 4>(a, tun, st);
+    case 8: return launch_scan<M, KP, 8>(a, tun, st);
+    default: return set_error(GBK_EINVAL, "scan tuning: codes per thread must be 2, 4 or 8");
+  }
+}
+
 template <int M>
-static gbk_status scan_k(const ScanArgs& a, cudaStream_t st) {  // a.k = largest k
-  if (a.k <= 32) return launch_scan<M, 32>(a, st);
-  if (a.k <= 128) return launch_scan<M, 128>(a, st);
-  if (a.k <= 256) return launch_scan<M, 256>(a, st);
-  return launch_scan<M, 1024>(a, st);
+static gbk_status scan_k(const ScanArgs& a, const ScanTuning& tun, cudaStream_t st) {
+  if (a.k <= 32) return scan_u<M, 32>(a, tun, st);  // a.k = largest k
+  if (a.k <= 128) return scan_u<M, 128>(a, tun, st);
+  if (a.k <= 256) return scan_u<M, 256>(a, tun, st);
+  return scan_u<M, 1024>(a, tun, st);
 }
 
 gbk_status ivf_scan_run(int M, int64_t nq, int nprobe, int k, const int64_t* cl_I,
@@ -414,15 +426,17 @@ gbk_status ivf_scan_run(int M, int64_t nq, int nprobe, int k, const int64_t* cl_
                         const int64_t* list_off, const uint8_t* codes, const int64_t* ids,
                         float* D, int64_t* I, cudaStream_t st, const int32_t* kq,
                         const int32_t* npq, const int64_t* out_off, const int64_t* order,
-                        unsigned long long* counter) {
+                        unsigned long long* counter, ScanTuning tun) {
   if (nq == 0) return GBK_OK;
+  if (tun.blocks_per_sm < 1 || tun.blocks_per_sm > 8)
+    return set_error(GBK_EINVAL, "scan tuning: blocks per SM must be in [1, 8]");
   ScanArgs a{nq, nprobe, k, cl_I, cl_D, T, t3, xq, coarse, pq, d, direct ? 1 : 0, list_off,
              codes, ids, D, I, kq, npq, out_off, order, counter, device_status()};
   if (!a.status) return set_error(GBK_ECUDA, "device status word unavailable");
   ProfScope prof("ivf_scan", st);
-  if (M == 8) return scan_k<8>(a, st);
-  if (M == 16) return scan_k<16>(a, st);
-  if (M == 32) return scan_k<32>(a, st);
+  if (M == 8) return scan_k<8>(a, tun, st);
+  if (M == 16) return scan_k<16>(a, tun, st);
+  if (M == 32) return scan_k<32>(a, tun, st);
   return set_error(GBK_EUNSUPPORTED, "IVFPQ scan supports M in {8, 16, 32}");
 }
 

@@ -81,3 +81,33 @@ def test_learned_nprobe_routing(gbk, index):
     # the same routing given explicitly reproduces the results
     D2, I2, _, _ = gbk.ivfpq_search_batched(ix, xq, kq, 10, used, 128)
     assert torch.equal(I, I2) and torch.equal(D, D2)
+
+
+def test_launch_shapes_do_not_change_results(gbk, index):
+    ix, xq = index
+    kq, npq = _mixed(xq.shape[0], 78)
+    ref = None
+    for u, b in ((4, 2), (2, 1), (8, 4), (8, 1), (2, 3)):
+        gbk.ivfpq_set_tuning(ix, u, b)
+        assert gbk.ivfpq_get_tuning(ix) == (u, b)
+        D, I, off, _ = gbk.ivfpq_search_batched(ix, xq, kq, 100, npq, 128)
+        Dp, Ip = ix.search(xq, 10, 32)
+        if ref is None:
+            ref = (D, I, Dp, Ip)
+        else:
+            assert torch.equal(ref[1], I) and torch.equal(ref[0], D)
+            assert torch.equal(ref[3], Ip) and torch.equal(ref[2], Dp)
+    gbk.ivfpq_set_tuning(ix, 4, 2)
+    for u, b in ((3, 2), (4, 0), (4, 9)):
+        with pytest.raises(gbk.GbkError):
+            gbk.ivfpq_set_tuning(ix, u, b)
+
+
+def test_autotune_keeps_a_valid_shape(gbk, index):
+    ix, xq = index
+    kq, npq = _mixed(xq.shape[0], 79)
+    (u, b), ms = gbk.ivfpq_autotune(ix, xq, kq, 100, npq, 128, reps=2)
+    assert u in (2, 4, 8) and 1 <= b <= 4 and ms > 0
+    D, I, off, used = gbk.ivfpq_search_batched(ix, xq, kq, 100, npq, 128)
+    _check_against_plain(ix, xq, kq, npq, D, I, off)
+    gbk.ivfpq_set_tuning(ix, 4, 2)
