@@ -276,14 +276,18 @@ gbk_status prepare_operand(const float* x, int64_t n, int d, int prec, int64_t n
   return GBK_OK;
 }
 
-// Chunks S minimising (waves x tiles per chunk); ties to fewer chunks.
-int plan_chunks(int nqt, int ntiles, int grid_cap) {
+// Chunks S minimising waves x (tiles per chunk + per-item overhead); ties to fewer chunks.
+// The overhead is a chunk's candidate lists learning their threshold again: measured at
+// about 0.9 k tiles per (query tile, chunk) item for k = 16..128 (1e4 - 5e4 queries), none
+// for k = 1.
+int plan_chunks(int nqt, int ntiles, int grid_cap, int k) {
   int best = 1;
   int64_t best_cost = INT64_MAX;
+  const int64_t ovh = k <= 1 ? 0 : (9 * (int64_t)k + 9) / 10;
   for (int S = 1; S <= std::min(ntiles, 512); S++) {
     const int64_t waves = ((int64_t)nqt * S + grid_cap - 1) / grid_cap;
     const int64_t tpc = (ntiles + S - 1) / S;
-    const int64_t cost = waves * tpc * 64 + S;  // small penalty per chunk (merge work)
+    const int64_t cost = waves * (tpc + ovh) * 64 + S;  // + small penalty per chunk (merge)
     if (cost < best_cost) {
       best_cost = cost;
       best = S;
@@ -353,7 +357,7 @@ gbk_status pairwise_run(const PreparedOperand& Q, const PreparedOperand& B, bool
   a.nb = (int)B.n;
   a.nqt = (int)((qn + GEMM_BM - 1) / GEMM_BM);
   a.ntiles = (int)((B.n + GEMM_BN - 1) / GEMM_BN);
-  a.chunks = plan_chunks(a.nqt, a.ntiles, device_info().sm_count);
+  a.chunks = plan_chunks(a.nqt, a.ntiles, device_info().sm_count, 1);
   a.tpc = (a.ntiles + a.chunks - 1) / a.chunks;
   a.chunks = (a.ntiles + a.tpc - 1) / a.tpc;
   a.ynorm = B.norms.as<float>();
@@ -404,7 +408,7 @@ static gbk_status select_run(const float* xq, const PreparedOperand& Q, const Pr
   a.nqt = (int)((nq + GEMM_BM - 1) / GEMM_BM);
   a.ntiles = ntiles;
   a.chunks = chunks_opt > 0 ? std::min(chunks_opt, ntiles)
-                            : plan_chunks(a.nqt, ntiles, device_info().sm_count);
+                            : plan_chunks(a.nqt, ntiles, device_info().sm_count, k);
   a.tpc = (ntiles + a.chunks - 1) / a.chunks;
   a.chunks = (ntiles + a.tpc - 1) / a.tpc;
   a.k = k;

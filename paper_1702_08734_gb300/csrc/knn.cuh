@@ -40,7 +40,7 @@ gbk_status pairwise_run(const PreparedOperand& Q, const PreparedOperand& B, bool
 gbk_status knn_run(const float* xq, int64_t nq, const float* xb, int64_t nb, int d, int k,
                    int metric, float* D, int64_t* I, const KnnPlan& plan, cudaStream_t st);
 
-int plan_chunks(int nqt, int ntiles, int grid_cap);
+int plan_chunks(int nqt, int ntiles, int grid_cap, int k);
 
 // Exact float32 re-rank of k' candidates (Ic, Dc: low-precision results) to the top k,
 // with the per-query certificate (see rerank.cu).
