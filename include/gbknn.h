@@ -96,11 +96,13 @@ gbk_status gbk_kselect(const float* vals, int64_t rows, int64_t len, int32_t k,
 /* Launch parameters of gbk_kselect_ex; 0 selects the library default. */
 typedef struct gbk_kselect_opts {
   int32_t segments; /* thread blocks per row (>1: two-pass selection, section 5.3) */
-  int32_t unroll;   /* 16-byte loads in flight per thread per iteration: 4 or 8      */
+  int32_t unroll;   /* how the row is streamed (k > 1): 4 or 8 = 16-byte register   */
+                    /* loads in flight per thread per iteration; 1 = a shared-memory */
+                    /* ring of four 16 KB bulk copies kept in flight per block      */
 } gbk_kselect_opts;
 
 /* gbk_kselect with explicit launch parameters (opts may be NULL).  Results do not
- * depend on the parameters.  Extra error: GBK_EINVAL for unroll other than 0, 4, 8. */
+ * depend on the parameters.  Extra error: GBK_EINVAL for unroll other than 0, 1, 4, 8. */
 gbk_status gbk_kselect_ex(const float* vals, int64_t rows, int64_t len, int32_t k,
                           int32_t largest, float* D, int64_t* I, const gbk_kselect_opts* opts,
                           void* stream);

@@ -165,8 +165,8 @@ gbk_status gbk_kselect_ex(const float* vals, int64_t rows, int64_t len, int32_t 
   GBK_REQUIRE(rows * (int64_t)k < (int64_t(1) << 40), "gbk_kselect: output too large");
   KselectTuning tu = kselect_default_tuning(rows, len, k);
   if (opts) {
-    GBK_REQUIRE(opts->unroll == 0 || opts->unroll == 4 || opts->unroll == 8,
-                "gbk_kselect_ex: unroll must be 0, 4 or 8");
+    GBK_REQUIRE(opts->unroll == 0 || opts->unroll == 1 || opts->unroll == 4 || opts->unroll == 8,
+                "gbk_kselect_ex: unroll must be 0, 1, 4 or 8");
     GBK_REQUIRE(opts->segments >= 0, "gbk_kselect_ex: segments < 0");
     if (opts->unroll) tu.unroll = opts->unroll;
     if (opts->segments) tu.segs = opts->segments;

@@ -13,8 +13,8 @@ from paper_1702_08734_gb300 import datagen
 pytestmark = pytest.mark.gpu
 
 
-def _check(gbk, v, k, largest):
-    D, I = gbk.kselect(torch.from_numpy(v).cuda(), k, largest=largest)
+def _check(gbk, v, k, largest, **kw):
+    D, I = gbk.kselect(torch.from_numpy(v).cuda(), k, largest=largest, **kw)
     torch.cuda.synchronize()
     Do, Io = oracle.kselect(v, k, largest=largest)
     np.testing.assert_array_equal(I.cpu().numpy(), Io)
@@ -84,10 +84,37 @@ def test_invalid_arguments_raise(gbk):
             gbk.kselect(v, k)
 
 
-@pytest.mark.parametrize("unroll,segments", [(4, 1), (8, 1), (4, 3), (8, 7)])
+@pytest.mark.parametrize("unroll,segments", [(4, 1), (8, 1), (4, 3), (8, 7), (1, 1), (1, 5)])
 def test_launch_options_do_not_change_results(gbk, unroll, segments):
     v = datagen.uniform_matrix(300 + unroll, 50, 30011)
     Do, Io = oracle.kselect(v, 77)
     D, I = gbk.kselect(torch.from_numpy(v).cuda(), 77, unroll=unroll, segments=segments)
     np.testing.assert_array_equal(I.cpu().numpy(), Io)
     np.testing.assert_array_equal(D.cpu().numpy(), Do)
+
+
+# the shared-memory ring of bulk copies (unroll=1): ragged and unaligned rows (row starts
+# off a 16-byte boundary, partial last stage), several stages per row, specials, segments
+@pytest.mark.parametrize("length", [1, 3, 31, 1000, 4099, 16389, 70001])
+@pytest.mark.parametrize("largest", [False, True])
+def test_ring_streaming_matches_oracle(gbk, length, largest):
+    v = datagen.uniform_matrix(2000 + length, 29, length)
+    for k in sorted({2, 31, 33, 100, 257, 1024}):
+        if k <= length:
+            _check(gbk, v, k, largest, unroll=1)
+
+
+@pytest.mark.parametrize("k", [7, 64, 1000])
+def test_ring_heavy_ties_and_specials(gbk, k):
+    rng = np.random.default_rng(k + 50)
+    v = rng.integers(-3, 4, size=(40, 20000)).astype(np.float32)
+    v[0, ::7] = np.nan
+    v[1, :] = np.nan
+    v[2, ::3] = np.inf
+    v[3, ::5] = -np.inf
+    v[4, :] = -0.0
+    v[4, 1::2] = 0.0
+    for largest in (False, True):
+        _check(gbk, v, k, largest, unroll=1)
+        _check(gbk, v, k, largest, unroll=1, segments=3)
+
