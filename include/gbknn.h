@@ -138,7 +138,7 @@ gbk_status gbk_row_norms(const float* x, int64_t n, int32_t d, float* out, void*
 /* Options of gbk_knn_brute (NULL = defaults). */
 typedef struct gbk_knn_opts {
   int32_t precision; /* GBK_PREC_FP32 (default), GBK_PREC_BF16 or GBK_PREC_FP8          */
-  int32_t kprime;    /* BF16/FP8: candidates re-ranked in float32 (0 = min(4k, max(2k, 64)), >= k, <= 1024) */
+  int32_t kprime;    /* BF16/FP8: candidates re-ranked in float32 (0 = 4k for k <= 16, else k + k/4; >= k, <= 1024) */
   int32_t chunks;    /* database chunks of the work decomposition (0 = planned)          */
   int32_t* certified; /* BF16/FP8, optional device [nq]: 1 if the result provably equals
                          the float32 top-k (see gbk_knn_brute), else 0                  */

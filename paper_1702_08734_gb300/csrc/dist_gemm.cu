@@ -441,9 +441,10 @@ gbk_status knn_run(const float* xq, int64_t nq, const float* xb, int64_t nb, int
     return r;
   if (plan.prec == GBK_PREC_FP32) return select_run(xq, Q, B, nq, nb, d, k, ip, plan.chunks, D, I, st);
   // low precision: over-fetch k' candidates, then exact float32 re-rank + certificate
-  // default over-fetch: 4k for small k, 2k (at least 64) once k is large enough that the
-  // candidates' rank statistics concentrate
-  int kp = plan.kprime > 0 ? plan.kprime : std::min(4 * k, std::max(2 * k, 64));
+  // default over-fetch: 4k for k <= 16, k + k/4 above (the low-precision error moves a
+  // neighbour by few ranks once k is large).  Not rounded up to the lists' power-of-two
+  // length: a larger k' loosens the selection threshold and costs candidate pushes.
+  int kp = plan.kprime > 0 ? plan.kprime : (k <= 16 ? 4 * k : k + k / 4);
   kp = std::min(kp, GBK_MAX_K);
   kp = (int)std::min<int64_t>(std::max(kp, k), nb);
   Scratch Dc, Ic;
