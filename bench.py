@@ -83,6 +83,21 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+def max_over_ranks(times_ms, world, device):
+    """Each timing's maximum over the ranks (the slowest replica sets the job's time)."""
+    if world <= 1:
+        return list(times_ms)
+    import torch
+    t = torch.tensor(list(times_ms), dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units all ranks processed per second of the (max-over-ranks) time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -520,12 +535,8 @@ def main():
     total_ms = e0.elapsed_time(e1)
     ksel_ms = sum(starts[i].elapsed_time(mids[i]) for i in range(args.steps))
     knn_ms = total_ms - ksel_ms
-    if world > 1:
-        t = torch.tensor([total_ms, knn_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, knn_ms = t.tolist()
-    queries = len(KNN_K) * NQ * args.steps * world
-    value = queries / (knn_ms / 1e3)
+    total_ms, knn_ms = max_over_ranks([total_ms, knn_ms], world, "cuda")
+    value = whole_job_rate(len(KNN_K) * NQ * args.steps, world, knn_ms)
     # per-kernel times from the library's own events
     by = {}
     for name, ms in prof:
