@@ -337,6 +337,18 @@ gbk_status gbk_recall_counts(const int64_t* I, const int64_t* G, int64_t nq, int
 gbk_status gbk_nprobe_features(const float* xq, int64_t nq, int32_t d, const float* coarse_dist,
                                int32_t tau, int32_t nfeat, float* F, void* stream);
 
+/* ------------------------------------------------------------------ shard merge */
+
+/* The extra k-selection after sharding (section 5.4): per query, the k best of nparts
+ * partial results D_parts / I_parts [nparts][nq][k_in] (device; each a shard's output,
+ * ids already global), by value then lower id (ascending; descending values with
+ * largest != 0).  Entries with id < 0 are padding and skipped; rows with fewer than k
+ * entries are padded (+inf or -inf, -1).  Ids must be below 2^32; -0 is returned as +0.
+ * D / I [nq][k] device.  1 <= k <= GBK_MAX_K. */
+gbk_status gbk_merge_topk(const float* D_parts, const int64_t* I_parts, int32_t nparts,
+                          int64_t nq, int32_t k_in, int32_t k, int32_t largest, float* D,
+                          int64_t* I, void* stream);
+
 /* ------------------------------------------------------------------ scan autotuning */
 
 /* Launch shape of the list scan (results never depend on it): codes each thread loads per

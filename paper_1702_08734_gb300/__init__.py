@@ -405,11 +405,24 @@ _SIGNATURES.update({
                                 _vp, _vp],
     "gbk_graph_launch": [_vp, _vp],
     "gbk_ivfpq_knn_graph": [_vp, _vp, _i64, _vp, _i32, _i32, _vp, _i64, _vp, _vp, _vp],
+    "gbk_merge_topk": [_vp, _vp, _i32, _i64, _i32, _i32, _i32, _vp, _vp, _vp],
     "gbk_ivfpq_set_tuning": [_vp, _i32, _i32],
     "gbk_ivfpq_get_tuning": [_vp, _vp, _vp],
     "gbk_ivfpq_autotune": [_vp, _vp, _i64, _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _i32, _vp,
                            _vp],
 })
+
+
+def merge_topk(D_parts: torch.Tensor, I_parts: torch.Tensor, k: int, largest: bool = False):
+    """k best per query of stacked partial results [nparts][nq][k_in] (value, then id)."""
+    _dev(D_parts, torch.float32, "D_parts")
+    _dev(I_parts, torch.int64, "I_parts")
+    nparts, nq, kin = D_parts.shape
+    D = torch.empty((nq, k), dtype=torch.float32, device=D_parts.device)
+    I = torch.empty((nq, k), dtype=torch.int64, device=D_parts.device)
+    _call("gbk_merge_topk", _ptr(D_parts), _ptr(I_parts), int(nparts), nq, int(kin), int(k),
+          int(bool(largest)), _ptr(D), _ptr(I), _stream())
+    return D, I
 
 
 def ivfpq_set_tuning(index, codes_per_thread: int, blocks_per_sm: int):

@@ -239,6 +239,20 @@ gbk_status gbk_knn_brute(const float* xq, int64_t nq, const float* xb, int64_t n
   return knn_run(xq, nq, xb, nb, d, k, metric, D, I, plan, as_stream(stream));
 }
 
+gbk_status gbk_merge_topk(const float* D_parts, const int64_t* I_parts, int32_t nparts,
+                          int64_t nq, int32_t k_in, int32_t k, int32_t largest, float* D,
+                          int64_t* I, void* stream) {
+  clear_error();
+  GBK_REQUIRE(nparts >= 1 && k_in >= 1 && k >= 1 && k <= GBK_MAX_K,
+              "gbk_merge_topk: bad sizes");
+  GBK_REQUIRE(nq >= 0 && nq < (int64_t(1) << 31), "gbk_merge_topk: nq out of range");
+  GBK_REQUIRE((int64_t)nparts * k_in < (int64_t(1) << 31), "gbk_merge_topk: too many entries");
+  if (nq == 0) return GBK_OK;
+  GBK_REQUIRE(D_parts && I_parts && D && I, "gbk_merge_topk: NULL pointer");
+  return merge_parts_run(D_parts, I_parts, nparts, nq, k_in, k, largest != 0, D, I,
+                         as_stream(stream));
+}
+
 gbk_status gbk_pairwise_distances(const float* xq, int64_t nq, const float* xb, int64_t nb,
                                   int32_t d, int32_t metric, int32_t precision, float* out,
                                   int64_t ldo, void* stream) {

@@ -186,6 +186,90 @@ gbk_status knn_merge(const uint64_t* part, int64_t nq, int chunks, int kp, int k
   return launch_knn_merge<512>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);
 }
 
+// ------------------------------------------------------------------ shard merge
+
+// Top k of nparts sorted partial results per query (section 5.4: the extra k-selection
+// after sharding).  Entries with a negative id are padding and skipped.
+template <int KP>
+__global__ void __launch_bounds__(256)
+    merge_parts_kernel(const float* __restrict__ Dp, const int64_t* __restrict__ Ip, int nparts,
+                       int64_t nq, int kin, int k, int largest, float* __restrict__ D,
+                       int64_t* __restrict__ I) {
+  constexpr int THREADS = 256, CAP = 4096;
+  using Sel = BlockSelect<THREADS, KP, CAP>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(smem_raw);
+  const int64_t q = blockIdx.x;
+  const int64_t nper = (int64_t)nparts * kin;
+  Sel::init(s);
+  __syncthreads();
+  uint64_t thr = ~0ull;
+  for (int64_t base = 0; base < nper; base += THREADS) {
+    const int64_t i = base + threadIdx.x;
+    uint64_t c[1];
+    uint32_t mask = 0;
+    if (i < nper) {
+      const int64_t p = i / kin, j = i % kin;
+      const int64_t e = (p * nq + q) * kin + j;
+      const int64_t id = Ip[e];
+      if (id >= 0) {
+        c[0] = composite(ordered_key(Dp[e], largest != 0), (uint32_t)id);
+        mask = c[0] <= thr ? 1u : 0u;
+      }
+    }
+    Sel::template push<1>(s, mask, c);
+    __syncthreads();
+    if (s.n_buf > CAP - THREADS) {
+      Sel::compact(s, k);
+      thr = s.thr;
+    }
+  }
+  Sel::finish(s, k);
+  for (int j = threadIdx.x; j < k; j += THREADS) {
+    const uint64_t e = s.top[j];
+    if (e == ~0ull) {
+      D[q * k + j] = largest ? -INFINITY : INFINITY;
+      I[q * k + j] = -1;
+    } else {
+      D[q * k + j] = key_value((uint32_t)(e >> 32), largest != 0);
+      I[q * k + j] = (int64_t)(uint32_t)e;
+    }
+  }
+}
+
+template <int KP>
+gbk_status launch_merge_parts(const float* Dp, const int64_t* Ip, int nparts, int64_t nq, int kin,
+                              int k, bool largest, float* D, int64_t* I, cudaStream_t st) {
+  using Sel = BlockSelect<256, KP, 4096>;
+  auto kern = merge_parts_kernel<KP>;
+  static bool attr = false;
+  if (!attr) {
+    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sizeof(typename Sel::Smem)));
+    attr = true;
+  }
+  kern<<<(unsigned)nq, 256, sizeof(typename Sel::Smem), st>>>(Dp, Ip, nparts, nq, kin, k,
+                                                              largest ? 1 : 0, D, I);
+  GBK_LAUNCH_CHECK();
+  return GBK_OK;
+}
+
+}  // namespace
+
+gbk_status merge_parts_run(const float* Dp, const int64_t* Ip, int nparts, int64_t nq, int kin,
+                           int k, bool largest, float* D, int64_t* I, cudaStream_t st) {
+  if (nq == 0) return GBK_OK;
+  ProfScope prof("merge_parts", st);
+  if (k <= 32) return launch_merge_parts<32>(Dp, Ip, nparts, nq, kin, k, largest, D, I, st);
+  if (k <= 64) return launch_merge_parts<64>(Dp, Ip, nparts, nq, kin, k, largest, D, I, st);
+  if (k <= 128) return launch_merge_parts<128>(Dp, Ip, nparts, nq, kin, k, largest, D, I, st);
+  if (k <= 256) return launch_merge_parts<256>(Dp, Ip, nparts, nq, kin, k, largest, D, I, st);
+  if (k <= 512) return launch_merge_parts<512>(Dp, Ip, nparts, nq, kin, k, largest, D, I, st);
+  return launch_merge_parts<1024>(Dp, Ip, nparts, nq, kin, k, largest, D, I, st);
+}
+
+namespace {
+
 // ------------------------------------------------------------------ TMA descriptors
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,

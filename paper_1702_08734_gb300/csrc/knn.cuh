@@ -42,6 +42,11 @@ gbk_status knn_run(const float* xq, int64_t nq, const float* xb, int64_t nb, int
 
 int plan_chunks(int nqt, int ntiles, int grid_cap, int k);
 
+// Top k of nparts sorted partial lists per query: Dp/Ip [nparts][nq][kin] (ids < 2^32;
+// negative ids skipped) -> D/I [nq][k], order (value, id); padding (+-inf, -1).
+gbk_status merge_parts_run(const float* Dp, const int64_t* Ip, int nparts, int64_t nq, int kin,
+                           int k, bool largest, float* D, int64_t* I, cudaStream_t st);
+
 // Exact float32 re-rank of k' candidates (Ic, Dc: low-precision results) to the top k,
 // with the per-query certificate (see rerank.cu).
 gbk_status rerank_run(const float* xq, const float* xb, int64_t nq, int64_t nb, int d,
