@@ -84,30 +84,45 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
   const int head = (int)(n < he ? n : he);
   const int64_t n4 = (n - head) / 4;
   const int tail = (int)(n - head - n4 * 4);
-  Sel::init(s);
-  if (tid == 0) *overflow = 0;
-  __syncthreads();
+  int* sure = overflow + 2;  // a compaction to k happened under the provisional threshold
+  // Provisional threshold (k > 32 on long rows): from the first iteration's sample, the
+  // r-th smallest of four group minima per thread, r ~ 1.25 k sample/n + 8; exact as soon
+  // as k values at or below it are found (checked at the end, else the row is redone with
+  // the plain threshold).
+  const int64_t sample = (n4 < (int64_t)C::CHUNK / 4 ? n4 : (int64_t)C::CHUNK / 4) * 4;
+  constexpr int GROUPS = 4;  // minima per thread (groups of PT / 4 values)
+  const int64_t r64 = n > 0 ? (5 * (int64_t)k * sample) / (4 * n) + 8 : 0;
+  const bool use_guess = k > 32 && r64 < (int64_t)(GROUPS * THREADS / 2) &&
+                         sample >= 4 * (int64_t)THREADS;
+  const int rank = (int)r64;
+  float ht_v = 0.f;  // this thread's head / tail element, offered after the guess
+  int64_t ht_e = -1;
+  if (tid < head) ht_e = tid;
+  else if (tid >= 32 && tid < 32 + tail) ht_e = head + n4 * 4 + (tid - 32);
+  if (ht_e >= 0) ht_v = p[ht_e];
+  const float4* p4 = reinterpret_cast<const float4*>(p + head);
+  const uint32_t idx0 = (uint32_t)(s0 + head);
   ValueFilter f;
+  for (int attempt = 0; attempt < 2; attempt++) {
+  const bool guess = use_guess && attempt == 0;
+  Sel::init(s);
+  if (tid == 0) {
+    *overflow = 0;
+    *sure = 0;
+  }
+  __syncthreads();
   f.set(NAN_KEY, LARGEST);
-  {
+  if (!guess) {
     uint64_t c[1];
     uint32_t mask = 0;
-    int64_t e = -1;
-    if (tid < head) e = tid;
-    else if (tid >= 32 && tid < 32 + tail) e = head + n4 * 4 + (tid - 32);
-    if (e >= 0) {
-      const float v = p[e];
-      if (f.pass(v)) {
-        c[0] = composite(ordered_key(v, LARGEST), (uint32_t)(s0 + e));
-        mask = 1u;
-      }
+    if (ht_e >= 0 && f.pass(ht_v)) {
+      c[0] = composite(ordered_key(ht_v, LARGEST), (uint32_t)(s0 + ht_e));
+      mask = 1u;
     }
     Sel::template push<1>(s, mask, c);
   }
   __syncthreads();
   if (tid == 0) *n_ok = s.n_buf;
-  const float4* p4 = reinterpret_cast<const float4*>(p + head);
-  const uint32_t idx0 = (uint32_t)(s0 + head);
   // PIPE: the next iteration's loads are issued before this one is filtered, so the
   // block's capacity barrier never leaves the SM without loads in flight.
   float4 nxt[PIPE ? UNROLL : 1];
@@ -136,8 +151,55 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
       v[u * 4 + 2] = x.z;
       v[u * 4 + 3] = x.w;
     }
-    uint32_t skip = 0u;  // slot already offered as this thread's minimum
-    if (base == 0 && k <= THREADS) {
+    uint32_t skip = 0u;  // slots already offered as this thread's minima
+    if (base == 0 && guess) {
+      // GROUPS group minima of every thread; their rank-th smallest, g, has at least
+      // rank sample values at or below it
+      uint64_t mn[GROUPS];
+      uint32_t gm = 0;
+#pragma unroll
+      for (int gi = 0; gi < GROUPS; gi++) mn[gi] = ~0ull;
+#pragma unroll
+      for (int u = 0; u < UNROLL; u++) {
+        if (u * THREADS + tid < n4) {
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            const int slot = u * 4 + j, gi = slot / (C::PT / GROUPS);
+            const uint64_t c = composite(ordered_key(v[slot], LARGEST),
+                                         idx0 + (uint32_t)((u * THREADS + tid) * 4 + j));
+            if (c < mn[gi]) mn[gi] = c;
+            gm |= 1u << gi;
+          }
+        }
+      }
+      Sel::template push<GROUPS>(s, gm, mn);
+      __syncthreads();
+      const bool have = s.n_buf > rank;  // uniform
+      if (have) Sel::compact(s, rank);
+      const uint32_t gkey = (uint32_t)(s.thr >> 32);
+      __syncthreads();
+      // the minima only located g: start the selection afresh with g as a provisional
+      // value threshold, so every value <= g (ties included) is offered below
+      if (tid == 0) {
+        s.n_top = 0;
+        s.n_buf = 0;
+        s.thr = ~0ull;
+      }
+      __syncthreads();
+      if (have) f.set(gkey, LARGEST);
+      {
+        uint64_t c[1];
+        uint32_t mask = 0;
+        if (ht_e >= 0 && f.pass(ht_v)) {
+          c[0] = composite(ordered_key(ht_v, LARGEST), (uint32_t)(s0 + ht_e));
+          mask = 1u;
+        }
+        Sel::template push<1>(s, mask, c);
+      }
+      __syncthreads();
+      if (tid == 0) *n_ok = s.n_buf;
+      __syncthreads();
+    } else if (base == 0 && k <= THREADS) {
       // Seed the threshold: every thread offers the smallest of its first values; the
       // k-th smallest of these distinct elements bounds the row's k-th from above and is
       // about as tight as the k-th of the whole first iteration, at 1/PT of the work.
@@ -218,6 +280,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
       if (tid == 0) {
         s.n_buf = *n_ok;  // successful reservations form a prefix of the buffer
         *overflow = 0;
+        *sure = 1;        // more than CAP >= k candidates: the threshold is a true bound
       }
       __syncthreads();
       Sel::compact(s, k);
@@ -226,6 +289,11 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
       __syncthreads();
     }
   }
+  __syncthreads();
+  // a provisional threshold is exact once k candidates at or below it were found
+  if (!guess || *sure != 0 || s.n_top + s.n_buf >= k) break;  // uniform (after a barrier)
+  __syncthreads();  // all have read the state before the retry resets it
+  }  // attempt
   Sel::finish(s, k);
   if (segs == 1) {
     for (int j = tid; j < k; j += THREADS) {
