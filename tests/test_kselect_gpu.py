@@ -118,3 +118,16 @@ def test_ring_heavy_ties_and_specials(gbk, k):
         _check(gbk, v, k, largest, unroll=1)
         _check(gbk, v, k, largest, unroll=1, segments=3)
 
+
+
+@pytest.mark.parametrize("k", [40, 257, 1000])
+@pytest.mark.parametrize("largest", [False, True])
+def test_sorted_rows_exercise_threshold_fallback(gbk, k, largest):
+    # Ascending rows put the smallest values first: the provisional threshold taken from
+    # the first iteration admits fewer than k values and the row is redone; descending
+    # rows make it admit everything and overflow the buffer (compactions).
+    v = datagen.uniform_matrix(4100 + k, 12, 70001)
+    v[:4] = np.sort(v[:4], axis=1)
+    v[4:8] = np.sort(v[4:8], axis=1)[:, ::-1].copy()
+    _check(gbk, v, k, largest)
+    _check(gbk, v, k, largest, segments=3)
