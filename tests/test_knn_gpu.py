@@ -189,3 +189,44 @@ def test_benchmark_workload_sampled(gbk, sift_like, k):
                I[torch.from_numpy(sample).cuda()], k)
     Dc = D.cpu()
     assert bool((Dc[:, 1:] >= Dc[:, :-1]).all())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+def test_fused_large_k(gbk, prec, metric):
+    # nb > 65,536 and k >= 32: the fused selection with candidate lists of 128
+    xq = datagen.gaussian_matrix(71, 300, 64)
+    xb = datagen.gaussian_matrix(72, 100000, 64)
+    k = 100
+    if prec == "fp32":
+        D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), k,
+                             metric=metric)
+        _check_knn(xq, xb, D, I, k, metric)
+    else:
+        D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), k,
+                             metric=metric, precision=prec)
+        Do, Io = oracle.knn(xq, xb, k, metric=metric)
+        assert (I.cpu().numpy() == Io).mean() > 0.99
+
+
+def test_clustered_near_duplicates_in_one_tile(gbk):
+    # the only close points sit in the first 128-row tile, far points elsewhere: one chunk
+    # holds every neighbour of queries 0 and 1, the others none (thresholds published by
+    # the first chunk must still leave the rest of the search exact)
+    rng = np.random.default_rng(3)
+    nq, d, k = 64, 32, 64
+    xq = rng.standard_normal((nq, d)).astype(np.float32)
+    xb = (rng.standard_normal((70000, d)) * 10).astype(np.float32)
+    xb[:40] = xq[0] + 0.01 * rng.standard_normal((40, d)).astype(np.float32)  # tile 0
+    xb[40:128] = xq[1] + 0.01 * rng.standard_normal((88, d)).astype(np.float32)
+    D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), k)
+    # absolute tolerance: distances ~2e-3 between near-duplicates come out of
+    # ||x||^2 + ||y||^2 - 2<x, y> with norms ~32 (Eq. 2 cancels; the oracle sums (x - y)^2)
+    D, I = D.cpu().numpy().astype(np.float64), I.cpu().numpy()
+    Do, Io = oracle.knn(xq, xb, k)
+    assert np.all(np.abs(D - Do) <= 1e-5 * np.abs(Do) + 2e-4)
+    qi = np.repeat(np.arange(nq), k)
+    ex = oracle.pair_dist(xq, xb, qi, I.ravel()).reshape(I.shape)
+    assert np.all(ex <= Do[:, -1:] + 2e-4)
+    assert all(len(set(r.tolist())) == k for r in I)
+    assert np.array_equal(np.sort(I[2:], axis=1), np.sort(Io[2:], axis=1))
