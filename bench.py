@@ -566,6 +566,28 @@ def main():
     kselect_obj = {"unit": "GB/s", "peak_hbm_gbs": hbm, "peak_source": src,
                    "gbs": ks_detail, "frac": {k: v / hbm for k, v in ks_detail.items()}}
 
+    # pattern 1 beside the float32 path (outside the timed region): BF16 / FP8 tensor-core
+    # distances, k' over-fetch, exact float32 re-rank; recall against the float32 results
+    lowp = {}
+    if rank == 0:
+        for prec in ("bf16", "fp8"):
+            row = {}
+            for k in KNN_K:
+                g.knn_brute(xq, xb, k, precision=prec)
+                torch.cuda.synchronize()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                for _ in range(2):
+                    Dl, Il, cert, _ = g.knn_brute(xq, xb, k, precision=prec, certify=True)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                c = torch.empty(NQ, dtype=torch.int32, device="cuda")
+                g.recall_counts(Il, kouts[k][1], c)
+                row["k%d" % k] = {"ms": ev0.elapsed_time(ev1) / 2,
+                                  "queries_per_s": NQ / (ev0.elapsed_time(ev1) / 2e3),
+                                  "recall_vs_fp32": float(c.float().mean().item()) / k,
+                                  "certified": float(cert.float().mean().item())}
+            lowp[prec] = row
     # end to end through the public API: host buffers in, host results out
     e2e = None
     if rank == 0:
@@ -598,6 +620,7 @@ def main():
                        "l2_flush": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU",
                        "knn_ms_per_step": knn_ms / args.steps, "kselect_ms_per_step": ksel_ms / args.steps},
             "roofline": roof, "kselect": kselect_obj, "cpu_baseline": cpu, "e2e": e2e,
+            "low_precision_rerank": lowp,
             "gpu_launches": launches, "clocks": clk,
             "kernel_ms": {k: sum(v) / len(v) for k, v in by.items()},
         }), flush=True)
