@@ -83,6 +83,30 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+GEMM_SOURCES = ("dist_gemm_kernel.cuh", "dist_gemm.cuh", "dist_gemm.cu", "dist_gemm_tf32x3.cu",
+                "sm100.cuh", "select_core.cuh")
+
+
+def gemm_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in GEMM_SOURCES:
+        with open(os.path.join(ROOT, "paper_1702_08734_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None when the
+    kernel's sources changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            j = json.load(f)[kernel]
+        return j["dram_bytes_per_launch"] if j["source_sha256"] == gemm_source_hash() else None
+    except Exception:
+        return None
+
+
 def max_over_ranks(times_ms, world, device):
     """Each timing's maximum over the ranks (the slowest replica sets the job's time)."""
     if world <= 1:
@@ -556,7 +580,7 @@ def main():
     gemm_avg = sum(gemm_ms) / len(gemm_ms) if gemm_ms else None
     flops = 2.0 * NQ * NB * D
     tf32_peak = bf16 / 2.0  # TF32 dense rate is half the BF16 rate (nominal ratio)
-    traffic = None
+    traffic = measured_traffic("dist_gemm_tf32x3")
     roof = {"bound": "tensor", "kernel": "dist_gemm_tf32x3 (3 TF32 passes per product)",
             "achieved": flops / (gemm_avg / 1e3) / 1e12 if gemm_avg else None,
             "peak": tf32_peak, "unit": "TFLOP/s",
