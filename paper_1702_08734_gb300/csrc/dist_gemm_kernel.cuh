@@ -24,6 +24,22 @@ __host__ __device__ inline GemmSmemLayout gemm_smem_layout(int pieces, int nkb, 
   return L;
 }
 
+// Candidate lists live in global memory and are re-read by every merge; the streamed
+// database would push them out of L2, so their accesses carry an evict-last policy.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t ld_keep(const uint64_t* p, uint64_t pol) {
+  uint64_t v;
+  asm volatile("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_keep(uint64_t* p, uint64_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+
 // Three-input min / max (sm_100 family); as with the two-input forms a NaN input is
 // ignored unless every input is NaN.
 __device__ __forceinline__ float min3f(float a, float b, float c) {
@@ -64,7 +80,7 @@ __device__ __forceinline__ float batch_best32(const float (&v)[32]) {
 template <int KPR, bool LARGEST>
 __device__ __forceinline__ void merge_queues(int limit, int& cnt, float& thr, const uint2* sQ,
                                              uint64_t* part, int64_t rowstride, int k,
-                                             int quarter, int lane) {
+                                             int quarter, int lane, uint64_t pol) {
   if constexpr (KPR == 0) return;  // k = 1 keeps no lists
   constexpr int KR = KPR > 0 ? KPR : 1;
   unsigned m = __ballot_sync(FULL_MASK, cnt > limit);
@@ -83,10 +99,10 @@ __device__ __forceinline__ void merge_queues(int limit, int& cnt, float& thr, co
     uint64_t* Lg = part + (int64_t)l * rowstride;
     uint64_t L[KR];
 #pragma unroll
-    for (int r = 0; r < KR; r++) L[r] = Lg[r * 32 + lane];
+    for (int r = 0; r < KR; r++) L[r] = ld_keep(Lg + r * 32 + lane, pol);
     warp_merge_list<KR>(L, v);
 #pragma unroll
-    for (int r = 0; r < KR; r++) Lg[r * 32 + lane] = L[r];
+    for (int r = 0; r < KR; r++) st_keep(Lg + r * 32 + lane, L[r], pol);
     // new threshold: element k-1 of the list
     const int kk = k - 1;
     uint64_t tk = 0;
@@ -265,6 +281,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
     uint64_t* myQ = sQ + (half * GEMM_BM + qrow) * GEMM_QSTRIDE;
     float* sY = reinterpret_cast<float*>(smem + lay.y_off) + (warp - 2) * 256;  // norms, scales
     const int lists = args.chunks * EPI;   // candidate lists per query
+    const uint64_t lpol = l2_keep_policy();
     const bool vec_out = MODE == MODE_STORE && (args.ldo & 3) == 0 &&
                          (reinterpret_cast<uintptr_t>(args.out) & 15) == 0;
     uint32_t gtile = 0;
@@ -297,7 +314,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
             const int qq = qt * GEMM_BM + quarter * 32 + j;
             if (qq < args.nq) {
               uint64_t* Lg = args.part + ((int64_t)qq * lists + ch * EPI + half) * args.kp;
-              for (int r = lane; r < args.kp; r += 32) Lg[r] = ~0ull;
+              for (int r = lane; r < args.kp; r += 32) st_keep(Lg + r, ~0ull, lpol);
             }
           }
           __syncwarp();
@@ -420,7 +437,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
                   }
                 }
                 merge_queues<KPR, LARGEST>(GEMM_QCAP - 16, cnt, thr, sQh, pbase, rowstride,
-                                           args.k, quarter, lane);
+                                           args.k, quarter, lane, lpol);
               }
             }
           }
@@ -473,11 +490,12 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       if (!ok) break;
       if (MODE == MODE_SELECT) {
         if (QUEUES) {
-          merge_queues<KPR, LARGEST>(0, cnt, thr, sQh, pbase, rowstride, args.k, quarter, lane);
+          merge_queues<KPR, LARGEST>(0, cnt, thr, sQh, pbase, rowstride, args.k, quarter, lane,
+                                     lpol);
           // publish this chunk's k-th distance as an upper bound for later chunks
           if (qvalid) {
             const uint64_t* Lg = args.part + ((int64_t)q * lists + ch * EPI + half) * args.kp;
-            const uint64_t tk = Lg[args.k - 1];
+            const uint64_t tk = ld_keep(Lg + args.k - 1, lpol);
             if (tk != ~0ull) atomicMin(&args.thr_key[q], (uint32_t)(tk >> 32));
           }
         } else if (qvalid) {
