@@ -230,3 +230,11 @@ def test_clustered_near_duplicates_in_one_tile(gbk):
     assert np.all(ex <= Do[:, -1:] + 2e-4)
     assert all(len(set(r.tolist())) == k for r in I)
     assert np.array_equal(np.sort(I[2:], axis=1), np.sort(Io[2:], axis=1))
+
+
+def test_small_exact_configuration(gbk):
+    # the small exact configuration: database 65,536 x 128 and 1,024 queries, N(0,1), k = 10
+    xb = datagen.gaussian_matrix(101, 65536, 128)
+    xq = datagen.gaussian_matrix(102, 1024, 128)
+    D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), 10)
+    _check_knn(xq, xb, D, I, 10)
