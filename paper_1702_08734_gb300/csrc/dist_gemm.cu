@@ -176,9 +176,34 @@ gbk_status launch_knn_merge(const uint64_t* part, int64_t nq, int chunks, int kp
   return GBK_OK;
 }
 
+// k = 1: a thread per query takes the least composite over its chunks.
+__global__ void knn_merge_k1_kernel(const uint64_t* __restrict__ part, int64_t nq, int chunks,
+                                    int kp, const float* __restrict__ xnorm, int largest,
+                                    float* __restrict__ D, int64_t* __restrict__ I) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  uint64_t best = ~0ull;
+  for (int c = 0; c < chunks; c++) best = min(best, part[(q * chunks + c) * kp]);
+  if (best == ~0ull) {
+    D[q] = largest ? -INFINITY : INFINITY;
+    I[q] = -1;
+  } else {
+    float dv = key_value((uint32_t)(best >> 32), largest != 0);
+    if (!largest) dv = fmaxf(dv + xnorm[q], 0.f);
+    D[q] = dv;
+    I[q] = (int64_t)(uint32_t)best;
+  }
+}
+
 gbk_status knn_merge(const uint64_t* part, int64_t nq, int chunks, int kp, int k,
                      const float* xnorm, int largest, float* D, int64_t* I, cudaStream_t st) {
   ProfScope prof("knn_merge", st);
+  if (k == 1) {
+    knn_merge_k1_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(part, nq, chunks, kp, xnorm,
+                                                                      largest, D, I);
+    GBK_LAUNCH_CHECK();
+    return GBK_OK;
+  }
   if (k <= 32) return launch_knn_merge<32>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);
   if (k <= 64) return launch_knn_merge<64>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);
   if (k <= 128) return launch_knn_merge<128>(part, nq, chunks, kp, k, xnorm, largest, D, I, st);

@@ -23,10 +23,14 @@ namespace gbk {
 
 // --------------------------------------------------------------------- encoding
 
-// One thread per (vector, sub-quantizer): residual sub-vector (float32), nearest of the 256
-// centroids by direct float32 distance (ties to the lowest), byte written to codes.
-// Shared memory holds all codebooks as [c][t][m] (broadcast across the M lanes of a vector).
-__global__ void __launch_bounds__(256)
+// Residual sub-vector (float32) of each (vector, sub-quantizer) and the nearest of its 256
+// centroids by direct float32 distance, summed over the dsub coordinates in order (ties to
+// the lowest), written to codes.  Persistent blocks hold all codebooks in shared memory as
+// [c][t][m] (consecutive lanes = consecutive sub-quantizers: conflict-free) and loop over
+// the vectors; each thread serves V vectors of one sub-quantizer, so every codebook read
+// feeds V distance updates.
+template <int DS, int V>
+__global__ void __launch_bounds__(512)
     pq_encode_kernel(const float* __restrict__ x, int64_t n, int d, int M,
                      const float* __restrict__ coarse, const int32_t* __restrict__ lists,
                      const float* __restrict__ pq, uint8_t* __restrict__ codes) {
@@ -37,32 +41,53 @@ __global__ void __launch_bounds__(256)
     cb[(c * dsub + t) * M + m] = pq[i];
   }
   __syncthreads();
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n * M) return;
-  const int64_t v = p / M;
-  const int m = (int)(p % M);
-  const int64_t L = lists[v];
-  float r[32];
+  const int G = (int)blockDim.x / M;  // vector groups per block
+  const int m = (int)threadIdx.x % M, g = (int)threadIdx.x / M;
+  if (g >= G) return;
+  for (int64_t v0 = ((int64_t)blockIdx.x * G + g) * V; v0 < n; v0 += (int64_t)gridDim.x * G * V) {
+    float r[V][DS];
 #pragma unroll
-  for (int t = 0; t < 32; t++)
-    r[t] = t < dsub ? x[v * d + m * dsub + t] - coarse[L * d + m * dsub + t] : 0.f;
-  float best = __int_as_float(0x7f800000);
-  int bc = 0;
-  for (int c = 0; c < 256; c++) {
-    float s = 0.f;
+    for (int vv = 0; vv < V; vv++) {
+      const int64_t v = v0 + vv;
+      const int64_t L = v < n ? lists[v] : 0;
 #pragma unroll
-    for (int t = 0; t < 32; t++) {
-      if (t < dsub) {
-        const float e = r[t] - cb[(c * dsub + t) * M + m];
-        s = fmaf(e, e, s);
+      for (int t = 0; t < DS; t++)
+        r[vv][t] = (v < n && t < dsub) ? x[v * d + m * dsub + t] - coarse[L * d + m * dsub + t]
+                                       : 0.f;
+    }
+    float best[V];
+    int bc[V];
+#pragma unroll
+    for (int vv = 0; vv < V; vv++) {
+      best[vv] = __int_as_float(0x7f800000);
+      bc[vv] = 0;
+    }
+    for (int c = 0; c < 256; c++) {
+      float sum[V];
+#pragma unroll
+      for (int vv = 0; vv < V; vv++) sum[vv] = 0.f;
+#pragma unroll
+      for (int t = 0; t < DS; t++) {
+        if (t < dsub) {
+          const float cv = cb[(c * dsub + t) * M + m];
+#pragma unroll
+          for (int vv = 0; vv < V; vv++) {
+            const float e = r[vv][t] - cv;
+            sum[vv] = fmaf(e, e, sum[vv]);
+          }
+        }
       }
+#pragma unroll
+      for (int vv = 0; vv < V; vv++)
+        if (sum[vv] < best[vv]) {
+          best[vv] = sum[vv];
+          bc[vv] = c;
+        }
     }
-    if (s < best) {
-      best = s;
-      bc = c;
-    }
+#pragma unroll
+    for (int vv = 0; vv < V; vv++)
+      if (v0 + vv < n) codes[(v0 + vv) * M + m] = (uint8_t)bc[vv];
   }
-  codes[v * M + m] = (uint8_t)bc;
 }
 
 // T[L][c][m] = ||C_m[c]||^2 + 2 <c_L^m, C_m[c]>  (block per list, thread per (c, m)); the
@@ -469,20 +494,22 @@ gbk_status pq_encode_run(const float* x, int64_t n, int d, int M, const float* c
   if (d / M > 32) return set_error(GBK_EUNSUPPORTED, "PQ sub-vectors longer than 32");
   ProfScope prof("pq_encode", st);
   const size_t smem = sizeof(float) * 256 * (size_t)d;
-  static bool attr = false;
-  if (!attr) {
-    GBK_CUDA_CHECK(cudaFuncSetAttribute(pq_encode_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)device_info().smem_optin));
-    attr = true;
-  }
-  if (smem > device_info().smem_optin)
+  const DeviceInfo& di = device_info();
+  if (smem > di.smem_optin)
     return set_error(GBK_EUNSUPPORTED, "PQ codebooks do not fit in shared memory (d too large)");
-  const int64_t pairs = n * M;
-  pq_encode_kernel<<<(unsigned)((pairs + 255) / 256), 256, smem, st>>>(x, n, d, M, coarse, lists, pq,
-                                                                       codes);
-  GBK_LAUNCH_CHECK();
-  return GBK_OK;
+  const int dsub = d / M;
+  const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, di.smem_optin / smem));
+  const unsigned grid = (unsigned)(di.sm_count * per_sm);
+  auto go = [&](auto kern) -> gbk_status {
+    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)di.smem_optin));
+    kern<<<grid, 512, smem, st>>>(x, n, d, M, coarse, lists, pq, codes);
+    GBK_LAUNCH_CHECK();
+    return GBK_OK;
+  };
+  if (dsub <= 8) return go(pq_encode_kernel<8, 4>);
+  if (dsub <= 16) return go(pq_encode_kernel<16, 2>);
+  return go(pq_encode_kernel<32, 1>);
 }
 
 gbk_status term1_run(const float* coarse, const float* pq, int nlist, int d, int M, float* T,
