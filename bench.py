@@ -204,9 +204,10 @@ def recall_stats(g, I, Igt, k=10):
     return float(one.float().mean().item()), float(cnt.float().mean().item()) / k
 
 
-def build_ivfadc_index(g, datagen, n):
+def build_ivfadc_index(g, datagen, n, keep_vectors=False):
     """The IVFADC workload's index: 10M x 128 Gaussian mixture (4,096 centres N(0,4I), noise
-    N(0,I)), nlist 4,096, PQ 16 x 256 trained on 256K points of the same mixture."""
+    N(0,I)), nlist 4,096, PQ 16 x 256 trained on 256K points of the same mixture; with
+    keep_vectors the index also holds the float32 vectors for exact re-ranking."""
     import torch
     d, nlist, M = 128, 4096, 16
     t = {}
@@ -222,6 +223,8 @@ def build_ivfadc_index(g, datagen, n):
              pq_init=datagen.permutation_prefix(306, 262144, 256))
     torch.cuda.synchronize()
     t["train_s"] = time.perf_counter() - t0
+    if keep_vectors:
+        ix.keep_vectors()
     t0 = time.perf_counter()
     ix.add(xb)
     assert ix.ntotal == n
@@ -246,14 +249,17 @@ def time_search(g, fn, steps):
 
 def run_ivfadc(args):
     """IVFADC workload, k = 100, nprobe in {1,4,16,64,256}, 10K queries from the mixture;
-    ground truth by exact search; reports q/s with 1-R@10 and 10-R@10."""
+    ground truth by exact search; reports q/s with 1-R@10 and 10-R@10.  Then the same index
+    with exact re-ranking of 1,000 ADC candidates, and IVF-Flat over the same vectors and
+    coarse quantizer."""
+    import numpy as np
     import torch
 
     import paper_1702_08734_gb300 as g
     from paper_1702_08734_gb300 import datagen
     g.load()
     nq, k = 10000, 100
-    ix, cen, xb, t = build_ivfadc_index(g, datagen, args.ivf_n)
+    ix, cen, xb, t = build_ivfadc_index(g, datagen, args.ivf_n, keep_vectors=True)
     xq = datagen.mixture_points_cuda(cen, 304, nq)
     t0 = time.perf_counter()
     _, Igt = g.knn_brute(xq, xb, k)
@@ -269,8 +275,46 @@ def run_ivfadc(args):
         r1, r10 = recall_stats(g, I, Igt)
         rows.append({"nprobe": nprobe, "ms": ms, "qps": nq / (ms / 1e3), "R1@10": r1,
                      "R10@10": r10, "scan_ms": sum(scan) / max(1, len(scan))})
+    # IVFADC + exact float32 re-rank of k' = 1000 ADC candidates from the kept vectors
+    refine = []
+    for nprobe in (1, 4, 16, 64):
+        g.profile_enable(True)
+        ms, (D, I) = time_search(g, lambda: ix.search_refine(xq, k, nprobe, 1000), args.steps)
+        g.profile_enable(False)
+        by = {}
+        for nm, tt in g.profile_read():
+            by.setdefault(nm, []).append(tt)
+        r1, r10 = recall_stats(g, I, Igt)
+        refine.append({"nprobe": nprobe, "kprime": 1000, "ms": ms, "qps": nq / (ms / 1e3),
+                       "R1@10": r1, "R10@10": r10,
+                       "kernel_ms": {kk: sum(v) / len(v) for kk, v in by.items()}})
+    # IVF-Flat on the same vectors and coarse quantizer: exact list scan
+    ex = ix.export()
+    coarse = torch.from_numpy(ex["coarse"]).cuda()
+    del ix
+    torch.cuda.empty_cache()
+    fx = g.IVFFlatIndex(128, 4096).set_centroids(coarse)
+    t0 = time.perf_counter()
+    fx.add(xb)
+    fx.search(xq[:1], 1, 1)  # builds the lists
+    torch.cuda.synchronize()
+    t["flat_add_s"] = time.perf_counter() - t0
+    sizes = torch.from_numpy(np.diff(fx.export()["list_off"])).cuda()
+    flat = []
+    for nprobe in (1, 4, 16, 64):
+        g.profile_enable(True)
+        ms, (D, I) = time_search(g, lambda: fx.search(xq, k, nprobe), args.steps)
+        g.profile_enable(False)
+        scan = [tt for nm, tt in g.profile_read() if nm == "ivf_flat_scan"]
+        scan_ms = sum(scan) / max(1, len(scan))
+        _, clI = g.knn_brute(xq, coarse, nprobe)
+        nbytes = float(sizes[clI].sum().item()) * 128 * 4  # algorithmic: every probed vector once
+        r1, r10 = recall_stats(g, I, Igt)
+        flat.append({"nprobe": nprobe, "ms": ms, "qps": nq / (ms / 1e3), "R1@10": r1,
+                     "R10@10": r10, "scan_ms": scan_ms,
+                     "scan_algorithmic_GBps": nbytes / (scan_ms * 1e-3) / 1e9})
     print(json.dumps({"workload": "ivfadc nb=%d d=128 nlist=4096 M=16 nq=1e4 k=100" % args.ivf_n,
-                      **t, "results": rows}), flush=True)
+                      **t, "results": rows, "refine": refine, "ivfflat": flat}), flush=True)
 
 
 def run_learned(args):

@@ -253,6 +253,58 @@ gbk_status gbk_ivfpq_info(gbk_index* index, int64_t* ntotal, int32_t* nlist, int
 gbk_status gbk_ivfpq_export(gbk_index* index, float* coarse, float* pq, int64_t* list_off,
                             uint8_t* codes, int64_t* ids, void* stream);
 
+/* Keep a float32 copy of every vector added from now on (n*d*4 bytes of device memory, in
+ * list order), for gbk_ivfpq_search_refine.  Must be set before the first add. */
+gbk_status gbk_ivfpq_keep_vectors(gbk_index* index, int32_t keep);
+
+/* IVFADC with exact re-ranking: the kprime best ADC candidates of each query (Algorithm 4,
+ * as gbk_ivfpq_search), then their exact squared distances sum_t (x_t - y_t)^2 (Eq. 1)
+ * computed in float32 from the kept vectors, and the k smallest of those.  D [nq][k]
+ * ascending, I [nq][k] ids; equal distances by list position; (+inf, -1) padding when
+ * fewer than k candidates exist.  1 <= k <= kprime <= GBK_MAX_K; d <= 1024; EINVAL when
+ * the index keeps no vectors. */
+gbk_status gbk_ivfpq_search_refine(gbk_index* index, const float* xq, int64_t nq, int32_t k,
+                                   int32_t nprobe, int32_t kprime, float* D, int64_t* I,
+                                   void* stream);
+
+/* ------------------------------------------------------------------ IVF-Flat */
+
+/* Inverted file with uncompressed lists (section 2's inverted file with the float32 vectors
+ * stored in place of codes; section 5.1's exact stage as the list scan).  The same coarse
+ * quantizer q1 as IVFADC; the scan computes exact squared distances sum_t (x_t - y_t)^2 in
+ * float32 (8 partial sums per vector, then a fixed butterfly) and keeps the k smallest.
+ * L2 only (EUNSUPPORTED otherwise); 1 <= d <= 4096. */
+typedef struct gbk_ivfflat gbk_ivfflat;
+gbk_status gbk_ivfflat_create(int32_t d, int32_t nlist, int32_t metric, gbk_ivfflat** out);
+void gbk_ivfflat_destroy(gbk_ivfflat* index);
+
+/* q1 by k-means on x [n][d] (device); opts->niter and opts->coarse_init as for IVFADC,
+ * other fields ignored.  nlist <= n < 2^31. */
+gbk_status gbk_ivfflat_train(gbk_ivfflat* index, const float* x, int64_t n,
+                             const gbk_train_opts* opts, void* stream);
+
+/* Install externally trained coarse centroids [nlist][d] (device or host float32). */
+gbk_status gbk_ivfflat_set_centroids(gbk_ivfflat* index, const float* coarse, void* stream);
+
+/* Append x [n][d] (device) to the list of its nearest centroid (ties lowest); ids as for
+ * gbk_ivfpq_add.  At most 2^32 - 1 vectors. */
+gbk_status gbk_ivfflat_add(gbk_ivfflat* index, const float* x, int64_t n, const int64_t* ids,
+                           void* stream);
+
+/* The nprobe nearest centroids (Eq. 5), exact distances to every vector of those lists, k
+ * smallest: D [nq][k] ascending, I [nq][k] ids, equal distances by list position, (+inf, -1)
+ * padding.  1 <= k, nprobe <= GBK_MAX_K, nprobe <= nlist. */
+gbk_status gbk_ivfflat_search(gbk_ivfflat* index, const float* xq, int64_t nq, int32_t k,
+                              int32_t nprobe, float* D, int64_t* I, void* stream);
+
+gbk_status gbk_ivfflat_info(gbk_ivfflat* index, int64_t* ntotal, int32_t* nlist, int32_t* d,
+                            void* stream);
+
+/* Copy out (any pointer may be NULL; host or device): coarse [nlist][d], list_off [nlist+1],
+ * ids [ntotal] in list order. */
+gbk_status gbk_ivfflat_export(gbk_ivfflat* index, float* coarse, int64_t* list_off, int64_t* ids,
+                              void* stream);
+
 /* ------------------------------------------------------------------ learned nprobe */
 
 /* A small multilayer perceptron f -> relu(W1 f + b1) -> relu(W2 . + b2) -> W3 . + b3 that

@@ -16,6 +16,9 @@ marshals numpy arrays.  Functions and the passages they follow:
 * ``ivfpq_encode`` - q1 + product-quantizer codes (section 2)
 * ``ivf_bucket``   - the inverted file, lists in insertion order (section 2)
 * ``ivfadc_search``- Algorithm 4 / Eq. (5), (6) and (10)
+* ``ivfflat_search``- the inverted file of section 2 with uncompressed lists: Eq. (5) for
+  the probed lists, then Eq. (1) directly for their vectors
+* ``ivfadc_refine`` - Algorithm 4 for k' candidates, then Eq. (1) for those and the k best
 """
 from __future__ import annotations
 
@@ -70,6 +73,8 @@ def _load():
             lib.or_ivfadc_search.argtypes = [_f32p, _i64, _i32, _f32p, _i32, _f32p, _i32, _i64p,
                                              _u8p, _i64p, _i32, _i32, _i32, _f64p, _i64p, _i64p,
                                              ctypes.c_int]
+            lib.or_ivfflat_search.argtypes = [_f32p, _i64, _i32, _f32p, _i32, _i64p, _f32p,
+                                              _i64p, _i32, _i32, _f64p, _i64p, ctypes.c_int]
             lib.or_default_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -227,3 +232,41 @@ def ivfadc_search(xq, coarse, pq, offsets, codes, ids, k: int, nprobe: int, form
                                     0 if form == "recon" else 1, _p(D, _f64p), _p(I, _i64p),
                                     _p(probes, _i64p), threads))
     return (D, I, probes) if return_probes else (D, I)
+
+
+def ivfflat_search(xq, coarse, offsets, vecs, ids, k: int, nprobe: int, threads: int = 0):
+    """IVF-Flat search: the nprobe nearest centroids (exact, ties to the lower list), exact
+    double-precision distances to every vector of those lists (``vecs`` and ``ids`` in list
+    order), k smallest by (distance, id), (+inf, -1) padding."""
+    xq = _c(xq, np.float32)
+    coarse = _c(coarse, np.float32)
+    offsets = _c(offsets, np.int64)
+    vecs = _c(vecs, np.float32)
+    ids = _c(ids, np.int64)
+    nq, d = xq.shape
+    D = np.empty((nq, k), np.float64)
+    I = np.empty((nq, k), np.int64)
+    _check(_load().or_ivfflat_search(_p(xq, _f32p), nq, d, _p(coarse, _f32p), coarse.shape[0],
+                                     _p(offsets, _i64p), _p(vecs, _f32p), _p(ids, _i64p), k,
+                                     nprobe, _p(D, _f64p), _p(I, _i64p), threads))
+    return D, I
+
+
+def ivfadc_refine(xq, xb, coarse, pq, offsets, codes, ids, k: int, nprobe: int, kprime: int,
+                  threads: int = 0):
+    """IVFADC followed by exact re-ranking: the kprime best ADC candidates (Algorithm 4),
+    their exact distances (Eq. 1, double) to the vectors xb[id], and the k best by
+    (distance, id); (+inf, -1) padding.  Also returns the candidates' ADC distances and ids."""
+    Dc, Ic = ivfadc_search(xq, coarse, pq, offsets, codes, ids, kprime, nprobe, threads=threads)
+    nq = Dc.shape[0]
+    D = np.full((nq, k), np.inf)
+    I = np.full((nq, k), -1, np.int64)
+    for q in range(nq):
+        cand = Ic[q][Ic[q] >= 0]
+        if cand.size == 0:
+            continue
+        ex = pair_dist(xq, xb, np.full(cand.size, q), cand)
+        o = np.lexsort((cand, ex))[:k]
+        D[q, :o.size] = ex[o]
+        I[q, :o.size] = cand[o]
+    return D, I, Dc, Ic

@@ -618,3 +618,76 @@ int or_ivfadc_search(const float* xq, int64_t nq, int32_t d, const float* coarse
   parallel_for(nq, nthreads, ivf_rows, &c);
   return OR_OK;
 }
+
+/* ------------------------------------------------------------------ IVF-Flat search */
+/* The inverted file of section 2 with the vectors themselves in the lists: the nprobe
+ * nearest centroids by exact double distance (ties to the lower list), then Eq. (1)
+ * evaluated directly for every vector of those lists, k smallest by (distance, id). */
+typedef struct {
+  const float *xq, *coarse, *vecs;
+  int32_t d, nlist, k, nprobe;
+  const int64_t* offsets;
+  const int64_t* ids;
+  double* outD;
+  int64_t* outI;
+} flat_ctx;
+
+static void flat_rows(void* p, int64_t q0, int64_t q1) {
+  flat_ctx* c = (flat_ctx*)p;
+  const int32_t d = c->d;
+  kheap coarse_h, h;
+  coarse_h.v = (double*)malloc(sizeof(double) * (size_t)c->nprobe);
+  coarse_h.id = (int64_t*)malloc(sizeof(int64_t) * (size_t)c->nprobe);
+  coarse_h.cap = c->nprobe;
+  coarse_h.largest = 0;
+  h.v = (double*)malloc(sizeof(double) * (size_t)(c->k > 0 ? c->k : 1));
+  h.id = (int64_t*)malloc(sizeof(int64_t) * (size_t)(c->k > 0 ? c->k : 1));
+  h.cap = c->k;
+  h.largest = 0;
+  double* cd = (double*)malloc(sizeof(double) * (size_t)c->nprobe);
+  int64_t* cl = (int64_t*)malloc(sizeof(int64_t) * (size_t)c->nprobe);
+  for (int64_t q = q0; q < q1; q++) {
+    const float* x = c->xq + q * d;
+    coarse_h.size = 0;
+    for (int32_t L = 0; L < c->nlist; L++) {
+      const float* cc = c->coarse + (int64_t)L * d;
+      double s = 0.0;
+      for (int32_t t = 0; t < d; t++) {
+        double e = (double)x[t] - (double)cc[t];
+        s += e * e;
+      }
+      heap_push(&coarse_h, s, L);
+    }
+    heap_drain_sorted(&coarse_h, cd, cl, c->nprobe, INFINITY);
+    h.size = 0;
+    for (int32_t pi = 0; pi < c->nprobe; pi++) {
+      const int64_t L = cl[pi];
+      if (L < 0) continue;
+      for (int64_t j = c->offsets[L]; j < c->offsets[L + 1]; j++) {
+        const float* y = c->vecs + j * d;
+        double s = 0.0;
+        for (int32_t t = 0; t < d; t++) {
+          double e = (double)x[t] - (double)y[t];
+          s += e * e;
+        }
+        heap_push(&h, s, c->ids[j]);
+      }
+    }
+    heap_drain_sorted(&h, c->outD + q * c->k, c->outI + q * c->k, c->k, INFINITY);
+  }
+  free(coarse_h.v);
+  free(coarse_h.id);
+  free(h.v);
+  free(h.id);
+  free(cd);
+  free(cl);
+}
+
+int or_ivfflat_search(const float* xq, int64_t nq, int32_t d, const float* coarse, int32_t nlist,
+                      const int64_t* offsets, const float* vecs, const int64_t* ids, int32_t k,
+                      int32_t nprobe, double* outD, int64_t* outI, int nthreads) {
+  if (nq < 0 || d <= 0 || k < 0 || nprobe < 1 || nprobe > nlist) return OR_EINVAL;
+  flat_ctx c = {xq, coarse, vecs, d, nlist, k, nprobe, offsets, ids, outD, outI};
+  parallel_for(nq, nthreads, flat_rows, &c);
+  return OR_OK;
+}

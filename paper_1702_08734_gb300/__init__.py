@@ -225,6 +225,15 @@ _SIGNATURES.update({
     "gbk_ivfpq_search": [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp],
     "gbk_ivfpq_info": [_vp, _vp, _vp, _vp, _vp, _vp],
     "gbk_ivfpq_export": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "gbk_ivfpq_keep_vectors": [_vp, _i32],
+    "gbk_ivfpq_search_refine": [_vp, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp],
+    "gbk_ivfflat_create": [_i32, _i32, _i32, _vp],
+    "gbk_ivfflat_train": [_vp, _vp, _i64, _vp, _vp],
+    "gbk_ivfflat_set_centroids": [_vp, _vp, _vp],
+    "gbk_ivfflat_add": [_vp, _vp, _i64, _vp, _vp],
+    "gbk_ivfflat_search": [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp],
+    "gbk_ivfflat_info": [_vp, _vp, _vp, _vp, _vp],
+    "gbk_ivfflat_export": [_vp, _vp, _vp, _vp, _vp],
 })
 
 
@@ -312,6 +321,24 @@ class IVFPQIndex:
               _stream())
         return D, I
 
+    def keep_vectors(self, keep: bool = True):
+        """Keep float32 copies of the vectors added from now on (for search_refine)."""
+        _call("gbk_ivfpq_keep_vectors", self._h, int(bool(keep)))
+        return self
+
+    def search_refine(self, xq: torch.Tensor, k: int, nprobe: int, kprime: int, out=None):
+        """kprime ADC candidates per query, re-ranked by exact float32 distances to k."""
+        _dev(xq, torch.float32, "xq")
+        nq = xq.shape[0]
+        if out is None:
+            D = torch.empty((nq, k), dtype=torch.float32, device=xq.device)
+            I = torch.empty((nq, k), dtype=torch.int64, device=xq.device)
+        else:
+            D, I = out
+        _call("gbk_ivfpq_search_refine", self._h, _ptr(xq), nq, int(k), int(nprobe), int(kprime),
+              _ptr(D), _ptr(I), _stream())
+        return D, I
+
     @property
     def ntotal(self):
         n = ctypes.c_int64()
@@ -332,6 +359,73 @@ class IVFPQIndex:
               _stream())
         torch.cuda.current_stream().synchronize()
         return {"coarse": coarse, "pq": pq, "list_off": off, "codes": codes[:n], "ids": ids[:n]}
+
+
+class IVFFlatIndex:
+    """Inverted file with float32 lists: coarse quantizer + exact list scan on the GPU."""
+
+    def __init__(self, d: int, nlist: int, metric="l2"):
+        self.d, self.nlist = int(d), int(nlist)
+        h = ctypes.c_void_p()
+        _call("gbk_ivfflat_create", self.d, self.nlist, _metric(metric), ctypes.byref(h))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.gbk_ivfflat_destroy(self._h)
+            self._h = None
+
+    def train(self, x: torch.Tensor, niter: int = 20, coarse_init=None):
+        _dev(x, torch.float32, "x")
+        ci = cip = None
+        if coarse_init is not None:
+            ci, cip = _host_i64(coarse_init)
+        o = TrainOpts(int(niter), 0, cip, None, 0)
+        _call("gbk_ivfflat_train", self._h, _ptr(x), x.shape[0], ctypes.byref(o), _stream())
+        torch.cuda.current_stream().synchronize()
+        return self
+
+    def set_centroids(self, coarse: torch.Tensor):
+        _dev(coarse, torch.float32, "coarse")
+        _call("gbk_ivfflat_set_centroids", self._h, _ptr(coarse), _stream())
+        return self
+
+    def add(self, x: torch.Tensor, ids: torch.Tensor = None):
+        _dev(x, torch.float32, "x")
+        if ids is not None:
+            _dev(ids, torch.int64, "ids")
+        _call("gbk_ivfflat_add", self._h, _ptr(x), x.shape[0], _ptr(ids), _stream())
+        return self
+
+    def search(self, xq: torch.Tensor, k: int, nprobe: int, out=None):
+        _dev(xq, torch.float32, "xq")
+        nq = xq.shape[0]
+        if out is None:
+            D = torch.empty((nq, k), dtype=torch.float32, device=xq.device)
+            I = torch.empty((nq, k), dtype=torch.int64, device=xq.device)
+        else:
+            D, I = out
+        _call("gbk_ivfflat_search", self._h, _ptr(xq), nq, int(k), int(nprobe), _ptr(D), _ptr(I),
+              _stream())
+        return D, I
+
+    @property
+    def ntotal(self):
+        n = ctypes.c_int64()
+        _call("gbk_ivfflat_info", self._h, ctypes.byref(n), None, None, _stream())
+        return n.value
+
+    def export(self):
+        """Host copies: coarse [nlist][d], list_off [nlist+1], ids [ntotal] in list order."""
+        import numpy as np
+        n = self.ntotal
+        coarse = np.empty((self.nlist, self.d), np.float32)
+        off = np.empty(self.nlist + 1, np.int64)
+        ids = np.empty(max(n, 1), np.int64)
+        _call("gbk_ivfflat_export", self._h, coarse.ctypes.data_as(_vp), off.ctypes.data_as(_vp),
+              ids.ctypes.data_as(_vp), _stream())
+        torch.cuda.current_stream().synchronize()
+        return {"coarse": coarse, "list_off": off, "ids": ids[:n]}
 
 
 # ---------------------------------------------------------------------------- learned nprobe MLP

@@ -28,47 +28,6 @@ gbk_status term1_run(const float* coarse, const float* pq, int nlist, int d, int
 gbk_status term3_run(const float* xq, int64_t nq, const float* pq, int d, int M, float* t3,
                      cudaStream_t st);
 
-// Persistent device allocation owned by an index (freed in gbk_ivfpq_destroy).
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-  gbk_status alloc(size_t b) {
-    release();
-    if (b == 0) return GBK_OK;
-    if (cudaMalloc(&p, b) != cudaSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-      return set_error(GBK_ENOMEM, "cudaMalloc(%zu) failed for index storage", b);
-    }
-    bytes = b;
-    return GBK_OK;
-  }
-  // grow to at least b bytes, keeping the first `keep` bytes (stream-ordered copy)
-  gbk_status grow(size_t b, size_t keep, cudaStream_t st) {
-    if (b <= bytes) return GBK_OK;
-    void* q = nullptr;
-    if (cudaMalloc(&q, b) != cudaSuccess) {
-      cudaGetLastError();
-      return set_error(GBK_ENOMEM, "cudaMalloc(%zu) failed for index storage", b);
-    }
-    if (keep) GBK_CUDA_CHECK(cudaMemcpyAsync(q, p, keep, cudaMemcpyDeviceToDevice, st));
-    GBK_CUDA_CHECK(cudaStreamSynchronize(st));
-    release();
-    p = q;
-    bytes = b;
-    return GBK_OK;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-  }
-  template <class T>
-  T* as() const {
-    return static_cast<T*>(p);
-  }
-};
-
 }  // namespace gbk
 
 struct gbk_index {
@@ -81,6 +40,9 @@ struct gbk_index {
   int64_t n_staged = 0, cap_staged = 0;
   // inverted file (built from the staging arrays on demand)
   gbk::DevBuf list_off, codes, ids;
+  // optional float32 copies of the added vectors (exact re-rank): staged, then list order
+  bool keep_vectors = false;
+  gbk::DevBuf st_vecs, vecs;
   int64_t ntotal = 0;
   bool dirty = true;
   int64_t max_list = 0;
@@ -95,6 +57,8 @@ struct gbk_index {
     list_off.release();
     codes.release();
     ids.release();
+    st_vecs.release();
+    vecs.release();
   }
 };
 
@@ -102,7 +66,7 @@ namespace gbk {
 
 // Algorithm 4 for a validated, finalized index (below).
 gbk_status search_run(gbk_index* ix, const float* xq, int64_t nq, int k, int nprobe, float* D,
-                      int64_t* I, cudaStream_t st);
+                      int64_t* I, cudaStream_t st, bool positions = false);
 
 namespace {
 
@@ -173,6 +137,13 @@ gbk_status finalize(gbk_index* ix, cudaStream_t st) {
                                                      ix->st_ids.as<int64_t>(),
                                                      ix->ids.as<int64_t>());
     GBK_LAUNCH_CHECK();
+  }
+  if (ix->keep_vectors) {
+    if ((r = ix->vecs.alloc(sizeof(float) * (size_t)std::max<int64_t>(n, 1) * ix->d)) != GBK_OK)
+      return r;
+    if ((r = gather_rows_run(ix->st_vecs.as<float>(), order.as<int64_t>(), n, ix->d,
+                             ix->vecs.as<float>(), st)) != GBK_OK)
+      return r;
   }
   ix->ntotal = n;
   ix->dirty = false;
@@ -310,8 +281,15 @@ gbk_status gbk_ivfpq_add(gbk_index* ix, const float* x, int64_t n, const int64_t
     if ((r = ix->st_list.grow(sizeof(int32_t) * cap, sizeof(int32_t) * keep, st)) != GBK_OK) return r;
     if ((r = ix->st_codes.grow((size_t)cap * ix->M, keep * ix->M, st)) != GBK_OK) return r;
     if ((r = ix->st_ids.grow(sizeof(int64_t) * cap, sizeof(int64_t) * keep, st)) != GBK_OK) return r;
+    if (ix->keep_vectors &&
+        (r = ix->st_vecs.grow(sizeof(float) * ix->d * cap, sizeof(float) * ix->d * keep, st)) !=
+            GBK_OK)
+      return r;
     ix->cap_staged = cap;
   }
+  if (ix->keep_vectors)
+    GBK_CUDA_CHECK(cudaMemcpyAsync(ix->st_vecs.as<float>() + (size_t)ix->n_staged * ix->d, x,
+                                   sizeof(float) * ix->d * (size_t)n, cudaMemcpyDeviceToDevice, st));
   Scratch a, dist;
   if ((r = a.alloc(sizeof(int64_t) * (size_t)n, st)) != GBK_OK) return r;
   if ((r = dist.alloc(sizeof(float) * (size_t)n, st)) != GBK_OK) return r;
@@ -350,12 +328,53 @@ gbk_status gbk_ivfpq_search(gbk_index* ix, const float* xq, int64_t nq, int32_t 
   return gbk::search_run(ix, xq, nq, k, nprobe, D, I, st);
 }
 
+gbk_status gbk_ivfpq_keep_vectors(gbk_index* ix, int32_t keep) {
+  clear_error();
+  GBK_REQUIRE(ix, "gbk_ivfpq_keep_vectors: NULL index");
+  GBK_REQUIRE(ix->n_staged == 0 || (keep != 0) == ix->keep_vectors,
+              "gbk_ivfpq_keep_vectors: must be set before the first add");
+  ix->keep_vectors = keep != 0;
+  return GBK_OK;
+}
+
+gbk_status gbk_ivfpq_search_refine(gbk_index* ix, const float* xq, int64_t nq, int32_t k,
+                                   int32_t nprobe, int32_t kprime, float* D, int64_t* I,
+                                   void* stream) {
+  clear_error();
+  GBK_REQUIRE(ix, "gbk_ivfpq_search_refine: NULL index");
+  GBK_REQUIRE(ix->trained, "gbk_ivfpq_search_refine: index not trained");
+  GBK_REQUIRE(ix->keep_vectors,
+              "gbk_ivfpq_search_refine: the index keeps no vectors (gbk_ivfpq_keep_vectors)");
+  GBK_REQUIRE(k >= 1 && kprime >= k && kprime <= GBK_MAX_K,
+              "gbk_ivfpq_search_refine: need 1 <= k <= kprime <= %d", GBK_MAX_K);
+  GBK_REQUIRE(nprobe >= 1 && nprobe <= ix->nlist && nprobe <= GBK_MAX_K,
+              "gbk_ivfpq_search_refine: nprobe out of [1, min(nlist, %d)]", GBK_MAX_K);
+  GBK_REQUIRE(nq >= 0 && nq < (int64_t(1) << 31), "gbk_ivfpq_search_refine: nq out of range");
+  if (nq == 0) return GBK_OK;
+  GBK_REQUIRE(xq && D && I, "gbk_ivfpq_search_refine: NULL pointer");
+  GBK_REQUIRE(ix->d <= 1024, "gbk_ivfpq_search_refine: d <= 1024");
+  cudaStream_t st = as_stream(stream);
+  gbk_status r;
+  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  Scratch Dc, Ic;
+  if ((r = Dc.alloc(sizeof(float) * (size_t)nq * kprime, st)) != GBK_OK) return r;
+  if ((r = Ic.alloc(sizeof(int64_t) * (size_t)nq * kprime, st)) != GBK_OK) return r;
+  // k' ADC candidates as list positions, exact distances from the stored vectors, top k
+  if ((r = gbk::search_run(ix, xq, nq, kprime, nprobe, Dc.as<float>(), Ic.as<int64_t>(), st,
+                           true)) != GBK_OK)
+    return r;
+  if ((r = rerank_rows_run(xq, ix->vecs.as<float>(), nq, ix->d, kprime, k, Ic.as<int64_t>(), D, I,
+                           st)) != GBK_OK)
+    return r;
+  return rows_to_ids_run(I, nq * (int64_t)k, ix->ids.as<int64_t>(), st);
+}
+
 }  // extern "C"
 
 namespace gbk {
 // Algorithm 4 for a validated, finalized index.
 gbk_status search_run(gbk_index* ix, const float* xq, int64_t nq, int k, int nprobe, float* D,
-                      int64_t* I, cudaStream_t st) {
+                      int64_t* I, cudaStream_t st, bool positions) {
   gbk_status r;
   Scratch clD, clI, t3;
   if ((r = clD.alloc(sizeof(float) * (size_t)nq * nprobe, st)) != GBK_OK) return r;
@@ -374,8 +393,8 @@ gbk_status search_run(gbk_index* ix, const float* xq, int64_t nq, int k, int npr
   return ivf_scan_run(ix->M, nq, nprobe, k, clI.as<int64_t>(), clD.as<float>(), ix->T.as<float>(),
                       t3.as<float>(), xq, ix->coarse.as<float>(), ix->pq.as<float>(), ix->d,
                       direct, ix->list_off.as<int64_t>(), ix->codes.as<uint8_t>(),
-                      ix->ids.as<int64_t>(), D, I, st, nullptr, nullptr, nullptr, nullptr,
-                      nullptr, ix->tuning);
+                      positions ? nullptr : ix->ids.as<int64_t>(), D, I, st, nullptr, nullptr,
+                      nullptr, nullptr, nullptr, ix->tuning);
 }
 }  // namespace gbk
 extern "C" {

@@ -1,4 +1,5 @@
-// Internal interfaces of the IVFADC index: stable bucketing, k-means, product quantizer.
+// Internal interfaces of the inverted-file indexes: stable bucketing, k-means, row gathers,
+// the flat list scan.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -6,6 +7,48 @@
 #include "common.cuh"
 
 namespace gbk {
+
+// Persistent device allocation owned by an index (freed when the index is destroyed).
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  gbk_status alloc(size_t b) {
+    release();
+    if (b == 0) return GBK_OK;
+    if (cudaMalloc(&p, b) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return set_error(GBK_ENOMEM, "cudaMalloc(%zu) failed for index storage", b);
+    }
+    bytes = b;
+    return GBK_OK;
+  }
+  // grow to at least b bytes, keeping the first `keep` bytes (stream-ordered copy)
+  gbk_status grow(size_t b, size_t keep, cudaStream_t st) {
+    if (b <= bytes) return GBK_OK;
+    void* q = nullptr;
+    if (cudaMalloc(&q, b) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(GBK_ENOMEM, "cudaMalloc(%zu) failed for index storage", b);
+    }
+    if (keep) GBK_CUDA_CHECK(cudaMemcpyAsync(q, p, keep, cudaMemcpyDeviceToDevice, st));
+    GBK_CUDA_CHECK(cudaStreamSynchronize(st));
+    release();
+    p = q;
+    bytes = b;
+    return GBK_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
 
 // Launch shape of the IVFADC list scan, chosen by gbk_ivfpq_autotune or set by the caller:
 // codes each thread loads per step (2, 4 or 8) and, in the persistent mixed-batch mode,
@@ -34,5 +77,25 @@ gbk_status kmeans_run(const float* x, int64_t n, int d, int ldx, int nc, int nit
 // nc <= 256: a[n] (int32), optional dist[n].
 gbk_status assign_direct_run(const float* x, int64_t n, int ldx, int d, const float* cent, int nc,
                              int32_t* a, float* dist, cudaStream_t st);
+
+// out[j] = in[order[j]] for rows of d floats, j < n (list-order copy of staged vectors).
+gbk_status gather_rows_run(const float* in, const int64_t* order, int64_t n, int d, float* out,
+                           cudaStream_t st);
+
+// Exact list scan (IVF-Flat): for query q and its probed lists cl_I[q][0..nprobe), the
+// squared L2 distance sum_t (x_t - y_t)^2 of every stored vector (vecs, list order) and the
+// k best per query by (distance, list position); ids[position] out, or the position itself
+// when ids is null.  Padding (+inf, -1).
+gbk_status ivf_flat_scan_run(const float* xq, int64_t nq, int d, int nprobe, int k,
+                             const int64_t* cl_I, const int64_t* list_off, const float* vecs,
+                             const int64_t* ids, float* D, int64_t* I, cudaStream_t st);
+
+// Exact float32 re-rank of k' candidates given as row numbers of xb (negative = none): the
+// k best by (distance, row) of sum_t (x_t - y_t)^2; rows out (or -1 with +inf).
+gbk_status rerank_rows_run(const float* xq, const float* xb, int64_t nq, int d, int kprime,
+                           int k, const int64_t* rows, float* D, int64_t* I, cudaStream_t st);
+
+// I[j] = ids[I[j]] for I[j] >= 0 (row numbers to stored ids), j < n.
+gbk_status rows_to_ids_run(int64_t* I, int64_t n, const int64_t* ids, cudaStream_t st);
 
 }  // namespace gbk

@@ -221,7 +221,7 @@ struct ScanArgs {
   int direct;            // 1: LUT[m][c] = ||(x - c_L)^m - C_m[c]||^2 computed in place
   const int64_t* list_off;
   const uint8_t* codes;
-  const int64_t* ids;
+  const int64_t* ids;    // null: list positions out instead of ids
   float* D;
   int64_t* I;
   // mixed batches (all optional): per-query k and nprobe (<= k, nprobe above), output
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(256)
         a.I[ob + j] = -1;
       } else {
         a.D[ob + j] = key_value((uint32_t)(e >> 32), false);
-        a.I[ob + j] = a.ids[(uint32_t)e];
+        a.I[ob + j] = a.ids ? a.ids[(uint32_t)e] : (int64_t)(uint32_t)e;
       }
     }
   }

@@ -11,8 +11,10 @@
 // |<x~,y~> - <x,y>| <= |e_x| |y~| + |x| |e_y| (Cauchy-Schwarz) plus float32 accumulation,
 // using the largest database norm and quantisation error.  (Inner product: mirror image.)
 #include <cmath>
+#include <cstdint>
 
 #include "common.cuh"
+#include "ivf.cuh"
 #include "knn.cuh"
 #include "select_core.cuh"
 
@@ -20,39 +22,87 @@ namespace gbk {
 
 namespace {
 
-// Block per query: warps take candidates round-robin, lanes stride over dimensions;
-// composites are then sorted in shared memory (bitonic, KP >= k').
+// Block per query: groups of 8 lanes take candidates (4 per warp, 2 such sets in flight),
+// each lane summing every 8th float4 (or float) of the row; the group then butterfly-sums
+// its partials.  Composites are then sorted in shared memory (bitonic, KP >= k').  v4:
+// rows are 16-byte aligned float4 rows (d % 4 == 0, aligned base), checked by the host.
 template <int KP>
 __global__ void __launch_bounds__(256)
     rerank_kernel(const float* __restrict__ xq, const float* __restrict__ xb, int d, int kprime,
                   int k, int largest, const int64_t* __restrict__ Ic,
                   const float* __restrict__ Dc, const float* __restrict__ eps,
                   float* __restrict__ D, int64_t* __restrict__ I,
-                  int32_t* __restrict__ certified, int all_candidates) {
+                  int32_t* __restrict__ certified, int all_candidates, int v4) {
+  constexpr int U = 2;
   __shared__ uint64_t keys[KP];
-  __shared__ float xs[1024];
+  __shared__ __align__(16) float xs[1024];
   const int64_t q = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int grp = lane >> 3, sub = lane & 7;
   for (int t = threadIdx.x; t < d; t += blockDim.x) xs[t] = xq[q * d + t];
   for (int j = threadIdx.x; j < KP; j += blockDim.x) keys[j] = ~0ull;
   __syncthreads();
-  for (int c = warp; c < kprime; c += nw) {
-    const int64_t id = Ic[q * kprime + c];
-    if (id < 0) continue;
-    const float* y = xb + id * d;
-    float s = 0.f;
-    for (int t = lane; t < d; t += 32) {
-      const float yv = y[t];
-      if (largest) {
-        s = fmaf(xs[t], yv, s);
-      } else {
-        const float e = xs[t] - yv;
-        s = fmaf(e, e, s);
+  for (int c0 = warp * 4 * U; c0 < kprime; c0 += nw * 4 * U) {
+    int64_t id[U];
+    float s[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int c = c0 + u * 4 + grp;
+      id[u] = c < kprime ? Ic[q * kprime + c] : -1;
+      s[u] = 0.f;
+    }
+    if (v4) {
+      const int nf = d >> 2;
+      const float4* y4 = reinterpret_cast<const float4*>(xb);
+      for (int f = sub; f < nf; f += 8) {
+        const float4 xv = reinterpret_cast<const float4*>(xs)[f];
+        float4 yv[U];
+#pragma unroll
+        for (int u = 0; u < U; u++)
+          yv[u] = id[u] >= 0 ? __ldg(y4 + id[u] * nf + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          if (largest) {
+            s[u] = fmaf(xv.x, yv[u].x, s[u]);
+            s[u] = fmaf(xv.y, yv[u].y, s[u]);
+            s[u] = fmaf(xv.z, yv[u].z, s[u]);
+            s[u] = fmaf(xv.w, yv[u].w, s[u]);
+          } else {
+            float e = xv.x - yv[u].x;
+            s[u] = fmaf(e, e, s[u]);
+            e = xv.y - yv[u].y;
+            s[u] = fmaf(e, e, s[u]);
+            e = xv.z - yv[u].z;
+            s[u] = fmaf(e, e, s[u]);
+            e = xv.w - yv[u].w;
+            s[u] = fmaf(e, e, s[u]);
+          }
+        }
+      }
+    } else {
+      for (int t = sub; t < d; t += 8) {
+        const float xv = xs[t];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const float yv = id[u] >= 0 ? __ldg(xb + id[u] * d + t) : 0.f;
+          if (largest) {
+            s[u] = fmaf(xv, yv, s[u]);
+          } else {
+            const float e = xv - yv;
+            s[u] = fmaf(e, e, s[u]);
+          }
+        }
       }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
-    if (lane == 0) keys[c] = composite(ordered_key(s, largest != 0), (uint32_t)id);
+    for (int u = 0; u < U; u++) {
+      s[u] += __shfl_xor_sync(FULL_MASK, s[u], 4);
+      s[u] += __shfl_xor_sync(FULL_MASK, s[u], 2);
+      s[u] += __shfl_xor_sync(FULL_MASK, s[u], 1);
+      const int c = c0 + u * 4 + grp;
+      if (sub == 0 && id[u] >= 0)
+        keys[c] = composite(ordered_key(s[u], largest != 0), (uint32_t)id[u]);
+    }
   }
   __syncthreads();
   for (int size = 2; size <= KP; size <<= 1) {
@@ -131,8 +181,9 @@ template <int KP>
 gbk_status launch_rerank(const float* xq, const float* xb, int64_t nq, int d, int kprime, int k,
                          int largest, const int64_t* Ic, const float* Dc, const float* eps,
                          float* D, int64_t* I, int32_t* cert, int all, cudaStream_t st) {
+  const int v4 = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(xb) & 15) == 0;
   rerank_kernel<KP><<<(unsigned)nq, 256, 0, st>>>(xq, xb, d, kprime, k, largest, Ic, Dc, eps, D,
-                                                  I, cert, all);
+                                                  I, cert, all, v4);
   GBK_LAUNCH_CHECK();
   return GBK_OK;
 }
@@ -172,6 +223,18 @@ gbk_status rerank_run(const float* xq, const float* xb, int64_t nq, int64_t nb, 
   if (kprime <= 256)
     return launch_rerank<256>(xq, xb, nq, d, kprime, k, lg, Ic, Dc, epsp, D, I, certified, all, st);
   return launch_rerank<1024>(xq, xb, nq, d, kprime, k, lg, Ic, Dc, epsp, D, I, certified, all, st);
+}
+
+gbk_status rerank_rows_run(const float* xq, const float* xb, int64_t nq, int d, int kprime,
+                           int k, const int64_t* rows, float* D, int64_t* I, cudaStream_t st) {
+  if (nq == 0) return GBK_OK;
+  if (d > 1024) return set_error(GBK_EUNSUPPORTED, "re-rank supports d <= 1024");
+  ProfScope prof("rerank", st);
+  if (kprime <= 64)
+    return launch_rerank<64>(xq, xb, nq, d, kprime, k, 0, rows, nullptr, nullptr, D, I, nullptr, 0, st);
+  if (kprime <= 256)
+    return launch_rerank<256>(xq, xb, nq, d, kprime, k, 0, rows, nullptr, nullptr, D, I, nullptr, 0, st);
+  return launch_rerank<1024>(xq, xb, nq, d, kprime, k, 0, rows, nullptr, nullptr, D, I, nullptr, 0, st);
 }
 
 }  // namespace gbk

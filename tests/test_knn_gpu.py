@@ -238,3 +238,22 @@ def test_small_exact_configuration(gbk):
     xq = datagen.gaussian_matrix(102, 1024, 128)
     D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), 10)
     _check_knn(xq, xb, D, I, 10)
+
+
+@pytest.mark.parametrize("d,offset", [(32, 1), (30, 0)])
+def test_low_precision_rerank_unaligned_rows(gbk, d, offset):
+    # database rows that are not 16-byte aligned (a view one float into its storage) or of a
+    # length that is not a multiple of 4: the re-rank reads them with scalar loads
+    xq = datagen.gaussian_matrix(81, 150, d)
+    xb = datagen.gaussian_matrix(82, 8000, d)
+    store = torch.zeros(xb.size + 4, device="cuda")
+    store[offset:offset + xb.size] = torch.from_numpy(xb.ravel()).cuda()
+    xbt = store[offset:offset + xb.size].view(8000, d)
+    assert (xbt.data_ptr() % 16 == 0) == (offset == 0)
+    D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), xbt, 10, precision="bf16", kprime=40)
+    D, I = D.cpu().numpy().astype(np.float64), I.cpu().numpy()
+    qi = np.repeat(np.arange(I.shape[0]), 10)
+    ex = oracle.pair_dist(xq, xb, qi, I.ravel()).reshape(I.shape)
+    np.testing.assert_allclose(D, ex, rtol=1e-5, atol=1e-4)
+    Do, Io = oracle.knn(xq, xb, 10)
+    assert (I == Io).mean() > 0.99

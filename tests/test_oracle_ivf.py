@@ -146,3 +146,71 @@ def test_ivfadc_pads_when_fewer_than_k():
         got = int((I[q] >= 0).sum())
         assert np.all(I[q, got:] == -1) and np.all(np.isinf(D[q, got:]))
         assert np.all(np.diff(D[q, :got]) >= 0)
+
+
+# ------------------------------------------------------------------ IVF-Flat and re-ranking
+
+def _flat_lists(x, coarse):
+    lists, _ = oracle.assign(x, coarse)
+    off, order = oracle.ivf_bucket(lists, coarse.shape[0])
+    return off, x[order], order.astype(np.int64)
+
+
+def test_ivfflat_full_probe_equals_exact_search():
+    # every list probed: the inverted file changes only the visiting order, so the result is
+    # exact search (Eq. 1), ties included (duplicated rows land in the same list)
+    x, coarse, _, _, _, _ = _tiny_index(140, n=2000)
+    x[1500:1600] = x[100:200]
+    off, vecs, ids = _flat_lists(x, coarse)
+    xq = datagen.gaussian_matrix(141, 25, 16) * 3
+    D, I = oracle.ivfflat_search(xq, coarse, off, vecs, ids, 40, coarse.shape[0])
+    De, Ie = oracle.knn(xq, x, 40)
+    np.testing.assert_array_equal(I, Ie)
+    np.testing.assert_array_equal(D, De)
+
+
+def test_ivfflat_partial_probe_is_brute_force_over_probed_lists():
+    x, coarse, _, _, _, _ = _tiny_index(150, n=1500)
+    off, vecs, ids = _flat_lists(x, coarse)
+    xq = datagen.mixture_points(datagen.mixture_centres(150, 12, 16), 151, 12)
+    lists = np.repeat(np.arange(coarse.shape[0]), np.diff(off))
+    for nprobe in (1, 3):
+        D, I = oracle.ivfflat_search(xq, coarse, off, vecs, ids, 15, nprobe)
+        for q in range(xq.shape[0]):
+            cd = ((coarse.astype(np.float64) - xq[q].astype(np.float64)) ** 2).sum(1)
+            probed = np.lexsort((np.arange(coarse.shape[0]), cd))[:nprobe]
+            sel = np.isin(lists, probed)
+            dist = ((vecs[sel].astype(np.float64) - xq[q].astype(np.float64)) ** 2).sum(1)
+            o = np.lexsort((ids[sel], dist))[:15]
+            got = min(15, int(sel.sum()))
+            np.testing.assert_array_equal(I[q, :got], ids[sel][o])
+            np.testing.assert_allclose(D[q, :got], dist[o], rtol=1e-12)
+            assert np.all(I[q, got:] == -1) and np.all(np.isinf(D[q, got:]))
+
+
+def test_refine_with_every_candidate_is_exact_search():
+    # k' >= the database and every list probed: the re-rank sees every vector
+    x, coarse, books, off, codes, ids = _tiny_index(160, n=700)
+    xq = datagen.gaussian_matrix(161, 10, 16) * 2
+    D, I, _, _ = oracle.ivfadc_refine(xq, x, coarse, books, off, codes, ids, 20, coarse.shape[0],
+                                      700)
+    De, Ie = oracle.knn(xq, x, 20)
+    np.testing.assert_array_equal(I, Ie)
+    np.testing.assert_allclose(D, De, rtol=1e-12)
+
+
+def test_refine_is_exact_top_k_of_the_adc_candidates():
+    x, coarse, books, off, codes, ids = _tiny_index(170)
+    xq = datagen.mixture_points(datagen.mixture_centres(170, 12, 16), 171, 15)
+    D, I, Dc, Ic = oracle.ivfadc_refine(xq, x, coarse, books, off, codes, ids, 10, 2, 40)
+    Da, Ia = oracle.ivfadc_search(xq, coarse, books, off, codes, ids, 40, 2)
+    np.testing.assert_array_equal(Ic, Ia)
+    for q in range(xq.shape[0]):
+        cand = Ia[q][Ia[q] >= 0]
+        ex = ((x[cand].astype(np.float64) - xq[q].astype(np.float64)) ** 2).sum(1)
+        o = np.lexsort((cand, ex))[:10]
+        np.testing.assert_array_equal(I[q], cand[o])
+        np.testing.assert_allclose(D[q], ex[o], rtol=1e-12)
+        # re-ranking never loses ground: the k-th exact distance is at most ADC's choice's
+        ex_adc = ((x[Ia[q, :10]].astype(np.float64) - xq[q].astype(np.float64)) ** 2).sum(1)
+        assert D[q, -1] <= np.sort(ex_adc)[-1] + 1e-12
