@@ -317,6 +317,51 @@ def run_ivfadc(args):
                       **t, "results": rows, "refine": refine, "ivfflat": flat}), flush=True)
 
 
+def run_kmeans(args):
+    """k-means with the exact k = 1 search as the assignment (section 6.2): the MNIST8m-shaped
+    clustering of the paper's k-means table (8.1M x 784, 20 iterations, 256 and 4,096
+    centroids; a seeded Gaussian mixture stands in for the images) and the large-scale case
+    of the same section (1e8 x 128 to 85,000 centroids), of which a few iterations are
+    timed.  The points are i.i.d. draws, so the large case's initial centroids are its first
+    85,000 rows (a uniform sample)."""
+    import numpy as np
+    import torch
+
+    import paper_1702_08734_gb300 as g
+    from paper_1702_08734_gb300 import datagen
+    g.load()
+
+    def run(x, init, niter):
+        torch.cuda.synchronize()
+        g.profile_enable(True)
+        t0 = time.perf_counter()
+        _, obj, ns = g.kmeans(x, init, niter)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        g.profile_enable(False)
+        by = {}
+        for nm, tt in g.profile_read():
+            by[nm] = by.get(nm, 0.0) + tt
+        return {"iterations": niter, "s": dt, "ms_per_iteration": dt * 1e3 / niter,
+                "objective_first": float(obj[0]), "objective_last": float(obj[-1]),
+                "empty_cluster_splits": ns,
+                "kernel_ms_per_iteration": {k: v / niter for k, v in by.items()}}
+
+    out = {}
+    n, d = args.km_n, 784
+    x = datagen.mixture_points_cuda(datagen.mixture_centres(601, 1024, d), 602, n)
+    for nc in (256, 4096):
+        out["mnist8m_shape_nc%d" % nc] = run(x, datagen.permutation_prefix(603, n, nc), 20)
+    del x
+    torch.cuda.empty_cache()
+    n2, nc2 = args.km_large_n, 85000
+    x = datagen.mixture_points_cuda(datagen.mixture_centres(611, 4096, 128), 612, n2)
+    out["large_1e8x128_nc85000"] = run(x, np.arange(nc2), args.km_large_iters)
+    print(json.dumps({"workload": "kmeans %d x 784 (nc 256, 4096; 20 iterations) and %d x 128 "
+                      "(nc 85000; %d iterations)" % (n, n2, args.km_large_iters), **out}),
+          flush=True)
+
+
 def run_learned(args):
     """Learned nprobe: labels = smallest nprobe in {1,..,256} whose 10-R@10 reaches
     min(10/10, the query's 10-R@10 at 256), for 200K training queries; the network (query +
@@ -516,7 +561,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="exact", choices=["exact", "ivfadc", "learned", "batched"])
+    ap.add_argument("--workload", default="exact",
+                    choices=["exact", "ivfadc", "learned", "batched", "kmeans"])
+    ap.add_argument("--km-n", type=int, default=8100000)
+    ap.add_argument("--km-large-n", type=int, default=100000000)
+    ap.add_argument("--km-large-iters", type=int, default=2)
     ap.add_argument("--batched-n", type=int, default=200000000)
     ap.add_argument("--batched-nlist", type=int, default=262144)
     ap.add_argument("--batched-iters", type=int, default=10)
@@ -538,6 +587,9 @@ def main():
         return
     if args.workload == "batched" and args.impl == "ours":
         run_batched(args)
+        return
+    if args.workload == "kmeans" and args.impl == "ours":
+        run_kmeans(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -158,9 +158,11 @@ typedef struct gbk_knn_opts {
  * keep the best k.  A query is certified when the k'-th low-precision distance minus
  * the error bound exceeds the k-th re-ranked distance (plus, for inner product), which
  * proves no other database row belongs to the top k.
- * Limits: nb, nq < 2^31; d <= 128 for k <= 512 (larger k tiles the distance matrix over
- * queries and allows d <= 160).  Errors: GBK_EINVAL, GBK_EUNSUPPORTED (d too large),
- * GBK_ENOMEM, GBK_ECUDA.  Inputs must be finite.
+ * Limits: nb, nq < 2^31; BF16/FP8 d <= 8192 (the float32 re-rank).  A 128-query tile of
+ * the GEMM stays in shared memory while d <= 128 (FP32), 512 (BF16) or 1024 (FP8) with
+ * candidate lists (k > 1), 128 / 704 / 1408 without; longer rows stream the query
+ * k-blocks through the shared-memory ring beside the database's (same results).  Errors:
+ * GBK_EINVAL, GBK_EUNSUPPORTED, GBK_ENOMEM, GBK_ECUDA.  Inputs must be finite.
  */
 gbk_status gbk_knn_brute(const float* xq, int64_t nq, const float* xb, int64_t nb, int32_t d,
                          int32_t k, int32_t metric, float* D, int64_t* I,
@@ -261,7 +263,7 @@ gbk_status gbk_ivfpq_keep_vectors(gbk_index* index, int32_t keep);
  * as gbk_ivfpq_search), then their exact squared distances sum_t (x_t - y_t)^2 (Eq. 1)
  * computed in float32 from the kept vectors, and the k smallest of those.  D [nq][k]
  * ascending, I [nq][k] ids; equal distances by list position; (+inf, -1) padding when
- * fewer than k candidates exist.  1 <= k <= kprime <= GBK_MAX_K; d <= 1024; EINVAL when
+ * fewer than k candidates exist.  1 <= k <= kprime <= GBK_MAX_K; EINVAL when
  * the index keeps no vectors. */
 gbk_status gbk_ivfpq_search_refine(gbk_index* index, const float* xq, int64_t nq, int32_t k,
                                    int32_t nprobe, int32_t kprime, float* D, int64_t* I,

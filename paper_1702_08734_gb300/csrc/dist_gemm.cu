@@ -435,13 +435,22 @@ gbk_status gemm_launch(int mode, int kpr, bool largest, const PreparedOperand& Q
   const int64_t avail = (int64_t)di.smem_optin - 1024 - l0.total;
   const int64_t stage_bytes = (int64_t)pieces * GEMM_TILE_BYTES + 16;
   int stages = (int)std::min<int64_t>(8, avail / stage_bytes);
-  if (stages < 2)
-    return set_error(GBK_EUNSUPPORTED, "d=%d too large for the fused tensor-core kernel", Q.d);
+  a.stream_a = 0;
+  if (stages < 2) {
+    // the query tile does not fit beside a 2-stage ring: stream its k-blocks with B's
+    const GemmSmemLayout l1 = gemm_smem_layout(2 * pieces, 0, 0, queues, epi);
+    const int64_t avail1 = (int64_t)di.smem_optin - 1024 - l1.total;
+    stages = (int)std::min<int64_t>(8, avail1 / (2 * stage_bytes));
+    if (stages < 2)
+      return set_error(GBK_EUNSUPPORTED, "d=%d too large for the fused tensor-core kernel", Q.d);
+    a.stream_a = 1;
+  }
   a.stages = stages;
   a.nkb = Q.nkb;
   // at least half the SM's shared memory, so one CTA per SM owns the TMEM it allocates
-  const size_t smem = std::max<size_t>(gemm_smem_layout(pieces, Q.nkb, stages, queues, epi).total + 1024,
-                                       di.smem_optin / 2 + 1024);
+  const GemmSmemLayout lf = a.stream_a ? gemm_smem_layout(2 * pieces, 0, stages, queues, epi)
+                                       : gemm_smem_layout(pieces, Q.nkb, stages, queues, epi);
+  const size_t smem = std::max<size_t>(lf.total + 1024, di.smem_optin / 2 + 1024);
   const int nitems = a.nqt * a.chunks;
   const int grid = std::min(nitems, di.sm_count);
   a.status = device_status();

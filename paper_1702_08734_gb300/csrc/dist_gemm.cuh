@@ -75,7 +75,9 @@ __host__ __device__ constexpr int gemm_epi(int prec) { return prec == 0 ? 1 : 2;
 struct GemmArgs {
   int nq, nb;            // queries, database rows
   int nkb;               // 128-byte k-blocks per row (padded d)
-  int stages;            // B ring depth
+  int stages;            // ring depth
+  int stream_a;          // 1: the query tile's k-blocks travel with B's through the ring
+                         // (rows too long to keep the query tile resident)
   int nqt, ntiles;       // query tiles, database tiles
   int chunks, tpc;       // database chunks, tiles per chunk
   int k, kp;             // k and the padded list length (power of two >= 32)

@@ -135,7 +135,11 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-  const GemmSmemLayout lay = gemm_smem_layout(PIECES, args.nkb, args.stages, QUEUES, EPI);
+  // stage = B's pieces, or A's and B's pieces of one k-block when A is streamed
+  const int SP = args.stream_a ? 2 * PIECES : PIECES;
+  const GemmSmemLayout lay = args.stream_a
+                                 ? gemm_smem_layout(2 * PIECES, 0, args.stages, QUEUES, EPI)
+                                 : gemm_smem_layout(PIECES, args.nkb, args.stages, QUEUES, EPI);
   unsigned char* sA = smem + lay.a_off;
   unsigned char* sB = smem + lay.b_off;
   uint64_t* sQ = reinterpret_cast<uint64_t*>(smem + lay.q_off);
@@ -190,16 +194,18 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, local++) {
         const int qt = item % args.nqt, ch = item / args.nqt;
         const int t0 = ch * args.tpc, t1 = min(args.ntiles, t0 + args.tpc);
-        ok = sm100::mbar_wait(a_empty, (uint32_t)((local & 1) ^ 1), args.status, abort_flag);
-        if (!ok) break;
-        sm100::mbar_arrive_expect_tx(a_full, (uint32_t)(PIECES * args.nkb) * GEMM_TILE_BYTES);
-        for (int kb = 0; kb < args.nkb; kb++) {
-          const int x = kb * (128 / T::ELEM);
-          sm100::tma_load_2d(sA + (0 * args.nkb + kb) * GEMM_TILE_BYTES, &tmA0, a_full, x,
-                             qt * GEMM_BM);
-          if (PIECES > 1)
-            sm100::tma_load_2d(sA + (1 * args.nkb + kb) * GEMM_TILE_BYTES, &tmA1, a_full, x,
+        if (!args.stream_a) {
+          ok = sm100::mbar_wait(a_empty, (uint32_t)((local & 1) ^ 1), args.status, abort_flag);
+          if (!ok) break;
+          sm100::mbar_arrive_expect_tx(a_full, (uint32_t)(PIECES * args.nkb) * GEMM_TILE_BYTES);
+          for (int kb = 0; kb < args.nkb; kb++) {
+            const int x = kb * (128 / T::ELEM);
+            sm100::tma_load_2d(sA + (0 * args.nkb + kb) * GEMM_TILE_BYTES, &tmA0, a_full, x,
                                qt * GEMM_BM);
+            if (PIECES > 1)
+              sm100::tma_load_2d(sA + (1 * args.nkb + kb) * GEMM_TILE_BYTES, &tmA1, a_full, x,
+                                 qt * GEMM_BM);
+          }
         }
         for (int t = t0; t < t1 && ok; t++) {
           for (int kb = 0; kb < args.nkb; kb++, gstage++) {
@@ -207,9 +213,15 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
             const uint32_t ph = (gstage / args.stages) & 1u;
             ok = sm100::mbar_wait(&b_empty[st], ph ^ 1u, args.status, abort_flag);
             if (!ok) break;
-            sm100::mbar_arrive_expect_tx(&b_full[st], (uint32_t)PIECES * GEMM_TILE_BYTES);
+            sm100::mbar_arrive_expect_tx(&b_full[st], (uint32_t)SP * GEMM_TILE_BYTES);
             const int x = kb * (128 / T::ELEM);
-            unsigned char* dst = sB + (uint32_t)st * PIECES * GEMM_TILE_BYTES;
+            unsigned char* dst = sB + (uint32_t)st * SP * GEMM_TILE_BYTES;
+            if (args.stream_a) {
+              sm100::tma_load_2d(dst, &tmA0, &b_full[st], x, qt * GEMM_BM);
+              if (PIECES > 1)
+                sm100::tma_load_2d(dst + GEMM_TILE_BYTES, &tmA1, &b_full[st], x, qt * GEMM_BM);
+              dst += PIECES * GEMM_TILE_BYTES;
+            }
             sm100::tma_load_2d(dst, &tmB0, &b_full[st], x, t * GEMM_BN);
             if (PIECES > 1)
               sm100::tma_load_2d(dst + GEMM_TILE_BYTES, &tmB1, &b_full[st], x, t * GEMM_BN);
@@ -226,9 +238,11 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, local++) {
         const int ch = item / args.nqt;
         const int t0 = ch * args.tpc, t1 = min(args.ntiles, t0 + args.tpc);
-        ok = sm100::mbar_wait(a_full, (uint32_t)(local & 1), args.status, abort_flag);
-        if (!ok) break;
-        sm100::tc_fence_after();
+        if (!args.stream_a) {
+          ok = sm100::mbar_wait(a_full, (uint32_t)(local & 1), args.status, abort_flag);
+          if (!ok) break;
+          sm100::tc_fence_after();
+        }
         const uint32_t a_base = sm100::smem_u32(sA);
         for (int t = t0; t < t1 && ok; t++, gtile++) {
           const int acc = (int)(gtile % GEMM_NACC);
@@ -243,16 +257,20 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
                                   abort_flag);
             if (!ok) break;
             sm100::tc_fence_after();
-            const uint32_t b_base = sm100::smem_u32(sB) + (uint32_t)st * PIECES * GEMM_TILE_BYTES;
+            const uint32_t s_base = sm100::smem_u32(sB) + (uint32_t)st * SP * GEMM_TILE_BYTES;
+            // A piece 0 / piece 1 and B of this k-block
+            const uint32_t a_kb0 = args.stream_a ? s_base : a_base + kb * GEMM_TILE_BYTES;
+            const uint32_t a_kb1 = args.stream_a ? s_base + GEMM_TILE_BYTES
+                                                 : a_base + (args.nkb + kb) * GEMM_TILE_BYTES;
+            const uint32_t b_base = args.stream_a ? s_base + PIECES * GEMM_TILE_BYTES : s_base;
 #pragma unroll
             for (int ks = 0; ks < 4; ks++) {  // 32 bytes of K per MMA
               const uint32_t koff = (uint32_t)ks * 32u;
-              const uint64_t a0 = sm100::sdesc_k_sw128(a_base + kb * GEMM_TILE_BYTES + koff);
+              const uint64_t a0 = sm100::sdesc_k_sw128(a_kb0 + koff);
               const uint64_t b0 = sm100::sdesc_k_sw128(b_base + koff);
               const uint32_t accum = (kb | ks) != 0 ? 1u : 0u;
               if (KIND == KIND_TF32X3) {
-                const uint64_t a1 = sm100::sdesc_k_sw128(a_base +
-                                                         (args.nkb + kb) * GEMM_TILE_BYTES + koff);
+                const uint64_t a1 = sm100::sdesc_k_sw128(a_kb1 + koff);
                 const uint64_t b1 = sm100::sdesc_k_sw128(b_base + GEMM_TILE_BYTES + koff);
                 sm100::mma_tf32(d_tmem, a0, b0, IDESC, accum);
                 sm100::mma_tf32(d_tmem, a0, b1, IDESC, 1u);
@@ -267,7 +285,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           }
           if (ok) sm100::mma_commit(&acc_full[acc]);
         }
-        if (ok) sm100::mma_commit(a_empty);
+        if (ok && !args.stream_a) sm100::mma_commit(a_empty);
       }
     }
   } else {

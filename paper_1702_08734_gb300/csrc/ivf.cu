@@ -352,7 +352,6 @@ gbk_status gbk_ivfpq_search_refine(gbk_index* ix, const float* xq, int64_t nq, i
   GBK_REQUIRE(nq >= 0 && nq < (int64_t(1) << 31), "gbk_ivfpq_search_refine: nq out of range");
   if (nq == 0) return GBK_OK;
   GBK_REQUIRE(xq && D && I, "gbk_ivfpq_search_refine: NULL pointer");
-  GBK_REQUIRE(ix->d <= 1024, "gbk_ivfpq_search_refine: d <= 1024");
   cudaStream_t st = as_stream(stream);
   gbk_status r;
   if ((r = finalize(ix, st)) != GBK_OK) return r;

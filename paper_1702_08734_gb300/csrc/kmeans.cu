@@ -4,8 +4,10 @@
 // Each iteration: assignment (tensor-core k-NN with k = 1, or direct float32 distances for
 // the small sub-vectors of the product quantizer), then the update.  The update sums each
 // cluster's members in double precision in increasing member index (stable bucketing gives
-// that order), one thread per dimension, and rounds the mean to float32 once - the same
-// arithmetic, in the same order, as a sequential CPU loop.  Empty clusters are re-seeded,
+// that order), one thread per dimension, and rounds the mean to float32 once.  When there
+// are few clusters for the GPU's size, each cluster's members are cut into S equal
+// segments summed in parallel and the S partial sums are added in segment order: the
+// double sum then differs from a sequential loop's by rounding far below float32's.  Empty clusters are re-seeded,
 // in increasing index, by splitting the currently most populated cluster (lowest index on
 // ties): c_e = c_s (1 + g/1024), c_s = c_s (1 - g/1024) with g = +1 on even and -1 on odd
 // dimensions; its count is halved between the two.
@@ -32,17 +34,50 @@ __global__ void to_i32_kernel(const int64_t* __restrict__ a, int64_t n, int32_t*
     b[i] = (int32_t)a[i];
 }
 
-__global__ void update_kernel(const float* __restrict__ x, int ldx, int d,
-                              const int64_t* __restrict__ offsets, const int64_t* __restrict__ order,
-                              float* __restrict__ cent, long long* __restrict__ counts) {
-  const int c = blockIdx.x;
+// Member sums of cluster c = blockIdx.x over segment blockIdx.y of S equal parts of its
+// members (in increasing member order, double precision, one thread per dimension, 8 rows
+// in flight).  S == 1 writes the mean directly; otherwise the partial sums go to
+// part[c][s][d] and update_combine_kernel adds them in segment order.
+__global__ void update_partial_kernel(const float* __restrict__ x, int ldx, int d,
+                                      const int64_t* __restrict__ offsets,
+                                      const int64_t* __restrict__ order, int S,
+                                      double* __restrict__ part, float* __restrict__ cent,
+                                      long long* __restrict__ counts) {
+  const int c = blockIdx.x, sg = blockIdx.y;
   const int64_t o0 = offsets[c], cnt = offsets[c + 1] - o0;
-  if (threadIdx.x == 0) counts[c] = cnt;
+  if (sg == 0 && threadIdx.x == 0) counts[c] = cnt;
+  const int64_t len = (cnt + S - 1) / S;
+  const int64_t j0 = min(cnt, (int64_t)sg * len), j1 = min(cnt, j0 + len);
+  const int64_t* ord = order + o0;
+  for (int t = threadIdx.x; t < d; t += blockDim.x) {
+    double acc = 0.0;
+    int64_t j = j0;
+    for (; j + 8 <= j1; j += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; u++) v[u] = __ldg(x + ord[j + u] * ldx + t);
+#pragma unroll
+      for (int u = 0; u < 8; u++) acc += (double)v[u];
+    }
+    for (; j < j1; j++) acc += (double)__ldg(x + ord[j] * ldx + t);
+    if (S == 1) {
+      if (cnt > 0) cent[(int64_t)c * d + t] = (float)(acc / (double)cnt);
+    } else {
+      part[((int64_t)c * S + sg) * d + t] = acc;
+    }
+  }
+}
+
+__global__ void update_combine_kernel(const double* __restrict__ part, int S, int d,
+                                      const int64_t* __restrict__ offsets,
+                                      float* __restrict__ cent) {
+  const int c = blockIdx.x;
+  const int64_t cnt = offsets[c + 1] - offsets[c];
   if (cnt == 0) return;
   for (int t = threadIdx.x; t < d; t += blockDim.x) {
-    double s = 0.0;
-    for (int64_t j = 0; j < cnt; j++) s += (double)x[order[o0 + j] * ldx + t];
-    cent[(int64_t)c * d + t] = (float)(s / (double)cnt);
+    double acc = 0.0;
+    for (int sg = 0; sg < S; sg++) acc += part[((int64_t)c * S + sg) * d + t];
+    cent[(int64_t)c * d + t] = (float)(acc / (double)cnt);
   }
 }
 
@@ -197,6 +232,12 @@ gbk_status kmeans_run(const float* x, int64_t n, int d, int ldx, int nc, int nit
   if (objective) GBK_CUDA_CHECK(cudaMemsetAsync(objective, 0, sizeof(double) * (size_t)niter, st));
   if (n_split) GBK_CUDA_CHECK(cudaMemsetAsync(n_split, 0, sizeof(long long), st));
   const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)device_info().sm_count * 8);
+  // update split: S segments per cluster when clusters are few and large (enough blocks to
+  // fill the GPU), each segment at least 256 members
+  const int64_t want = ((int64_t)device_info().sm_count * 16 + nc - 1) / nc;
+  const int S = (int)std::max<int64_t>(1, std::min<int64_t>({want, 64, n / ((int64_t)nc * 256)}));
+  Scratch part;
+  if (S > 1 && (r = part.alloc(sizeof(double) * (size_t)nc * S * d, st)) != GBK_OK) return r;
   for (int it = 0; it < niter; it++) {
     if (assign_direct) {
       if ((r = assign_direct_run(x, n, ldx, d, cent, nc, a32.as<int32_t>(), dist.as<float>(), st)) !=
@@ -219,8 +260,13 @@ gbk_status kmeans_run(const float* x, int64_t n, int d, int ldx, int nc, int nit
       return r;
     {
       ProfScope prof("kmeans_update", st);
-      update_kernel<<<nc, 128, 0, st>>>(x, ldx, d, offs.as<int64_t>(), order.as<int64_t>(), cent,
-                                        counts.as<long long>());
+      const int threads = std::min(1024, (d + 31) / 32 * 32);
+      update_partial_kernel<<<dim3((unsigned)nc, (unsigned)S), threads, 0, st>>>(
+          x, ldx, d, offs.as<int64_t>(), order.as<int64_t>(), S, part.as<double>(), cent,
+          counts.as<long long>());
+      if (S > 1)
+        update_combine_kernel<<<nc, threads, 0, st>>>(part.as<double>(), S, d, offs.as<int64_t>(),
+                                                      cent);
       empty_split_kernel<<<1, 1024, 0, st>>>(cent, d, counts.as<long long>(), nc, n_split);
       GBK_LAUNCH_CHECK();
     }

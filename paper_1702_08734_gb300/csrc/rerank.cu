@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256)
                   int32_t* __restrict__ certified, int all_candidates, int v4) {
   constexpr int U = 2;
   __shared__ uint64_t keys[KP];
-  __shared__ __align__(16) float xs[1024];
+  extern __shared__ __align__(16) float xs[];  // the query, d floats
   const int64_t q = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int grp = lane >> 3, sub = lane & 7;
@@ -182,8 +182,8 @@ gbk_status launch_rerank(const float* xq, const float* xb, int64_t nq, int d, in
                          int largest, const int64_t* Ic, const float* Dc, const float* eps,
                          float* D, int64_t* I, int32_t* cert, int all, cudaStream_t st) {
   const int v4 = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(xb) & 15) == 0;
-  rerank_kernel<KP><<<(unsigned)nq, 256, 0, st>>>(xq, xb, d, kprime, k, largest, Ic, Dc, eps, D,
-                                                  I, cert, all, v4);
+  rerank_kernel<KP><<<(unsigned)nq, 256, sizeof(float) * (size_t)d, st>>>(
+      xq, xb, d, kprime, k, largest, Ic, Dc, eps, D, I, cert, all, v4);
   GBK_LAUNCH_CHECK();
   return GBK_OK;
 }
@@ -195,7 +195,7 @@ gbk_status rerank_run(const float* xq, const float* xb, int64_t nq, int64_t nb, 
                       const float* qscale, const float* ynorm2, const float* bscale,
                       const int64_t* Ic, const float* Dc, float* D, int64_t* I,
                       int32_t* certified, float* eps_out, cudaStream_t st) {
-  if (d > 1024) return set_error(GBK_EUNSUPPORTED, "re-rank supports d <= 1024");
+  if (d > 8192) return set_error(GBK_EUNSUPPORTED, "re-rank supports d <= 8192");
   // unit roundoff of the format; `sub` = half the smallest subnormal step relative to scale
   const float u = prec == GBK_PREC_BF16 ? 0.00390625f /* 2^-8 */ : 0.0625f /* 2^-4 */;
   const float sub = prec == GBK_PREC_FP8 ? 0.0009765625f /* 2^-10 */ : 0.f;
@@ -228,7 +228,7 @@ gbk_status rerank_run(const float* xq, const float* xb, int64_t nq, int64_t nb, 
 gbk_status rerank_rows_run(const float* xq, const float* xb, int64_t nq, int d, int kprime,
                            int k, const int64_t* rows, float* D, int64_t* I, cudaStream_t st) {
   if (nq == 0) return GBK_OK;
-  if (d > 1024) return set_error(GBK_EUNSUPPORTED, "re-rank supports d <= 1024");
+  if (d > 8192) return set_error(GBK_EUNSUPPORTED, "re-rank supports d <= 8192");
   ProfScope prof("rerank", st);
   if (kprime <= 64)
     return launch_rerank<64>(xq, xb, nq, d, kprime, k, 0, rows, nullptr, nullptr, D, I, nullptr, 0, st);

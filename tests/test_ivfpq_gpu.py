@@ -33,6 +33,22 @@ def test_kmeans_matches_oracle(gbk, d, nc, direct):
     np.testing.assert_allclose(obj, objo, rtol=1e-4)
 
 
+@pytest.mark.parametrize("d,direct", [(32, False), (16, True)])
+def test_kmeans_segmented_update_matches_oracle(gbk, d, direct):
+    # few large clusters: each cluster's member sum is split into segments added in order;
+    # the double sums then differ from the oracle's sequential ones far below float32
+    # one initial row per mixture component: every assignment is far from a tie
+    x, _ = _mixture(30 + d, 200000, d, ncent=8, std=8.0)
+    u = datagen.randint(31 + d, 0, x.shape[0], 8, stream=0)
+    init = np.array([int(np.argmax(u == c)) for c in range(8)])
+    c, obj, _ = gbk.kmeans(torch.from_numpy(x).cuda(), init, 3, direct=direct)
+    co, objo, _ = oracle.kmeans(x, init, 3)
+    np.testing.assert_allclose(c.cpu().numpy(), co, rtol=1e-6, atol=1e-6)
+    # the objective sums the assignment's float32 distances, formed as ||x||^2 + ||c||^2 -
+    # 2<x,c> (Eq. 2): cancellation against norms ~60x the distances costs ~1e-5 relative
+    np.testing.assert_allclose(obj, objo, rtol=1e-4)
+
+
 @pytest.mark.parametrize("direct", [True, False])
 def test_kmeans_empty_cluster_rule_matches_oracle(gbk, direct):
     # Duplicate initial rows tie exactly, so the lowest centroid takes every point and the

@@ -257,3 +257,37 @@ def test_low_precision_rerank_unaligned_rows(gbk, d, offset):
     np.testing.assert_allclose(D, ex, rtol=1e-5, atol=1e-4)
     Do, Io = oracle.knn(xq, xb, 10)
     assert (I == Io).mean() > 0.99
+
+
+@pytest.mark.parametrize("d", [160, 784, 1000])
+@pytest.mark.parametrize("k", [1, 10, 100])
+def test_knn_long_rows_stream_query_tile(gbk, d, k):
+    # rows too long to keep a 128-query tile resident beside the ring (float32-accurate
+    # pieces beyond d = 128): the query k-blocks travel with the database's through the ring
+    xq = datagen.gaussian_matrix(91, 200, d)
+    xb = datagen.gaussian_matrix(92, 3000, d)
+    D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), k)
+    _check_knn(xq, xb, D, I, k)
+
+
+@pytest.mark.parametrize("prec,d", [("bf16", 784), ("fp8", 1200)])
+def test_low_precision_long_rows(gbk, prec, d):
+    xq = datagen.gaussian_matrix(93, 150, d)
+    xb = datagen.gaussian_matrix(94, 4000, d)
+    D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), 10,
+                         precision=prec, kprime=80)
+    D, I = D.cpu().numpy().astype(np.float64), I.cpu().numpy()
+    qi = np.repeat(np.arange(I.shape[0]), 10)
+    ex = oracle.pair_dist(xq, xb, qi, I.ravel()).reshape(I.shape)
+    np.testing.assert_allclose(D, ex, rtol=1e-5, atol=1e-3)
+    Do, Io = oracle.knn(xq, xb, 10)
+    assert (I == Io).mean() > 0.99
+
+
+def test_pairwise_long_rows(gbk):
+    d = 784
+    xq = datagen.gaussian_matrix(95, 130, d)
+    xb = datagen.gaussian_matrix(96, 700, d)
+    P = gbk.pairwise_distances(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda())
+    ex = ((xq.astype(np.float64)[:, None, :] - xb.astype(np.float64)[None]) ** 2).sum(-1)
+    np.testing.assert_allclose(P.cpu().numpy(), ex, rtol=2e-5, atol=1e-3)
