@@ -255,6 +255,20 @@ gbk_status gbk_ivfpq_info(gbk_index* index, int64_t* ntotal, int32_t* nlist, int
 gbk_status gbk_ivfpq_export(gbk_index* index, float* coarse, float* pq, int64_t* list_off,
                             uint8_t* codes, int64_t* ids, void* stream);
 
+/* OPQ pre-rotation (the optimized product quantization used by the paper's DEEP1B and
+ * YFCC100M experiments, sections 1 and 6.4): with R [d][d] row-major (device or host
+ * float32, typically orthogonal) every vector given to train, add, the searches and the
+ * k-NN graph is replaced by R y before anything else, computed as the inner-product GEMM
+ * y R^T on the tensor cores (float32-accurate).  The quantizers (set_quantizers, export),
+ * the kept vectors and the learned-nprobe features then live in the rotated space; use
+ * gbk_ivfpq_rotate to map vectors there.  Must be set before training / set_quantizers
+ * and before the first add (EINVAL otherwise).  R = NULL removes it. */
+gbk_status gbk_ivfpq_set_rotation(gbk_index* index, const float* R, void* stream);
+
+/* out [n][d] = x [n][d] rotated by the index's R (a copy when it has none). */
+gbk_status gbk_ivfpq_rotate(gbk_index* index, const float* x, int64_t n, float* out,
+                            void* stream);
+
 /* Keep a float32 copy of every vector added from now on (n*d*4 bytes of device memory, in
  * list order), for gbk_ivfpq_search_refine.  Must be set before the first add. */
 gbk_status gbk_ivfpq_keep_vectors(gbk_index* index, int32_t keep);

@@ -19,6 +19,7 @@ marshals numpy arrays.  Functions and the passages they follow:
 * ``ivfflat_search``- the inverted file of section 2 with uncompressed lists: Eq. (5) for
   the probed lists, then Eq. (1) directly for their vectors
 * ``ivfadc_refine`` - Algorithm 4 for k' candidates, then Eq. (1) for those and the k best
+* ``rotate``        - the OPQ pre-rotation y -> R y (sections 1 and 6.4), in double
 """
 from __future__ import annotations
 
@@ -270,3 +271,10 @@ def ivfadc_refine(xq, xb, coarse, pq, offsets, codes, ids, k: int, nprobe: int, 
         D[q, :o.size] = ex[o]
         I[q, :o.size] = cand[o]
     return D, I, Dc, Ic
+
+
+def rotate(x, R):
+    """Rows y of x replaced by R y, computed in double and rounded to float32 once."""
+    x = np.asarray(x, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    return (x @ R.T).astype(np.float32)

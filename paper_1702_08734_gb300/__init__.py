@@ -226,6 +226,8 @@ _SIGNATURES.update({
     "gbk_ivfpq_info": [_vp, _vp, _vp, _vp, _vp, _vp],
     "gbk_ivfpq_export": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "gbk_ivfpq_keep_vectors": [_vp, _i32],
+    "gbk_ivfpq_set_rotation": [_vp, _vp, _vp],
+    "gbk_ivfpq_rotate": [_vp, _vp, _i64, _vp, _vp],
     "gbk_ivfpq_search_refine": [_vp, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp],
     "gbk_ivfflat_create": [_i32, _i32, _i32, _vp],
     "gbk_ivfflat_train": [_vp, _vp, _i64, _vp, _vp],
@@ -320,6 +322,20 @@ class IVFPQIndex:
         _call("gbk_ivfpq_search", self._h, _ptr(xq), nq, int(k), int(nprobe), _ptr(D), _ptr(I),
               _stream())
         return D, I
+
+    def set_rotation(self, R: torch.Tensor = None):
+        """OPQ pre-rotation R [d][d]: every input vector y becomes R y (before training)."""
+        if R is not None:
+            _dev(R, torch.float32, "R")
+        _call("gbk_ivfpq_set_rotation", self._h, _ptr(R), _stream())
+        return self
+
+    def rotate(self, x: torch.Tensor):
+        """x rotated by the index's R (the space of its quantizers)."""
+        _dev(x, torch.float32, "x")
+        out = torch.empty_like(x)
+        _call("gbk_ivfpq_rotate", self._h, _ptr(x), x.shape[0], _ptr(out), _stream())
+        return out
 
     def keep_vectors(self, keep: bool = True):
         """Keep float32 copies of the vectors added from now on (for search_refine)."""

@@ -43,6 +43,9 @@ struct gbk_index {
   // optional float32 copies of the added vectors (exact re-rank): staged, then list order
   bool keep_vectors = false;
   gbk::DevBuf st_vecs, vecs;
+  // optional OPQ pre-rotation R [d][d]: every input vector y is replaced by R y
+  gbk::DevBuf rot;
+  bool rotated = false;
   int64_t ntotal = 0;
   bool dirty = true;
   int64_t max_list = 0;
@@ -59,6 +62,7 @@ struct gbk_index {
     ids.release();
     st_vecs.release();
     vecs.release();
+    rot.release();
   }
 };
 
@@ -66,7 +70,13 @@ namespace gbk {
 
 // Algorithm 4 for a validated, finalized index (below).
 gbk_status search_run(gbk_index* ix, const float* xq, int64_t nq, int k, int nprobe, float* D,
-                      int64_t* I, cudaStream_t st, bool positions = false);
+                      int64_t* I, cudaStream_t st, bool positions = false,
+                      bool prerotated = false);
+
+// Rows of x replaced by R y (the OPQ pre-rotation) as the inner-product GEMM x R^T on the
+// tensor cores (float32-accurate), in chunks of 2^20 rows; without a rotation *out = x.
+gbk_status rotate_rows(const gbk_index* ix, const float* x, int64_t n, Scratch& buf,
+                       const float** out, cudaStream_t st);
 
 namespace {
 
@@ -181,10 +191,10 @@ gbk_status gbk_ivfpq_create(int32_t d, int32_t nlist, int32_t M, int32_t nbits, 
 
 void gbk_ivfpq_destroy(gbk_index* ix) { delete ix; }
 
-gbk_status gbk_ivfpq_train(gbk_index* ix, const float* x, int64_t n, const gbk_train_opts* opts,
-                           void* stream) {
+gbk_status gbk_ivfpq_train(gbk_index* ix, const float* x_in, int64_t n,
+                           const gbk_train_opts* opts, void* stream) {
   clear_error();
-  GBK_REQUIRE(ix && x, "gbk_ivfpq_train: NULL argument");
+  GBK_REQUIRE(ix && x_in, "gbk_ivfpq_train: NULL argument");
   GBK_REQUIRE(n >= ix->nlist && n >= 256 && n < (int64_t(1) << 31),
               "gbk_ivfpq_train: need max(nlist, 256) <= n < 2^31 training vectors");
   cudaStream_t st = as_stream(stream);
@@ -197,6 +207,9 @@ gbk_status gbk_ivfpq_train(gbk_index* ix, const float* x, int64_t n, const gbk_t
   for (int64_t v : pinit) GBK_REQUIRE(v >= 0 && v < n, "gbk_ivfpq_train: pq_init out of range");
   if (opts) ix->use_precomputed = opts->use_precomputed;
   gbk_status r;
+  Scratch xr;
+  const float* x = x_in;
+  if ((r = rotate_rows(ix, x_in, n, xr, &x, st)) != GBK_OK) return r;
   const int d = ix->d, M = ix->M, dsub = ix->dsub;
   if ((r = ix->coarse.alloc(sizeof(float) * (size_t)ix->nlist * d)) != GBK_OK) return r;
   if ((r = ix->pq.alloc(sizeof(float) * (size_t)M * 256 * dsub)) != GBK_OK) return r;
@@ -263,17 +276,20 @@ gbk_status gbk_ivfpq_set_quantizers(gbk_index* ix, const float* coarse, const fl
   return GBK_OK;
 }
 
-gbk_status gbk_ivfpq_add(gbk_index* ix, const float* x, int64_t n, const int64_t* ids,
+gbk_status gbk_ivfpq_add(gbk_index* ix, const float* x_in, int64_t n, const int64_t* ids,
                          void* stream) {
   clear_error();
   GBK_REQUIRE(ix, "gbk_ivfpq_add: NULL index");
   GBK_REQUIRE(ix->trained, "gbk_ivfpq_add: index not trained");
   GBK_REQUIRE(n >= 0, "gbk_ivfpq_add: n < 0");
   if (n == 0) return GBK_OK;
-  GBK_REQUIRE(x, "gbk_ivfpq_add: NULL x");
+  GBK_REQUIRE(x_in, "gbk_ivfpq_add: NULL x");
   GBK_REQUIRE(ix->n_staged + n < (int64_t(1) << 32) - 1, "gbk_ivfpq_add: index full (2^32)");
   cudaStream_t st = as_stream(stream);
   gbk_status r;
+  Scratch xr;
+  const float* x = x_in;
+  if ((r = rotate_rows(ix, x_in, n, xr, &x, st)) != GBK_OK) return r;
   const int64_t need = ix->n_staged + n;
   if (need > ix->cap_staged) {
     int64_t cap = std::max<int64_t>(need, ix->cap_staged * 2);
@@ -337,6 +353,40 @@ gbk_status gbk_ivfpq_keep_vectors(gbk_index* ix, int32_t keep) {
   return GBK_OK;
 }
 
+gbk_status gbk_ivfpq_set_rotation(gbk_index* ix, const float* R, void* stream) {
+  clear_error();
+  GBK_REQUIRE(ix, "gbk_ivfpq_set_rotation: NULL index");
+  GBK_REQUIRE(!ix->trained && ix->n_staged == 0,
+              "gbk_ivfpq_set_rotation: must be set before training and adding");
+  if (!R) {
+    ix->rot.release();
+    ix->rotated = false;
+    return GBK_OK;
+  }
+  gbk_status r;
+  const size_t b = sizeof(float) * (size_t)ix->d * ix->d;
+  if ((r = ix->rot.alloc(b)) != GBK_OK) return r;
+  GBK_CUDA_CHECK(cudaMemcpyAsync(ix->rot.p, R, b, cudaMemcpyDefault, as_stream(stream)));
+  ix->rotated = true;
+  return GBK_OK;
+}
+
+gbk_status gbk_ivfpq_rotate(gbk_index* ix, const float* x, int64_t n, float* out, void* stream) {
+  clear_error();
+  GBK_REQUIRE(ix, "gbk_ivfpq_rotate: NULL index");
+  GBK_REQUIRE(n >= 0 && n < (int64_t(1) << 31), "gbk_ivfpq_rotate: n out of range");
+  if (n == 0) return GBK_OK;
+  GBK_REQUIRE(x && out, "gbk_ivfpq_rotate: NULL pointer");
+  cudaStream_t st = as_stream(stream);
+  gbk_status r;
+  Scratch xr;
+  const float* y = x;
+  if ((r = rotate_rows(ix, x, n, xr, &y, st)) != GBK_OK) return r;
+  GBK_CUDA_CHECK(cudaMemcpyAsync(out, y, sizeof(float) * (size_t)n * ix->d,
+                                 cudaMemcpyDeviceToDevice, st));
+  return GBK_OK;
+}
+
 gbk_status gbk_ivfpq_search_refine(gbk_index* ix, const float* xq, int64_t nq, int32_t k,
                                    int32_t nprobe, int32_t kprime, float* D, int64_t* I,
                                    void* stream) {
@@ -359,11 +409,14 @@ gbk_status gbk_ivfpq_search_refine(gbk_index* ix, const float* xq, int64_t nq, i
   if ((r = Dc.alloc(sizeof(float) * (size_t)nq * kprime, st)) != GBK_OK) return r;
   if ((r = Ic.alloc(sizeof(int64_t) * (size_t)nq * kprime, st)) != GBK_OK) return r;
   // k' ADC candidates as list positions, exact distances from the stored vectors, top k
-  if ((r = gbk::search_run(ix, xq, nq, kprime, nprobe, Dc.as<float>(), Ic.as<int64_t>(), st,
-                           true)) != GBK_OK)
+  Scratch xr;
+  const float* xqr = xq;
+  if ((r = rotate_rows(ix, xq, nq, xr, &xqr, st)) != GBK_OK) return r;
+  if ((r = gbk::search_run(ix, xqr, nq, kprime, nprobe, Dc.as<float>(), Ic.as<int64_t>(), st,
+                           true, true)) != GBK_OK)
     return r;
-  if ((r = rerank_rows_run(xq, ix->vecs.as<float>(), nq, ix->d, kprime, k, Ic.as<int64_t>(), D, I,
-                           st)) != GBK_OK)
+  if ((r = rerank_rows_run(xqr, ix->vecs.as<float>(), nq, ix->d, kprime, k, Ic.as<int64_t>(), D,
+                           I, st)) != GBK_OK)
     return r;
   return rows_to_ids_run(I, nq * (int64_t)k, ix->ids.as<int64_t>(), st);
 }
@@ -372,10 +425,36 @@ gbk_status gbk_ivfpq_search_refine(gbk_index* ix, const float* xq, int64_t nq, i
 
 namespace gbk {
 // Algorithm 4 for a validated, finalized index.
-gbk_status search_run(gbk_index* ix, const float* xq, int64_t nq, int k, int nprobe, float* D,
-                      int64_t* I, cudaStream_t st, bool positions) {
+gbk_status rotate_rows(const gbk_index* ix, const float* x, int64_t n, Scratch& buf,
+                       const float** out, cudaStream_t st) {
+  if (!ix->rotated || n == 0) {
+    *out = x;
+    return GBK_OK;
+  }
   gbk_status r;
-  Scratch clD, clI, t3;
+  const int d = ix->d;
+  if ((r = buf.alloc(sizeof(float) * (size_t)n * d, st)) != GBK_OK) return r;
+  PreparedOperand Rp;
+  if ((r = prepare_operand(ix->rot.as<float>(), d, d, GBK_PREC_FP32, (d + 127) / 128 * 128, 0.f,
+                           &Rp, st)) != GBK_OK)
+    return r;
+  const int64_t CH = int64_t(1) << 20;
+  for (int64_t r0 = 0; r0 < n; r0 += CH) {
+    const int64_t c = std::min(CH, n - r0);
+    PreparedOperand Q;
+    if ((r = prepare_operand(x + r0 * d, c, d, GBK_PREC_FP32, c, 0.f, &Q, st)) != GBK_OK) return r;
+    if ((r = pairwise_run(Q, Rp, true, buf.as<float>() + r0 * d, d, st)) != GBK_OK) return r;
+  }
+  *out = buf.as<float>();
+  return GBK_OK;
+}
+
+gbk_status search_run(gbk_index* ix, const float* xq_in, int64_t nq, int k, int nprobe, float* D,
+                      int64_t* I, cudaStream_t st, bool positions, bool prerotated) {
+  gbk_status r;
+  Scratch clD, clI, t3, xr;
+  const float* xq = xq_in;
+  if (!prerotated && (r = rotate_rows(ix, xq_in, nq, xr, &xq, st)) != GBK_OK) return r;
   if ((r = clD.alloc(sizeof(float) * (size_t)nq * nprobe, st)) != GBK_OK) return r;
   if ((r = clI.alloc(sizeof(int64_t) * (size_t)nq * nprobe, st)) != GBK_OK) return r;
   // L_IVF (Eq. 5): the nprobe nearest coarse centroids, with term 2 = ||x - c||^2
@@ -481,11 +560,14 @@ gbk_status mlp_forward_classes(gbk_mlp* net, const float* X, int64_t B, int32_t*
                                cudaStream_t st);
 int mlp_inputs(const gbk_mlp* n);
 
-gbk_status batched_run(gbk_index* ix, const float* xq, int64_t nq, const int32_t* kq, int max_k,
-                       const int32_t* npq_in, int max_nprobe, gbk_mlp* mlp,
+gbk_status batched_run(gbk_index* ix, const float* xq_in, int64_t nq, const int32_t* kq,
+                       int max_k, const int32_t* npq_in, int max_nprobe, gbk_mlp* mlp,
                        const int64_t* out_off, float* D, int64_t* I, int32_t* np_used,
                        cudaStream_t st) {
   gbk_status r;
+  Scratch xr;
+  const float* xq = xq_in;
+  if ((r = rotate_rows(ix, xq_in, nq, xr, &xq, st)) != GBK_OK) return r;
   const int nfeat = 64;
   const int tau = std::min(ix->nlist, mlp ? std::max(max_nprobe, nfeat) : max_nprobe);
   Scratch clD, clI, t3, npq_s, F, cls, key, order, off32, counter;

@@ -27,7 +27,9 @@ def _same_up_to_near_ties(D, I, Do, Io):
     fin = np.isfinite(Do)
     assert np.array_equal(np.isfinite(D), fin)
     assert np.all(I[~fin] == -1)
-    assert np.all(np.abs(np.where(fin, D - Do, 0)) <= _tol(np.where(fin, Do, 0)))
+    diff = np.zeros_like(Do)
+    diff[fin] = D[fin] - Do[fin]
+    assert np.all(np.abs(diff) <= _tol(np.where(fin, Do, 0)))
     gap = np.full(Do.shape, np.inf)
     dd = np.abs(np.diff(np.where(fin, Do, 1e30), axis=1))
     gap[:, 1:] = np.minimum(gap[:, 1:], dd)

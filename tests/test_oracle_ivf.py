@@ -214,3 +214,24 @@ def test_refine_is_exact_top_k_of_the_adc_candidates():
         # re-ranking never loses ground: the k-th exact distance is at most ADC's choice's
         ex_adc = ((x[Ia[q, :10]].astype(np.float64) - xq[q].astype(np.float64)) ** 2).sum(1)
         assert D[q, -1] <= np.sort(ex_adc)[-1] + 1e-12
+
+
+# ------------------------------------------------------------------ OPQ pre-rotation
+
+def test_rotate_by_permutation_and_identity():
+    x = datagen.gaussian_matrix(180, 50, 6)
+    P = np.zeros((6, 6), np.float32)
+    perm = [1, 2, 0, 4, 5, 3]           # R y picks y[perm[i]] for output i (not an involution)
+    P[np.arange(6), perm] = 1.0
+    np.testing.assert_array_equal(oracle.rotate(x, P), x[:, perm])
+    np.testing.assert_array_equal(oracle.rotate(x, np.eye(6, dtype=np.float32)), x)
+
+
+def test_orthogonal_rotation_preserves_distances():
+    d = 24
+    Q, _ = np.linalg.qr(datagen.gaussian_matrix(181, d, d).astype(np.float64))
+    x = datagen.gaussian_matrix(182, 40, d)
+    y = oracle.rotate(x, Q.astype(np.float32))
+    D0 = ((x[:, None].astype(np.float64) - x[None]) ** 2).sum(-1)
+    D1 = ((y[:, None].astype(np.float64) - y[None]) ** 2).sum(-1)
+    np.testing.assert_allclose(D1, D0, rtol=1e-5, atol=1e-5)
