@@ -374,11 +374,12 @@ def run_learned(args):
     from paper_1702_08734_gb300 import datagen
     from oracle import mlp as omlp  # seeded initial weights only (uniform draws)
     g.load()
-    ix, cen, xb, t = build_ivfadc_index(g, datagen, args.ivf_n)
+    ix, cen, xb, t = build_ivfadc_index(g, datagen, args.ivf_n, keep_vectors=True)
+    KPR = 100  # k' of the re-ranked form (k = 10)
     coarse = torch.from_numpy(ix.export()["coarse"]).cuda()
     ntr, nq, chunk = args.learn_n, 10000, 20000
     taus = [1 << c for c in range(9)]
-    F_all, y_all = [], []
+    F_all, y_all, yr_all = [], [], []
     t0 = time.perf_counter()
     for q0 in range(0, ntr, chunk):
         xq = datagen.mixture_points_cuda(cen, 501, min(chunk, ntr - q0), row0=q0)
@@ -392,10 +393,21 @@ def run_learned(args):
         C = torch.stack(cnts, 1)                    # [q][9] overlap counts out of 10
         target = torch.clamp(C[:, -1:], max=10)     # min(10/10, recall at 256)
         y = torch.argmax((C >= target).to(torch.int32), dim=1).to(torch.int32)
+        # the same labels for the re-ranked search (k' = KPR exact re-rank)
+        cr = []
+        for tau in taus:
+            _, I = ix.search_refine(xq, 10, tau, KPR)
+            c = torch.empty(xq.shape[0], dtype=torch.int32, device="cuda")
+            g.recall_counts(I, Igt, c)
+            cr.append(c)
+        Cr = torch.stack(cr, 1)
+        yr_all.append(torch.argmax((Cr >= torch.clamp(Cr[:, -1:], max=10)).to(torch.int32),
+                                   dim=1).to(torch.int32))
         clD, _ = g.knn_brute(xq, coarse, 64)
         F_all.append(g.nprobe_features(xq, clD))
         y_all.append(y)
     F = torch.cat(F_all)
+    yr = torch.cat(yr_all)
     y = torch.cat(y_all)
     t["labels_s"] = time.perf_counter() - t0
     hist = torch.bincount(y.long(), minlength=9).cpu().tolist()
@@ -415,6 +427,16 @@ def run_learned(args):
         losses.append(float(l.item()))
     torch.cuda.synchronize()
     t["mlp_train_s"] = time.perf_counter() - t0
+    # a second network of the same shape and initial weights on the re-ranked labels
+    hist_r = torch.bincount(yr.long(), minlength=9).cpu().tolist()
+    net_r = g.MLP(192, 256, 256, 9,
+                  params=np.concatenate([p[kk].ravel() for kk in omlp.PARAM_NAMES]).astype(np.float32))
+    for ep in range(args.learn_epochs):
+        perm = torch.from_numpy(np.argsort(datagen.hash_u64(perm_seed + ep, 0, F.shape[0]))).cuda()
+        for b0 in range(0, F.shape[0] - bs + 1, bs):
+            idx = perm[b0:b0 + bs]
+            net_r.train_step(F[idx].contiguous(), yr[idx].contiguous(), lr=1e-3)
+    torch.cuda.synchronize()
     # evaluation queries
     xq = datagen.mixture_points_cuda(cen, 304, nq)
     _, Igt = g.knn_brute(xq, xb, 10)
@@ -460,17 +482,38 @@ def run_learned(args):
         g.recall_counts(G[samp].contiguous(), gt, c)
         graph[name] = {"seconds": el, "nodes": int(xb.shape[0]),
                        "R10@10_sampled": float(c.float().mean().item()) / 10}
-    # fixed-nprobe q/s at the learned recall (log-linear interpolation between neighbours)
-    eq = None
-    for a, b in zip(fixed, fixed[1:]):
-        if a["R10@10"] <= r10 <= b["R10@10"] and b["R10@10"] > a["R10@10"]:
-            w = (r10 - a["R10@10"]) / (b["R10@10"] - a["R10@10"])
-            eq = float(np.exp(np.log(a["qps"]) * (1 - w) + np.log(b["qps"]) * w))
+    def qps_at(rows, r):
+        """fixed-nprobe q/s at recall r (log-linear interpolation between neighbours)"""
+        for a, b in zip(rows, rows[1:]):
+            if a["R10@10"] <= r <= b["R10@10"] and b["R10@10"] > a["R10@10"]:
+                w = (r - a["R10@10"]) / (b["R10@10"] - a["R10@10"])
+                return float(np.exp(np.log(a["qps"]) * (1 - w) + np.log(b["qps"]) * w))
+        return None
+
+    eq = qps_at(fixed, r10)
+    # the re-ranked form: fixed nprobe + exact re-rank of k' = KPR vs the learned route +
+    # the same re-rank (one batched launch), at equal 10-R@10
+    fixed_r = []
+    for tau in taus:
+        ms, (D, I) = time_search(g, lambda: ix.search_refine(xq, 10, tau, KPR), args.steps)
+        _, rr = recall_stats(g, I, Igt)
+        fixed_r.append({"nprobe": tau, "qps": nq / (ms / 1e3), "R10@10": rr})
+    ms, (D, I, used_r) = time_search(
+        g, lambda: g.ivfpq_search_batched_refine(ix, xq, 10, KPR, None, cap, mlp=net_r),
+        args.steps)
+    _, rr = recall_stats(g, I, Igt)
+    eq_r = qps_at(fixed_r, rr)
+    refined = {"kprime": KPR, "label_hist": hist_r, "fixed": fixed_r,
+               "learned": {"qps": nq / (ms / 1e3), "R10@10": rr,
+                           "mean_nprobe": float(used_r.float().mean().item())},
+               "fixed_qps_at_learned_recall": eq_r,
+               "speedup_at_equal_recall": (nq / (ms / 1e3)) / eq_r if eq_r else None}
     print(json.dumps({"workload": "learned nprobe, nb=%d, %d training queries" % (args.ivf_n, ntr),
                       **t, "label_hist": hist, "loss_per_epoch": losses, "fixed": fixed,
                       "learned": learned, "knn_graph_k10": graph,
                       "fixed_qps_at_learned_recall": eq,
-                      "speedup_at_equal_recall": learned["qps"] / eq if eq else None}), flush=True)
+                      "speedup_at_equal_recall": learned["qps"] / eq if eq else None,
+                      "reranked": refined}), flush=True)
 
 
 def run_batched(args):

@@ -376,6 +376,19 @@ gbk_status gbk_ivfpq_search_batched(gbk_index* index, const float* xq, int64_t n
                                     gbk_mlp* mlp, const int64_t* out_offsets, float* D,
                                     int64_t* I, int32_t* nprobe_used, void* stream);
 
+/* Batched search with exact re-ranking (patterns 2 and 4 with the re-rank of
+ * gbk_ivfpq_search_refine): every query takes its kprime best ADC candidates from its own
+ * nprobe_per_q[q] lists (or the network's choice when nprobe_per_q is NULL, capped at
+ * max_nprobe, as in gbk_ivfpq_search_batched), then their exact float32 distances to the
+ * kept vectors and the k smallest.  D, I [nq][k]; nprobe_used [nq] (device, may be NULL).
+ * Query q's results equal gbk_ivfpq_search_refine's with its nprobe. */
+gbk_status gbk_ivfpq_search_batched_refine(gbk_index* index, const float* xq, int64_t nq,
+                                           int32_t k, int32_t kprime,
+                                           const int32_t* nprobe_per_q, int32_t max_nprobe,
+                                           gbk_mlp* mlp, float* D, int64_t* I,
+                                           int32_t* nprobe_used, void* stream);
+
+
 /* The launches of gbk_ivfpq_search_batched captured once into a CUDA graph on a private
  * stream (the index must not change afterwards; `stream` is synchronised before capture).
  * The graph reads the buffers given here on every replay: refill xq (and k_per_q,

@@ -511,6 +511,8 @@ _SIGNATURES.update({
     "gbk_nprobe_features": [_vp, _i64, _i32, _vp, _i32, _i32, _vp, _vp],
     "gbk_ivfpq_search_batched": [_vp, _vp, _i64, _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp,
                                  _vp],
+    "gbk_ivfpq_search_batched_refine": [_vp, _vp, _i64, _i32, _i32, _vp, _i32, _vp, _vp, _vp,
+                                        _vp, _vp],
     "gbk_ivfpq_batched_graph": [_vp, _vp, _i64, _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp,
                                 _vp, _vp],
     "gbk_graph_launch": [_vp, _vp],
@@ -598,6 +600,22 @@ def ivfpq_search_batched(index, xq, k_per_q, max_k, nprobe_per_q=None, max_nprob
           int(max_nprobe), mlp._h if mlp is not None else None, _ptr(off), _ptr(D), _ptr(I),
           _ptr(used), _stream())
     return D, I, off, used
+
+
+def ivfpq_search_batched_refine(index, xq, k, kprime, nprobe_per_q=None, max_nprobe=256,
+                                mlp=None):
+    """Batched search (per-query nprobe, or chosen by a trained MLP) of kprime ADC candidates
+    re-ranked by exact float32 distances to the kept vectors.  Returns (D, I, nprobe_used)."""
+    _dev(xq, torch.float32, "xq")
+    nq = xq.shape[0]
+    D = torch.empty((nq, k), dtype=torch.float32, device=xq.device)
+    I = torch.empty((nq, k), dtype=torch.int64, device=xq.device)
+    used = torch.empty(nq, dtype=torch.int32, device=xq.device)
+    npq = nprobe_per_q.to(torch.int32).contiguous() if nprobe_per_q is not None else None
+    _call("gbk_ivfpq_search_batched_refine", index._h, _ptr(xq), nq, int(k), int(kprime),
+          _ptr(npq), int(max_nprobe), mlp._h if mlp is not None else None, _ptr(D), _ptr(I),
+          _ptr(used), _stream())
+    return D, I, used
 
 
 def knn_graph(index, x, k, nprobe, mlp=None, self_ids=None, batch=0, distances=True):

@@ -560,14 +560,16 @@ gbk_status mlp_forward_classes(gbk_mlp* net, const float* X, int64_t B, int32_t*
                                cudaStream_t st);
 int mlp_inputs(const gbk_mlp* n);
 
+// kq / out_off may be null (every query max_k results at q * max_k); positions: list
+// positions out instead of ids; prerotated: xq already in the index's rotated space.
 gbk_status batched_run(gbk_index* ix, const float* xq_in, int64_t nq, const int32_t* kq,
                        int max_k, const int32_t* npq_in, int max_nprobe, gbk_mlp* mlp,
                        const int64_t* out_off, float* D, int64_t* I, int32_t* np_used,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool positions = false, bool prerotated = false) {
   gbk_status r;
   Scratch xr;
   const float* xq = xq_in;
-  if ((r = rotate_rows(ix, xq_in, nq, xr, &xq, st)) != GBK_OK) return r;
+  if (!prerotated && (r = rotate_rows(ix, xq_in, nq, xr, &xq, st)) != GBK_OK) return r;
   const int nfeat = 64;
   const int tau = std::min(ix->nlist, mlp ? std::max(max_nprobe, nfeat) : max_nprobe);
   Scratch clD, clI, t3, npq_s, F, cls, key, order, off32, counter;
@@ -619,9 +621,9 @@ gbk_status batched_run(gbk_index* ix, const float* xq_in, int64_t nq, const int3
   GBK_CUDA_CHECK(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), st));
   return ivf_scan_run(ix->M, nq, tau, max_k, clI.as<int64_t>(), clD.as<float>(), ix->T.as<float>(),
                       t3.as<float>(), xq, ix->coarse.as<float>(), ix->pq.as<float>(), ix->d, direct,
-                      ix->list_off.as<int64_t>(), ix->codes.as<uint8_t>(), ix->ids.as<int64_t>(),
-                      D, I, st, kq, npq, out_off, order.as<int64_t>(),
-                      counter.as<unsigned long long>(), ix->tuning);
+                      ix->list_off.as<int64_t>(), ix->codes.as<uint8_t>(),
+                      positions ? nullptr : ix->ids.as<int64_t>(), D, I, st, kq, npq, out_off,
+                      order.as<int64_t>(), counter.as<unsigned long long>(), ix->tuning);
 }
 
 }  // namespace gbk
@@ -668,6 +670,46 @@ gbk_status gbk_ivfpq_search_batched(gbk_index* ix, const float* xq, int64_t nq,
   if ((r = finalize(ix, st)) != GBK_OK) return r;
   return batched_run(ix, xq, nq, k_per_q, max_k, nprobe_per_q, max_nprobe, mlp, out_offsets, D, I,
                      nprobe_used, st);
+}
+
+gbk_status gbk_ivfpq_search_batched_refine(gbk_index* ix, const float* xq, int64_t nq,
+                                           int32_t k, int32_t kprime,
+                                           const int32_t* nprobe_per_q, int32_t max_nprobe,
+                                           gbk_mlp* mlp, float* D, int64_t* I,
+                                           int32_t* nprobe_used, void* stream) {
+  clear_error();
+  GBK_REQUIRE(ix && ix->trained, "batched refine: index missing or not trained");
+  GBK_REQUIRE(ix->keep_vectors, "batched refine: the index keeps no vectors");
+  GBK_REQUIRE(k >= 1 && kprime >= k && kprime <= GBK_MAX_K,
+              "batched refine: need 1 <= k <= kprime <= %d", GBK_MAX_K);
+  GBK_REQUIRE(nq >= 0 && nq < (int64_t(1) << 31), "batched refine: nq out of range");
+  GBK_REQUIRE(max_nprobe >= 1 && max_nprobe <= ix->nlist && max_nprobe <= GBK_MAX_K,
+              "batched refine: max_nprobe out of range");
+  GBK_REQUIRE(nprobe_per_q || mlp, "batched refine: give nprobe_per_q or a network");
+  if (!nprobe_per_q) {
+    GBK_REQUIRE(ix->nlist >= 64, "learned nprobe needs nlist >= 64 (64 coarse-distance features)");
+    GBK_REQUIRE(gbk::mlp_inputs(mlp) == ix->d + 64,
+                "learned nprobe: network inputs must be d + 64 = %d", ix->d + 64);
+  }
+  if (nq == 0) return GBK_OK;
+  GBK_REQUIRE(xq && D && I, "batched refine: NULL pointer");
+  cudaStream_t st = as_stream(stream);
+  gbk_status r;
+  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  Scratch xr, Dc, Ic;
+  const float* xqr = xq;
+  if ((r = rotate_rows(ix, xq, nq, xr, &xqr, st)) != GBK_OK) return r;
+  if ((r = Dc.alloc(sizeof(float) * (size_t)nq * kprime, st)) != GBK_OK) return r;
+  if ((r = Ic.alloc(sizeof(int64_t) * (size_t)nq * kprime, st)) != GBK_OK) return r;
+  // k' ADC candidates per query (list positions) from the mixed-nprobe scan, then the exact
+  // float32 re-rank from the kept vectors and the ids of the k winners
+  if ((r = batched_run(ix, xqr, nq, nullptr, kprime, nprobe_per_q, max_nprobe, mlp, nullptr,
+                       Dc.as<float>(), Ic.as<int64_t>(), nprobe_used, st, true, true)) != GBK_OK)
+    return r;
+  if ((r = rerank_rows_run(xqr, ix->vecs.as<float>(), nq, ix->d, kprime, k, Ic.as<int64_t>(), D,
+                           I, st)) != GBK_OK)
+    return r;
+  return rows_to_ids_run(I, nq * (int64_t)k, ix->ids.as<int64_t>(), st);
 }
 
 gbk_status gbk_ivfpq_batched_graph(gbk_index* ix, const float* xq, int64_t nq,

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "ivf.cuh"
+#include "knn.cuh"
 #include "select_core.cuh"
 #include "sm100.cuh"
 
@@ -109,47 +110,18 @@ __global__ void term1_kernel(const float* __restrict__ coarse, const float* __re
   }
 }
 
-// term3[q][c][m] = <x^m, C_m[c]>.  A block serves T3_QB queries so each codebook row is
-// read once per block (into registers) instead of once per query; thread per (c, m) with m
-// fastest, so the output rows are written contiguously.
-constexpr int T3_QB = 8;
-__global__ void __launch_bounds__(256)
-    term3_kernel(const float* __restrict__ xq, int64_t nq, const float* __restrict__ pq, int d,
-                 int M, float* __restrict__ t3) {
-  const int64_t q0 = (int64_t)blockIdx.x * T3_QB;
-  const int nqb = nq - q0 < T3_QB ? (int)(nq - q0) : T3_QB;
+// term3[q][c][m] = <x^m, C_m[c]> (Eq. 11's third term) is one GEMM: against the
+// block-diagonal codebook matrix E [256 M][d] whose row c M + m holds C_m[c] in the
+// columns of sub-vector m (zeros elsewhere), x E^T is exactly term3 in its [c][m] layout.
+// The zeros cost M times the useful multiply-adds, which the tensor cores absorb.
+__global__ void expand_codebooks_kernel(const float* __restrict__ pq, int d, int M,
+                                        float* __restrict__ E) {
   const int dsub = d / M;
-  extern __shared__ __align__(16) float xs[];  // [T3_QB][d]
-  for (int i = threadIdx.x; i < nqb * d; i += blockDim.x) xs[i] = xq[q0 * d + i];
-  __syncthreads();
-  for (int e = threadIdx.x; e < M * 256; e += blockDim.x) {  // e = c * M + m
-    const int m = e % M, c = e / M;
-    const float* C = pq + ((int64_t)m * 256 + c) * dsub;
-    float cr[32];
-#pragma unroll
-    for (int t = 0; t < 32; t++) cr[t] = t < dsub ? __ldg(C + t) : 0.f;
-    const bool v4 = (dsub & 3) == 0 && (d & 3) == 0;  // 16-byte reads of the sub-vector
-    for (int j = 0; j < nqb; j++) {
-      const float* x = xs + j * d + m * dsub;
-      float ip = 0.f;
-      if (v4) {
-#pragma unroll
-        for (int t4 = 0; t4 < 8; t4++) {
-          if (4 * t4 < dsub) {
-            const float4 xv = reinterpret_cast<const float4*>(x)[t4];
-            ip = fmaf(xv.x, cr[4 * t4], ip);
-            ip = fmaf(xv.y, cr[4 * t4 + 1], ip);
-            ip = fmaf(xv.z, cr[4 * t4 + 2], ip);
-            ip = fmaf(xv.w, cr[4 * t4 + 3], ip);
-          }
-        }
-      } else {
-#pragma unroll
-        for (int t = 0; t < 32; t++)
-          if (t < dsub) ip = fmaf(x[t], cr[t], ip);
-      }
-      t3[(q0 + j) * M * 256 + e] = ip;
-    }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)256 * M * d;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int row = (int)(e / d), t = (int)(e % d);
+    const int c = row / M, m = row % M;
+    E[e] = (t / dsub == m) ? pq[((int64_t)m * 256 + c) * dsub + (t % dsub)] : 0.f;
   }
 }
 
@@ -523,18 +495,20 @@ gbk_status term1_run(const float* coarse, const float* pq, int nlist, int d, int
 gbk_status term3_run(const float* xq, int64_t nq, const float* pq, int d, int M, float* t3,
                      cudaStream_t st) {
   if (nq == 0) return GBK_OK;
-  if (d > 1024) return set_error(GBK_EUNSUPPORTED, "term 3 supports d <= 1024");
   ProfScope prof("term3", st);
-  const size_t smem = sizeof(float) * T3_QB * d;  // <= 64 KB
-  static bool attr = false;
-  if (!attr) {
-    GBK_CUDA_CHECK(cudaFuncSetAttribute(term3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(float) * T3_QB * 1024)));
-    attr = true;
-  }
-  term3_kernel<<<(unsigned)((nq + T3_QB - 1) / T3_QB), 256, smem, st>>>(xq, nq, pq, d, M, t3);
+  gbk_status r;
+  const int64_t ne = (int64_t)256 * M;
+  Scratch E;
+  if ((r = E.alloc(sizeof(float) * (size_t)ne * d, st)) != GBK_OK) return r;
+  expand_codebooks_kernel<<<(unsigned)std::min<int64_t>((ne * d + 255) / 256, 4096), 256, 0, st>>>(
+      pq, d, M, E.as<float>());
   GBK_LAUNCH_CHECK();
-  return GBK_OK;
+  PreparedOperand Q, B;
+  if ((r = prepare_operand(xq, nq, d, GBK_PREC_FP32, nq, 0.f, &Q, st)) != GBK_OK) return r;
+  if ((r = prepare_operand(E.as<float>(), ne, d, GBK_PREC_FP32, (ne + 127) / 128 * 128, 0.f, &B,
+                           st)) != GBK_OK)
+    return r;
+  return pairwise_run(Q, B, true, t3, ne, st);
 }
 
 }  // namespace gbk

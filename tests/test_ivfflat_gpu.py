@@ -197,3 +197,17 @@ def test_refine_arguments(gbk):
     for k, kprime in ((10, 5), (0, 5), (10, 1025)):
         with pytest.raises(gbk.GbkError):
             ix2.search_refine(xqt, k, 2, kprime)
+
+
+def test_batched_refine_equals_per_query_refine(gbk):
+    # mixed nprobe in one persistent scan + re-rank: each query's results are those of the
+    # single-nprobe refine search (same candidates, same re-rank arithmetic)
+    ix, x, xq, _, _ = _ivfpq(gbk, 280)
+    xqt = torch.from_numpy(xq).cuda()
+    npq = torch.from_numpy(np.array([1, 2, 4, 8])[datagen.randint(281, 0, xq.shape[0], 4)]).cuda()
+    D, I, used = gbk.ivfpq_search_batched_refine(ix, xqt, 10, 60, npq, 8)
+    assert torch.equal(used, npq.to(torch.int32))
+    for t in (1, 2, 4, 8):
+        sel = (npq == t).nonzero().flatten()
+        Dr, Ir = ix.search_refine(xqt[sel].contiguous(), 10, t, 60)
+        assert torch.equal(I[sel], Ir) and torch.equal(D[sel], Dr)
