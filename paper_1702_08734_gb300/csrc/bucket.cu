@@ -3,9 +3,11 @@
 // layout of section 2 ("groups the vectors into inverted lists"), lists in insertion
 // order, and the member lists of k-means clusters.
 //
-// counts (atomics) -> exclusive scan (one block) -> scatter (atomic cursors, unordered)
-// -> per-bucket ordering: buckets of up to SORT_CAP members are sorted in shared memory;
-// larger ones are rebuilt by an order-preserving compaction over the key array.
+// Many buckets: counts (atomics) -> exclusive scan (one block) -> scatter (atomic cursors,
+// unordered) -> per-bucket ordering: buckets of up to SORT_CAP members are sorted in shared
+// memory; larger ones are rebuilt by an order-preserving compaction over the key array.
+// Few buckets (<= 4,096): per-tile histograms, a bucket-major scan of them, and a stable
+// scatter from each tile sorted by (key, position) in shared memory.
 #include <algorithm>
 
 #include "common.cuh"
@@ -124,11 +126,143 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
+// ---- tiled path (few buckets): per-tile histograms, a bucket-major scan, and a stable
+// scatter from a sorted tile.  No global atomics, so few large buckets cost no contention.
+constexpr int TILE = 2048, TILE_T = 256, TILE_BITS = 11;
+
+__global__ void __launch_bounds__(TILE_T)
+    tile_hist_kernel(const int32_t* __restrict__ keys, int64_t n, int nb, int ntiles,
+                     uint32_t* __restrict__ H) {
+  extern __shared__ uint32_t h[];  // [nb]
+  const int tile = blockIdx.x;
+  for (int b = threadIdx.x; b < nb; b += TILE_T) h[b] = 0u;
+  __syncthreads();
+  const int64_t i0 = (int64_t)tile * TILE;
+  for (int j = threadIdx.x; j < TILE; j += TILE_T)
+    if (i0 + j < n) atomicAdd(&h[keys[i0 + j]], 1u);
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += TILE_T) H[(int64_t)b * ntiles + tile] = h[b];
+}
+
+// Block-wide exclusive scan of one value per thread (TILE_T threads); returns the total.
+__device__ __forceinline__ int64_t block_exscan(int64_t v, int64_t* sh, int64_t& excl) {
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int o = 1; o < TILE_T; o <<= 1) {
+    const int64_t u = t >= o ? sh[t - o] : 0;
+    __syncthreads();
+    sh[t] += u;
+    __syncthreads();
+  }
+  excl = sh[t] - v;
+  const int64_t tot = sh[TILE_T - 1];
+  __syncthreads();
+  return tot;
+}
+
+// One block per bucket: the bucket's total over all tiles.
+__global__ void __launch_bounds__(TILE_T)
+    row_total_kernel(const uint32_t* __restrict__ H, int ntiles,
+                     unsigned long long* __restrict__ tot) {
+  __shared__ int64_t sh[TILE_T];
+  const int b = blockIdx.x;
+  int64_t s = 0;
+  for (int t = threadIdx.x; t < ntiles; t += TILE_T) s += H[(int64_t)b * ntiles + t];
+  int64_t excl;
+  const int64_t all = block_exscan(s, sh, excl);
+  if (threadIdx.x == 0) tot[b] = (unsigned long long)all;
+}
+
+// One block per bucket: H[b][t] <- offsets[b] + sum of H[b][t'] for t' < t (global base of
+// bucket b's members in tile t).  Rows are scanned in per-thread runs of consecutive tiles.
+__global__ void __launch_bounds__(TILE_T)
+    row_scan_kernel(uint32_t* __restrict__ H, int ntiles, const int64_t* __restrict__ offsets,
+                    int64_t* __restrict__ base) {
+  __shared__ int64_t sh[TILE_T];
+  const int b = blockIdx.x;
+  const int per = (ntiles + TILE_T - 1) / TILE_T;
+  const int t0 = threadIdx.x * per, t1 = min(ntiles, t0 + per);
+  int64_t s = 0;
+  for (int t = t0; t < t1; t++) s += H[(int64_t)b * ntiles + t];
+  int64_t run;
+  block_exscan(s, sh, run);
+  run += offsets[b];
+  for (int t = t0; t < t1; t++) {
+    const int64_t c = H[(int64_t)b * ntiles + t];
+    base[(int64_t)b * ntiles + t] = run;
+    run += c;
+  }
+}
+
+// Per tile: sort (key << 11 | position in tile) in shared memory; an element's rank among
+// the tile's members of its bucket is its distance to the start of its key's run.
+__global__ void __launch_bounds__(TILE_T)
+    tile_scatter_kernel(const int32_t* __restrict__ keys, int64_t n, int nb, int ntiles,
+                        const int64_t* __restrict__ base, int64_t* __restrict__ order) {
+  __shared__ uint32_t v[TILE];
+  extern __shared__ uint32_t start[];  // [nb] first sorted index of each key in the tile
+  const int tile = blockIdx.x;
+  const int64_t i0 = (int64_t)tile * TILE;
+  for (int j = threadIdx.x; j < TILE; j += TILE_T)
+    v[j] = i0 + j < n ? ((uint32_t)keys[i0 + j] << TILE_BITS) | (uint32_t)j : 0xffffffffu;
+  __syncthreads();
+  for (int size = 2; size <= TILE; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < TILE / 2; t += TILE_T) {
+        const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+        const bool asc = (lo & size) == 0;
+        const uint32_t a = v[lo], c = v[hi];
+        if ((a > c) == asc) {
+          v[lo] = c;
+          v[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int j = threadIdx.x; j < TILE; j += TILE_T) {
+    const uint32_t e = v[j];
+    if (e != 0xffffffffu && (j == 0 || (v[j - 1] >> TILE_BITS) != (e >> TILE_BITS)))
+      start[e >> TILE_BITS] = (uint32_t)j;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < TILE; j += TILE_T) {
+    const uint32_t e = v[j];
+    if (e == 0xffffffffu) continue;
+    const uint32_t key = e >> TILE_BITS;
+    order[base[(int64_t)key * ntiles + tile] + (j - (int)start[key])] =
+        i0 + (int64_t)(e & (TILE - 1));
+  }
+}
+
 }  // namespace
+
+static gbk_status bucket_tiled(const int32_t* keys, int64_t n, int nb, int64_t* offsets,
+                               int64_t* order, cudaStream_t st) {
+  const int ntiles = (int)((n + TILE - 1) / TILE);
+  Scratch H, base, tot, cursor;
+  gbk_status r;
+  if ((r = H.alloc(sizeof(uint32_t) * (size_t)nb * ntiles, st)) != GBK_OK) return r;
+  if ((r = base.alloc(sizeof(int64_t) * (size_t)nb * ntiles, st)) != GBK_OK) return r;
+  if ((r = tot.alloc(sizeof(unsigned long long) * (size_t)nb, st)) != GBK_OK) return r;
+  if ((r = cursor.alloc(sizeof(int64_t) * (size_t)nb, st)) != GBK_OK) return r;
+  const size_t hs = sizeof(uint32_t) * (size_t)nb;
+  tile_hist_kernel<<<ntiles, TILE_T, hs, st>>>(keys, n, nb, ntiles, H.as<uint32_t>());
+  row_total_kernel<<<nb, TILE_T, 0, st>>>(H.as<uint32_t>(), ntiles, tot.as<unsigned long long>());
+  scan_kernel<<<1, 1024, 0, st>>>(tot.as<unsigned long long>(), nb, offsets, cursor.as<int64_t>());
+  row_scan_kernel<<<nb, TILE_T, 0, st>>>(H.as<uint32_t>(), ntiles, offsets, base.as<int64_t>());
+  tile_scatter_kernel<<<ntiles, TILE_T, hs, st>>>(keys, n, nb, ntiles, base.as<int64_t>(), order);
+  GBK_LAUNCH_CHECK();
+  return GBK_OK;
+}
 
 gbk_status bucket_stable(const int32_t* keys, int64_t n, int nb, int64_t* offsets, int64_t* order,
                          cudaStream_t st) {
   ProfScope prof("bucket_stable", st);
+  // few buckets (k-means with up to 4,096 clusters, work-order keys): the tiled path
+  if (n > 0 && nb <= 4096 && (int64_t)nb * ((n + TILE - 1) / TILE) <= (int64_t(1) << 24))
+    return bucket_tiled(keys, n, nb, offsets, order, st);
   Scratch counts, cursor, big;
   gbk_status r;
   if ((r = counts.alloc(sizeof(unsigned long long) * (size_t)nb, st)) != GBK_OK) return r;
