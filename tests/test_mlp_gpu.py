@@ -104,3 +104,27 @@ def test_training_reduces_loss_and_is_deterministic(gbk):
         runs.append((l0, l1, net.params().cpu().numpy()))
     assert runs[0][1] < 0.5 * runs[0][0], runs[0][:2]
     np.testing.assert_array_equal(runs[0][2], runs[1][2])
+
+
+@pytest.mark.parametrize("sizes", [(100, 70, 50, 5), (64, 256, 33, 40), (300, 64, 64, 9)])
+def test_forward_other_sizes_match_oracle(gbk, sizes):
+    # shapes other than the learned-nprobe network's: ragged tiles in every layer
+    n_in, h1, h2, n_out = sizes
+    shapes = [(h1, n_in), (h1,), (h2, h1), (h2,), (n_out, h2), (n_out,)]
+    n = sum(int(np.prod(s)) for s in shapes)
+    p = omlp.init_params(sizes, datagen.uniform24(7, 0, n).astype(np.float64))
+    flat = np.concatenate([p[k].ravel() for k in omlp.PARAM_NAMES]).astype(np.float32)
+    net = gbk.MLP(*sizes, params=flat)
+    X = datagen.gaussian_matrix(8, 77, n_in)  # a ragged last block of rows
+    z, cls = net.forward(torch.from_numpy(X).cuda())
+    ref, pos = {}, 0
+    for name, shp in zip(omlp.PARAM_NAMES, shapes):
+        cnt = int(np.prod(shp))
+        v = torch.from_numpy(np.ascontiguousarray(flat[pos:pos + cnt]))
+        if name.startswith("W"):
+            v = v.to(torch.bfloat16).to(torch.float32)
+        ref[name] = v.numpy().astype(np.float64).reshape(shp)
+        pos += cnt
+    zo, _ = omlp.forward(ref, X)
+    np.testing.assert_allclose(z.cpu().numpy(), zo, rtol=1e-4, atol=1e-4)
+    assert (cls.cpu().numpy() == zo.argmax(1)).mean() > 0.97
