@@ -355,8 +355,9 @@ def run_kmeans(args):
     del x
     torch.cuda.empty_cache()
     n2, nc2 = args.km_large_n, 85000
-    x = datagen.mixture_points_cuda(datagen.mixture_centres(611, 4096, 128), 612, n2)
-    out["large_1e8x128_nc85000"] = run(x, np.arange(nc2), args.km_large_iters)
+    if n2 > 0:  # --km-large-n 0 leaves the large case out (profiling runs)
+        x = datagen.mixture_points_cuda(datagen.mixture_centres(611, 4096, 128), 612, n2)
+        out["large_1e8x128_nc85000"] = run(x, np.arange(nc2), args.km_large_iters)
     print(json.dumps({"workload": "kmeans %d x 784 (nc 256, 4096; 20 iterations) and %d x 128 "
                       "(nc 85000; %d iterations)" % (n, n2, args.km_large_iters), **out}),
           flush=True)
