@@ -10,6 +10,12 @@ step).  All inputs (2.6 GB + 0.5 GB) exceed the 129 MB L2, so no flush is needed
 
 --impl reference times the CPU oracle (plain double-precision C, all host cores) on a
 bounded sample of the same workload.
+
+Other workloads (one JSON object each, not the bench line): --workload ivfadc (IVFADC on a
+10M x 128 mixture, nprobe sweep with recall; exact re-rank of ADC candidates; IVF-Flat),
+learned (learned vs fixed nprobe at equal recall, plain and re-ranked; the 10M-node k-NN
+graph), batched (200M x 96, one graph-captured mixed-k / mixed-nprobe launch), kmeans
+(8.1M x 784 and 1e8 x 128 clustering).
 """
 import argparse
 import json
