@@ -479,10 +479,11 @@ def run_learned(args):
     gt = np.stack([np.concatenate([r[r != s_], r[r == s_]])[:10] for r, s_ in zip(Ie, sid)])
     gt = torch.from_numpy(gt).cuda()
     graph = {}
-    for name, kw in (("learned", {"mlp": net}), ("fixed_nprobe1", {})):
+    for name, kw in (("learned", {"mlp": net}), ("fixed_nprobe1", {}),
+                     ("fixed_nprobe1_reranked_kprime32", {"kprime": 32})):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, G = g.knn_graph(ix, xb, 10, cap if kw else 1, distances=False, **kw)
+        _, G = g.knn_graph(ix, xb, 10, cap if "mlp" in kw else 1, distances=False, **kw)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         c = torch.empty(samp.shape[0], dtype=torch.int32, device="cuda")

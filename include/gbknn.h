@@ -204,7 +204,7 @@ gbk_status gbk_kmeans(const float* x, int64_t n, int32_t d, int32_t nc, int32_t 
  * owns its device memory.  Not thread-safe: serialise calls on one index. */
 typedef struct gbk_index gbk_index;
 
-/* d % M == 0, M in {8, 16, 32}, d / M <= 32, nbits == 8, metric == GBK_METRIC_L2 (the
+/* d % M == 0, M in {4, 8, 16, 32}, d / M <= 32, nbits == 8, metric == GBK_METRIC_L2 (the
  * paper's IVFADC is defined for L2, Eq. 6; others give GBK_EUNSUPPORTED). */
 gbk_status gbk_ivfpq_create(int32_t d, int32_t nlist, int32_t M, int32_t nbits, int32_t metric,
                             gbk_index** out);
@@ -465,6 +465,16 @@ gbk_status gbk_ivfpq_autotune(gbk_index* index, const float* xq, int64_t nq,
 gbk_status gbk_ivfpq_knn_graph(gbk_index* index, const float* x, int64_t n,
                                const int64_t* self_ids, int32_t k, int32_t nprobe, gbk_mlp* mlp,
                                int64_t batch, float* GD, int64_t* G, void* stream);
+
+/* The same graph with exact re-ranking: each vector's kprime best ADC candidates (kprime >
+ * k, as in gbk_ivfpq_search_refine) are re-scored by exact float32 distances to the kept
+ * vectors, the k + 1 best kept, its own id dropped.  GD then holds exact squared
+ * distances.  Needs gbk_ivfpq_keep_vectors before the adds (EINVAL otherwise); scratch
+ * grows by batch * kprime * 12 bytes. */
+gbk_status gbk_ivfpq_knn_graph_refine(gbk_index* index, const float* x, int64_t n,
+                                      const int64_t* self_ids, int32_t k, int32_t nprobe,
+                                      int32_t kprime, gbk_mlp* mlp, int64_t batch, float* GD,
+                                      int64_t* G, void* stream);
 
 #ifdef __cplusplus
 }

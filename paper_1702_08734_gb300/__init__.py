@@ -517,6 +517,8 @@ _SIGNATURES.update({
                                 _vp, _vp],
     "gbk_graph_launch": [_vp, _vp],
     "gbk_ivfpq_knn_graph": [_vp, _vp, _i64, _vp, _i32, _i32, _vp, _i64, _vp, _vp, _vp],
+    "gbk_ivfpq_knn_graph_refine": [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _i64, _vp,
+                                   _vp, _vp],
     "gbk_merge_topk": [_vp, _vp, _i32, _i64, _i32, _i32, _i32, _vp, _vp, _vp],
     "gbk_ivfpq_set_tuning": [_vp, _i32, _i32],
     "gbk_ivfpq_get_tuning": [_vp, _vp, _vp],
@@ -618,16 +620,22 @@ def ivfpq_search_batched_refine(index, xq, k, kprime, nprobe_per_q=None, max_npr
     return D, I, used
 
 
-def knn_graph(index, x, k, nprobe, mlp=None, self_ids=None, batch=0, distances=True):
+def knn_graph(index, x, k, nprobe, mlp=None, self_ids=None, batch=0, distances=True, kprime=0):
     """k-NN graph (section 6.5): each row of x searched for k+1 neighbours, its own id
-    (self_ids[i], default i) removed.  Returns (GD, G) [n][k] (GD None if not requested)."""
+    (self_ids[i], default i) removed; kprime > k re-ranks that many ADC candidates by exact
+    distances to the kept vectors.  Returns (GD, G) [n][k] (GD None if not requested)."""
     _dev(x, torch.float32, "x")
     n = x.shape[0]
     G = torch.empty((n, k), dtype=torch.int64, device=x.device)
     GD = torch.empty((n, k), dtype=torch.float32, device=x.device) if distances else None
     sid = self_ids.to(torch.int64).contiguous() if self_ids is not None else None
-    _call("gbk_ivfpq_knn_graph", index._h, _ptr(x), n, _ptr(sid), int(k), int(nprobe),
-          mlp._h if mlp is not None else None, int(batch), _ptr(GD), _ptr(G), _stream())
+    h = mlp._h if mlp is not None else None
+    if kprime:
+        _call("gbk_ivfpq_knn_graph_refine", index._h, _ptr(x), n, _ptr(sid), int(k), int(nprobe),
+              int(kprime), h, int(batch), _ptr(GD), _ptr(G), _stream())
+    else:
+        _call("gbk_ivfpq_knn_graph", index._h, _ptr(x), n, _ptr(sid), int(k), int(nprobe), h,
+              int(batch), _ptr(GD), _ptr(G), _stream())
     return GD, G
 
 

@@ -177,8 +177,8 @@ gbk_status gbk_ivfpq_create(int32_t d, int32_t nlist, int32_t M, int32_t nbits, 
   if (nbits != 8) return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: only 8-bit codes");
   if (metric != GBK_METRIC_L2)
     return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: IVFADC is defined for L2 (Eq. 6)");
-  if (M != 8 && M != 16 && M != 32)
-    return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: M must be 8, 16 or 32");
+  if (M != 4 && M != 8 && M != 16 && M != 32)
+    return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: M must be 4, 8, 16 or 32");
   if (d / M > 32) return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: d/M must be <= 32");
   gbk_index* ix = new gbk_index();
   ix->d = d;
@@ -822,14 +822,15 @@ __global__ void fill_graph_args_kernel(int64_t n, int kk, int32_t* kq, int64_t* 
 
 extern "C" {
 
-gbk_status gbk_ivfpq_knn_graph(gbk_index* ix, const float* x, int64_t n, const int64_t* self_ids,
-                               int32_t k, int32_t nprobe, gbk_mlp* mlp, int64_t batch,
-                               float* GD, int64_t* G, void* stream) {
-  clear_error();
+static gbk_status knn_graph_run(gbk_index* ix, const float* x, int64_t n, const int64_t* self_ids,
+                                int32_t k, int32_t nprobe, int32_t kprime, gbk_mlp* mlp,
+                                int64_t batch, float* GD, int64_t* G, void* stream) {
   GBK_REQUIRE(ix && ix->trained, "gbk_ivfpq_knn_graph: index missing or not trained");
   GBK_REQUIRE(k >= 1 && k < GBK_MAX_K, "gbk_ivfpq_knn_graph: k out of [1, %d)", GBK_MAX_K);
   GBK_REQUIRE(nprobe >= 1 && nprobe <= ix->nlist && nprobe <= GBK_MAX_K,
               "gbk_ivfpq_knn_graph: nprobe out of range");
+  GBK_REQUIRE(kprime == 0 || (kprime > k && kprime <= GBK_MAX_K && ix->keep_vectors),
+              "gbk_ivfpq_knn_graph: re-rank needs k < kprime <= %d and kept vectors", GBK_MAX_K);
   GBK_REQUIRE(n >= 0, "gbk_ivfpq_knn_graph: n < 0");
   if (n == 0) return GBK_OK;
   GBK_REQUIRE(x && G, "gbk_ivfpq_knn_graph: NULL pointer");
@@ -838,16 +839,21 @@ gbk_status gbk_ivfpq_knn_graph(gbk_index* ix, const float* x, int64_t n, const i
     GBK_REQUIRE(gbk::mlp_inputs(mlp) == ix->d + 64,
                 "learned nprobe: network inputs must be d + 64 = %d", ix->d + 64);
   }
+  const int kk = k + 1;
+  const int kc = kprime > 0 ? kprime : kk;  // candidates per query from the scan
   if (batch <= 0) batch = int64_t(1) << 20;
-  batch = std::min<int64_t>(batch, std::min<int64_t>(n, (int64_t(1) << 31) / (k + 1) - 1));
+  batch = std::min<int64_t>(batch, std::min<int64_t>(n, (int64_t(1) << 31) / (kc + 1) - 1));
   cudaStream_t st = as_stream(stream);
   gbk_status r;
   if ((r = finalize(ix, st)) != GBK_OK) return r;
-  const int kk = k + 1;
-  Scratch D1, I1, kq, off;
+  Scratch D1, I1, Dc, Ic, kq, off;
   if ((r = D1.alloc(sizeof(float) * (size_t)batch * kk, st)) != GBK_OK) return r;
   if ((r = I1.alloc(sizeof(int64_t) * (size_t)batch * kk, st)) != GBK_OK) return r;
-  if (mlp) {
+  if (kprime > 0) {
+    if ((r = Dc.alloc(sizeof(float) * (size_t)batch * kc, st)) != GBK_OK) return r;
+    if ((r = Ic.alloc(sizeof(int64_t) * (size_t)batch * kc, st)) != GBK_OK) return r;
+  }
+  if (mlp && kprime == 0) {
     if ((r = kq.alloc(sizeof(int32_t) * (size_t)batch, st)) != GBK_OK) return r;
     if ((r = off.alloc(sizeof(int64_t) * (size_t)(batch + 1), st)) != GBK_OK) return r;
     gbk::fill_graph_args_kernel<<<(unsigned)((batch + 256) / 256), 256, 0, st>>>(
@@ -858,11 +864,31 @@ gbk_status gbk_ivfpq_knn_graph(gbk_index* ix, const float* x, int64_t n, const i
   for (int64_t b0 = 0; b0 < n; b0 += batch) {
     const int64_t nb = std::min(batch, n - b0);
     const float* xb = x + b0 * ix->d;
-    if (mlp)
+    if (kprime > 0) {
+      // k' ADC candidates as list positions, exact float32 re-rank from the kept vectors
+      Scratch xr;
+      const float* xbr = xb;
+      if ((r = gbk::rotate_rows(ix, xb, nb, xr, &xbr, st)) != GBK_OK) return r;
+      if (mlp)
+        r = gbk::batched_run(ix, xbr, nb, nullptr, kc, nullptr, nprobe, mlp, nullptr,
+                             Dc.as<float>(), Ic.as<int64_t>(), nullptr, st, true, true);
+      else
+        r = gbk::search_run(ix, xbr, nb, kc, nprobe, Dc.as<float>(), Ic.as<int64_t>(), st, true,
+                            true);
+      if (r != GBK_OK) return r;
+      if ((r = gbk::rerank_rows_run(xbr, ix->vecs.as<float>(), nb, ix->d, kc, kk,
+                                    Ic.as<int64_t>(), D1.as<float>(), I1.as<int64_t>(), st)) !=
+          GBK_OK)
+        return r;
+      if ((r = gbk::rows_to_ids_run(I1.as<int64_t>(), nb * (int64_t)kk, ix->ids.as<int64_t>(),
+                                    st)) != GBK_OK)
+        return r;
+    } else if (mlp) {
       r = gbk::batched_run(ix, xb, nb, kq.as<int32_t>(), kk, nullptr, nprobe, mlp,
                            off.as<int64_t>(), D1.as<float>(), I1.as<int64_t>(), nullptr, st);
-    else
+    } else {
       r = gbk::search_run(ix, xb, nb, kk, nprobe, D1.as<float>(), I1.as<int64_t>(), st);
+    }
     if (r != GBK_OK) return r;
     gbk::drop_self_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(
         D1.as<float>(), I1.as<int64_t>(), nb, k, self_ids ? self_ids + b0 : nullptr, b0,
@@ -870,6 +896,22 @@ gbk_status gbk_ivfpq_knn_graph(gbk_index* ix, const float* x, int64_t n, const i
     GBK_LAUNCH_CHECK();
   }
   return GBK_OK;
+}
+
+gbk_status gbk_ivfpq_knn_graph(gbk_index* ix, const float* x, int64_t n, const int64_t* self_ids,
+                               int32_t k, int32_t nprobe, gbk_mlp* mlp, int64_t batch,
+                               float* GD, int64_t* G, void* stream) {
+  clear_error();
+  return knn_graph_run(ix, x, n, self_ids, k, nprobe, 0, mlp, batch, GD, G, stream);
+}
+
+gbk_status gbk_ivfpq_knn_graph_refine(gbk_index* ix, const float* x, int64_t n,
+                                      const int64_t* self_ids, int32_t k, int32_t nprobe,
+                                      int32_t kprime, gbk_mlp* mlp, int64_t batch, float* GD,
+                                      int64_t* G, void* stream) {
+  clear_error();
+  GBK_REQUIRE(kprime >= 1, "gbk_ivfpq_knn_graph_refine: kprime < 1");
+  return knn_graph_run(ix, x, n, self_ids, k, nprobe, kprime, mlp, batch, GD, G, stream);
 }
 
 }  // extern "C"

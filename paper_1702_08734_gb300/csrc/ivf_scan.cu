@@ -155,7 +155,9 @@ __device__ __forceinline__ void rotate_code(uint32_t (&w)[M / 4], int rot) {
 
 template <int M>
 __device__ __forceinline__ void load_code(const uint8_t* codes, int64_t i, uint32_t (&w)[M / 4]) {
-  if constexpr (M == 8) {
+  if constexpr (M == 4) {
+    w[0] = __ldg(reinterpret_cast<const uint32_t*>(codes) + i);
+  } else if constexpr (M == 8) {
     const uint2 v = __ldg(reinterpret_cast<const uint2*>(codes) + i);
     w[0] = v.x;
     w[1] = v.y;
@@ -431,10 +433,11 @@ gbk_status ivf_scan_run(int M, int64_t nq, int nprobe, int k, const int64_t* cl_
              codes, ids, D, I, kq, npq, out_off, order, counter, device_status()};
   if (!a.status) return set_error(GBK_ECUDA, "device status word unavailable");
   ProfScope prof("ivf_scan", st);
+  if (M == 4) return scan_k<4>(a, tun, st);
   if (M == 8) return scan_k<8>(a, tun, st);
   if (M == 16) return scan_k<16>(a, tun, st);
   if (M == 32) return scan_k<32>(a, tun, st);
-  return set_error(GBK_EUNSUPPORTED, "IVFPQ scan supports M in {8, 16, 32}");
+  return set_error(GBK_EUNSUPPORTED, "IVFPQ scan supports M in {4, 8, 16, 32}");
 }
 
 // Work of each query (codes scanned) for longest-first scheduling: key = 31 - log2(work)

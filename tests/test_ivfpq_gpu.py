@@ -77,7 +77,7 @@ def _index_with_oracle_quantizers(gbk, seed, n=20000, d=32, nlist=16, M=8, preco
     return ix, x, coarse, books
 
 
-@pytest.mark.parametrize("M", [8, 16, 32])
+@pytest.mark.parametrize("M", [4, 8, 16, 32])
 def test_encode_and_lists_match_oracle(gbk, M):
     d = 64
     ix, x, coarse, books = _index_with_oracle_quantizers(gbk, 30 + M, d=d, M=M)
@@ -98,7 +98,9 @@ def test_encode_and_lists_match_oracle(gbk, M):
         assert abs(dg - do) <= 1e-5 * max(do, 1e-12), (dg, do)
 
 
-def _check_search(D, I, Do, Io, rtol=1e-4):
+def _check_search(D, I, Do, Io, rtol=1e-4, Do_next=None):
+    """Do_next: the oracle's (k+1)-th distances, so that a near-tie across the k-th place
+    (the list's last entry against the first one left out) is recognised as one."""
     D = D.cpu().numpy().astype(np.float64)
     I = I.cpu().numpy()
     fin = np.isfinite(Do)
@@ -110,6 +112,9 @@ def _check_search(D, I, Do, Io, rtol=1e-4):
     dd = np.abs(np.diff(np.where(fin, Do, 1e30), axis=1))
     gap[:, 1:] = np.minimum(gap[:, 1:], dd)
     gap[:, :-1] = np.minimum(gap[:, :-1], dd)
+    if Do_next is not None:
+        gap[:, -1] = np.minimum(gap[:, -1], np.abs(np.where(np.isfinite(Do_next), Do_next, 1e30)
+                                                   - np.where(fin[:, -1], Do[:, -1], 1e30)))
     sep = fin & (gap > 4 * rtol * np.maximum(np.abs(np.where(fin, Do, 0)), 1e-2))
     assert (I[sep] == Io[sep]).mean() > 0.999
 
@@ -125,6 +130,20 @@ def test_search_matches_oracle(gbk, precomputed, nprobe, k):
     Do, Io = oracle.ivfadc_search(xq, coarse, books, ex["list_off"], ex["codes"], ex["ids"], k,
                                   nprobe)
     _check_search(D, I, Do, Io)
+
+
+@pytest.mark.parametrize("M", [4, 32])
+@pytest.mark.parametrize("nprobe,k", [(2, 10), (8, 100)])
+def test_search_other_code_sizes_match_oracle(gbk, M, nprobe, k):
+    # 4-byte codes (8 LUT copies per warp row) and 32-byte codes against the oracle
+    ix, x, coarse, books = _index_with_oracle_quantizers(gbk, 45 + M, M=M)
+    ex = ix.export()
+    xq, _ = _mixture(45 + M, 300, 32)
+    xq = xq + datagen.gaussian_matrix(46, 300, 32) * 0.1
+    D, I = ix.search(torch.from_numpy(xq).cuda(), k, nprobe)
+    Do, Io = oracle.ivfadc_search(xq, coarse, books, ex["list_off"], ex["codes"], ex["ids"],
+                                  k + 1, nprobe)
+    _check_search(D, I, Do[:, :k], Io[:, :k], Do_next=Do[:, k])
 
 
 def test_full_probe_is_exhaustive_adc_and_padding(gbk):

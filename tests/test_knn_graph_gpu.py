@@ -127,3 +127,32 @@ def test_learned_route_graph(gbk):
                         np.arange(x.shape[0]), k)
     np.testing.assert_array_equal(G.cpu().numpy(), Ig)
     np.testing.assert_array_equal(GD.cpu().numpy(), Dg)
+
+
+def test_refined_graph_equals_per_row_refine(gbk):
+    # the re-ranked graph: each row's k' ADC candidates re-scored exactly from the kept
+    # vectors, then its own id dropped - the rows of search_refine(k + 1) minus self
+    d, nlist, M, seed = 32, 16, 8, 97
+    cen = datagen.mixture_centres(seed, 64, d)
+    x = datagen.mixture_points(cen, seed + 1, 5000)
+    nt = 3000
+    coarse, _, _ = oracle.kmeans(x[:nt], datagen.permutation_prefix(seed + 2, nt, nlist), 6)
+    books = oracle.train_pq(oracle.residual_training_set(x[:nt], coarse), M,
+                            datagen.permutation_prefix(seed + 3, nt, 256), 6)
+    ix = gbk.IVFPQIndex(d, nlist, M).set_quantizers(torch.from_numpy(coarse).cuda(),
+                                                   torch.from_numpy(books).cuda())
+    ix.keep_vectors()
+    xt = torch.from_numpy(x).cuda()
+    ix.add(xt)
+    k, nprobe, kp = 10, 2, 64
+    GD, G = gbk.knn_graph(ix, xt, k, nprobe, batch=1300, kprime=kp)
+    Dr, Ir = ix.search_refine(xt, k + 1, nprobe, kp)
+    Dg, Ig = _drop_self(Dr.cpu().numpy(), Ir.cpu().numpy(), np.arange(x.shape[0]), k)
+    np.testing.assert_array_equal(G.cpu().numpy(), Ig)
+    np.testing.assert_array_equal(GD.cpu().numpy(), Dg)
+    # exact distances of the listed neighbours
+    qi = np.repeat(np.arange(x.shape[0]), k)
+    ex = oracle.pair_dist(x, x, qi, G.cpu().numpy().ravel()).reshape(G.shape)
+    np.testing.assert_allclose(GD.cpu().numpy(), ex, rtol=1e-5, atol=1e-5)
+    with pytest.raises(gbk.GbkError):
+        gbk.knn_graph(ix, xt, k, nprobe, kprime=k)  # kprime must exceed k
