@@ -479,17 +479,19 @@ def run_learned(args):
     gt = np.stack([np.concatenate([r[r != s_], r[r == s_]])[:10] for r, s_ in zip(Ie, sid)])
     gt = torch.from_numpy(gt).cuda()
     graph = {}
-    for name, kw in (("learned", {"mlp": net}), ("fixed_nprobe1", {}),
-                     ("fixed_nprobe1_reranked_kprime32", {"kprime": 32})):
+    for name, tau, kw in (("learned", cap, {"mlp": net}), ("fixed_nprobe1", 1, {}),
+                          ("fixed_nprobe1_reranked_kprime32", 1, {"kprime": 32}),
+                          ("fixed_nprobe4_reranked_kprime128", 4, {"kprime": 128})):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, G = g.knn_graph(ix, xb, 10, cap if "mlp" in kw else 1, distances=False, **kw)
+        _, G = g.knn_graph(ix, xb, 10, tau, distances=False, **kw)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         c = torch.empty(samp.shape[0], dtype=torch.int32, device="cuda")
         g.recall_counts(G[samp].contiguous(), gt, c)
         graph[name] = {"seconds": el, "nodes": int(xb.shape[0]),
                        "R10@10_sampled": float(c.float().mean().item()) / 10}
+
     def qps_at(rows, r):
         """fixed-nprobe q/s at recall r (log-linear interpolation between neighbours)"""
         for a, b in zip(rows, rows[1:]):
