@@ -269,8 +269,10 @@ gbk_status gbk_ivfpq_set_rotation(gbk_index* index, const float* R, void* stream
 gbk_status gbk_ivfpq_rotate(gbk_index* index, const float* x, int64_t n, float* out,
                             void* stream);
 
-/* Keep a float32 copy of every vector added from now on (n*d*4 bytes of device memory, in
- * list order), for gbk_ivfpq_search_refine.  Must be set before the first add. */
+/* Keep a float32 copy of every vector added from now on (n*d*4 bytes of device memory in
+ * list order, plus the same again as staging until the next search rebuilds the lists),
+ * for gbk_ivfpq_search_refine and the re-ranked searches.  keep != 0 must be set before
+ * the first add (EINVAL otherwise); keep = 0 before any add turns it off again. */
 gbk_status gbk_ivfpq_keep_vectors(gbk_index* index, int32_t keep);
 
 /* IVFADC with exact re-ranking: the kprime best ADC candidates of each query (Algorithm 4,
@@ -313,6 +315,7 @@ gbk_status gbk_ivfflat_add(gbk_ivfflat* index, const float* x, int64_t n, const 
 gbk_status gbk_ivfflat_search(gbk_ivfflat* index, const float* xq, int64_t nq, int32_t k,
                               int32_t nprobe, float* D, int64_t* I, void* stream);
 
+/* Sizes of the index (host outputs, any may be NULL; ntotal counts every added vector). */
 gbk_status gbk_ivfflat_info(gbk_ivfflat* index, int64_t* ntotal, int32_t* nlist, int32_t* d,
                             void* stream);
 
