@@ -269,6 +269,14 @@ gbk_status gbk_ivfpq_set_rotation(gbk_index* index, const float* R, void* stream
 gbk_status gbk_ivfpq_rotate(gbk_index* index, const float* x, int64_t n, float* out,
                             void* stream);
 
+/* Arithmetic of the queries' coarse search (Eq. 5) in every search of this index:
+ * GBK_PREC_FP32 (default), or GBK_PREC_BF16 / GBK_PREC_FP8 tensor-core GEMMs that fetch
+ * nprobe + nprobe/4 (4 nprobe for nprobe <= 16) candidate lists and re-rank them by exact
+ * float32 distances, as gbk_knn_brute does (pattern 1): the probed lists are then the
+ * exact nearest ones unless a true one fell outside the over-fetch, and term 2 is exact.
+ * Adding (q1 assignment) always uses float32. */
+gbk_status gbk_ivfpq_set_coarse_precision(gbk_index* index, int32_t precision);
+
 /* Keep a float32 copy of every vector added from now on (n*d*4 bytes of device memory in
  * list order, plus the same again as staging until the next search rebuilds the lists),
  * for gbk_ivfpq_search_refine and the re-ranked searches.  keep != 0 must be set before

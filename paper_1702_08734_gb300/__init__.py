@@ -226,6 +226,7 @@ _SIGNATURES.update({
     "gbk_ivfpq_info": [_vp, _vp, _vp, _vp, _vp, _vp],
     "gbk_ivfpq_export": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "gbk_ivfpq_keep_vectors": [_vp, _i32],
+    "gbk_ivfpq_set_coarse_precision": [_vp, _i32],
     "gbk_ivfpq_set_rotation": [_vp, _vp, _vp],
     "gbk_ivfpq_rotate": [_vp, _vp, _i64, _vp, _vp],
     "gbk_ivfpq_search_refine": [_vp, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp],
@@ -336,6 +337,12 @@ class IVFPQIndex:
         out = torch.empty_like(x)
         _call("gbk_ivfpq_rotate", self._h, _ptr(x), x.shape[0], _ptr(out), _stream())
         return out
+
+    def set_coarse_precision(self, precision="fp32"):
+        """Coarse-search GEMM precision ("fp32", "bf16", "fp8"; low precision re-ranks the
+        over-fetched lists in float32)."""
+        _call("gbk_ivfpq_set_coarse_precision", self._h, PRECISIONS[precision])
+        return self
 
     def keep_vectors(self, keep: bool = True):
         """Keep float32 copies of the vectors added from now on (for search_refine)."""

@@ -46,6 +46,9 @@ struct gbk_index {
   // optional OPQ pre-rotation R [d][d]: every input vector y is replaced by R y
   gbk::DevBuf rot;
   bool rotated = false;
+  // arithmetic of the coarse search of queries (Eq. 5); low precision over-fetches and
+  // re-ranks the candidate lists in float32, so term 2 stays exact
+  int coarse_prec = GBK_PREC_FP32;
   int64_t ntotal = 0;
   bool dirty = true;
   int64_t max_list = 0;
@@ -344,6 +347,16 @@ gbk_status gbk_ivfpq_search(gbk_index* ix, const float* xq, int64_t nq, int32_t 
   return gbk::search_run(ix, xq, nq, k, nprobe, D, I, st);
 }
 
+gbk_status gbk_ivfpq_set_coarse_precision(gbk_index* ix, int32_t precision) {
+  clear_error();
+  GBK_REQUIRE(ix, "gbk_ivfpq_set_coarse_precision: NULL index");
+  GBK_REQUIRE(precision == GBK_PREC_FP32 || precision == GBK_PREC_BF16 ||
+                  precision == GBK_PREC_FP8,
+              "gbk_ivfpq_set_coarse_precision: bad precision");
+  ix->coarse_prec = precision;
+  return GBK_OK;
+}
+
 gbk_status gbk_ivfpq_keep_vectors(gbk_index* ix, int32_t keep) {
   clear_error();
   GBK_REQUIRE(ix, "gbk_ivfpq_keep_vectors: NULL index");
@@ -459,6 +472,7 @@ gbk_status search_run(gbk_index* ix, const float* xq_in, int64_t nq, int k, int 
   if ((r = clI.alloc(sizeof(int64_t) * (size_t)nq * nprobe, st)) != GBK_OK) return r;
   // L_IVF (Eq. 5): the nprobe nearest coarse centroids, with term 2 = ||x - c||^2
   KnnPlan plan;
+  plan.prec = ix->coarse_prec;
   if ((r = knn_run(xq, nq, ix->coarse.as<float>(), ix->nlist, ix->d, nprobe, GBK_METRIC_L2,
                    clD.as<float>(), clI.as<int64_t>(), plan, st)) != GBK_OK)
     return r;
@@ -576,6 +590,7 @@ gbk_status batched_run(gbk_index* ix, const float* xq_in, int64_t nq, const int3
   if ((r = clD.alloc(sizeof(float) * (size_t)nq * tau, st)) != GBK_OK) return r;
   if ((r = clI.alloc(sizeof(int64_t) * (size_t)nq * tau, st)) != GBK_OK) return r;
   KnnPlan plan;
+  plan.prec = ix->coarse_prec;
   // L_IVF (Eq. 5) for the largest nprobe of the batch, with term 2
   if ((r = knn_run(xq, nq, ix->coarse.as<float>(), ix->nlist, ix->d, tau, GBK_METRIC_L2,
                    clD.as<float>(), clI.as<int64_t>(), plan, st)) != GBK_OK)

@@ -191,3 +191,29 @@ def test_errors(gbk):
     ix = gbk.IVFPQIndex(32, 8, 8)
     with pytest.raises(gbk.GbkError):
         ix.search(torch.zeros((2, 32), device="cuda"), 5, 2)  # not trained
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_low_precision_coarse_search(gbk, prec):
+    # pattern 1 on the coarse quantizer: low-precision GEMM, over-fetched lists re-ranked in
+    # float32 - the probed lists and term 2 equal the float32 search's for nearly every
+    # query, so the results do too; batched and plain searches agree with each other
+    ix, x, coarse, books = _index_with_oracle_quantizers(gbk, 70, nlist=64)
+    xq, _ = _mixture(70, 400, 32)
+    xqt = torch.from_numpy(xq + datagen.gaussian_matrix(71, 400, 32) * 0.1).cuda()
+    D32, I32 = ix.search(xqt, 20, 8)
+    ix.set_coarse_precision(prec)
+    D, I = ix.search(xqt, 20, 8)
+    same = (I == I32).all(dim=1).float().mean().item()
+    assert same > 0.97, same
+    # term 2 comes from the exact re-rank (sum of squared differences) instead of Eq. 2's
+    # norm expansion: the distances differ by float32 rounding of the latter
+    agree = torch.isclose(D, D32, rtol=1e-4, atol=1e-3).all(dim=1)
+    assert agree.float().mean().item() > 0.97
+    kq = torch.full((400,), 20, dtype=torch.int32, device="cuda")
+    npq = torch.full((400,), 8, dtype=torch.int32, device="cuda")
+    Db, Ib, _, _ = gbk.ivfpq_search_batched(ix, xqt, kq, 20, npq, 8)
+    assert torch.equal(Ib.view(400, 20), I) and torch.equal(Db.view(400, 20), D)
+    ix.set_coarse_precision("fp32")
+    D2, I2 = ix.search(xqt, 20, 8)
+    assert torch.equal(I2, I32) and torch.equal(D2, D32)
