@@ -576,7 +576,7 @@ def run_batched(args):
         ix.set_coarse_precision(prec)
         graphs[prec] = g.BatchedGraph(ix, xq, kq, 100, npq, 128)
         times[prec], _ = time_search(g, graphs[prec].launch, args.steps)
-    gr, ms = graphs["fp8"], times["fp8"]
+    gr, ms = graphs["fp32"], times["fp32"]  # the faster form at this shape (both reported)
     by = {}
     # recall of the first 1,000 queries against exact search over the regenerated chunks
     ns = 1000
@@ -604,17 +604,18 @@ def run_batched(args):
         return {kk: float(np.mean(v)) for kk, v in sorted(rec.items())}
 
     rec = recall_of(gr)
-    rec32 = recall_of(graphs["fp32"])
+    rec8 = recall_of(graphs["fp8"])
     print(json.dumps({
         "workload": "batched mixed IVFPQ nb=%d d=96 nlist=%d M=16 nq=%d, k in {1,10,100}, nprobe in {8,32,128}" % (n, nlist, nq),
         "metric": "queries/s of one graph-captured mixed batch", "value": nq / (ms / 1e3),
         "unit": "queries/s", "ms_per_batch": ms, "scan_shape": {"codes_per_thread": shape[0], "blocks_per_sm": shape[1]},
         "autotune_ms": tuned_ms, **t,
         "kernel_ms": {kk: sum(v) / len(v) for kk, v in by.items()},
-        "coarse": "FP8 GEMM, over-fetch + float32 re-rank of the candidate lists",
+        "coarse": "float32 (TF32x3) GEMM",
         "recall_at_k_sampled": rec,
-        "fp32_coarse": {"value": nq / (times["fp32"] / 1e3), "ms_per_batch": times["fp32"],
-                        "recall_at_k_sampled": rec32},
+        "fp8_coarse": {"what": "FP8 GEMM, over-fetch + float32 re-rank of the candidate lists",
+                       "value": nq / (times["fp8"] / 1e3), "ms_per_batch": times["fp8"],
+                       "recall_at_k_sampled": rec8},
         "sample": "first %d queries, exact top-100 over all %d vectors" % (ns, n)}), flush=True)
 
 
