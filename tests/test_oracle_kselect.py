@@ -141,3 +141,27 @@ def test_pair_dist_matches_knn():
     qi = np.repeat(np.arange(5), 4)
     pd = oracle.pair_dist(xq, xb, qi, I.ravel())
     np.testing.assert_array_equal(pd, D.ravel())
+
+
+def test_event_distribution_matches_appendix_recurrence():
+    # Brute force over every permutation of l distinct keys: the distribution of the number
+    # of successive min-k elements the oracle's single scan meets equals gamma(l, m, k) of
+    # the Appendix recurrence (tests/golden/appendix_min_k_distribution.txt, exact fractions)
+    import itertools
+    import math
+    import os
+    from fractions import Fraction
+    path = os.path.join(os.path.dirname(__file__), "golden", "appendix_min_k_distribution.txt")
+    want = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        l, k, m, num, den = map(int, line.split())
+        want.setdefault((l, k), {})[m] = Fraction(num, den)
+    assert len(want) == sum(min(3, l) for l in range(1, 8))
+    for (l, k), dist in want.items():
+        perms = np.array(list(itertools.permutations(range(l))), dtype=np.float32)
+        _, _, ev = oracle.kselect(perms, k, return_events=True)
+        vals, cnt = np.unique(ev, return_counts=True)
+        got = {int(m): Fraction(int(c), math.factorial(l)) for m, c in zip(vals, cnt)}
+        assert got == dist, (l, k, got, dist)
