@@ -47,3 +47,30 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.gbk_kselect(None, 0, 10, 3, 0, None, None, None) == 0
     lib.gbk_version.restype = ctypes.c_int32
     assert lib.gbk_version() >= 100
+
+
+def test_index_argument_errors_need_no_gpu(lib):
+    # index creation and option setters are host-side: their argument checks run anywhere
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    for name, args in (("gbk_ivfpq_create", [i32, i32, i32, i32, i32, vp]),
+                       ("gbk_ivfflat_create", [i32, i32, i32, vp]),
+                       ("gbk_ivfpq_set_coarse_precision", [vp, i32]),
+                       ("gbk_ivfpq_keep_vectors", [vp, i32])):
+        getattr(lib, name).restype = i32
+        getattr(lib, name).argtypes = args
+    lib.gbk_ivfpq_destroy.argtypes = [vp]
+    lib.gbk_ivfflat_destroy.argtypes = [vp]
+    h = ctypes.c_void_p()
+    assert lib.gbk_ivfpq_create(30, 16, 8, 8, 0, ctypes.byref(h)) == 1   # M does not divide d
+    assert lib.gbk_ivfpq_create(36, 16, 12, 8, 0, ctypes.byref(h)) == 5  # M = 12 unsupported
+    assert lib.gbk_ivfpq_create(32, 16, 8, 8, 1, ctypes.byref(h)) == 5   # inner product
+    assert lib.gbk_ivfpq_create(32, 16, 4, 8, 0, ctypes.byref(h)) == 0   # 4-byte codes
+    assert lib.gbk_ivfpq_set_coarse_precision(h, 7) == 1
+    assert lib.gbk_ivfpq_set_coarse_precision(h, 2) == 0
+    assert lib.gbk_ivfpq_keep_vectors(h, 1) == 0
+    lib.gbk_ivfpq_destroy(h)
+    f = ctypes.c_void_p()
+    assert lib.gbk_ivfflat_create(16, 4, 1, ctypes.byref(f)) == 5        # L2 only
+    assert lib.gbk_ivfflat_create(0, 4, 0, ctypes.byref(f)) == 1
+    assert lib.gbk_ivfflat_create(16, 4, 0, ctypes.byref(f)) == 0
+    lib.gbk_ivfflat_destroy(f)
