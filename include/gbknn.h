@@ -255,6 +255,19 @@ gbk_status gbk_ivfpq_info(gbk_index* index, int64_t* ntotal, int32_t* nlist, int
 gbk_status gbk_ivfpq_export(gbk_index* index, float* coarse, float* pq, int64_t* list_off,
                             uint8_t* codes, int64_t* ids, void* stream);
 
+/* Checkpoint of an index to a file and back (section 2's inverted file with its
+ * quantizers; the paper does not specify a format).  gbk_ivfpq_save writes a header
+ * (sizes, table mode, coarse precision, kept vectors, rotation, scan tuning) followed by
+ * the coarse centroids, the codebooks, the rotation, the list offsets, the codes (byte m =
+ * sub-quantizer m), the ids and the kept vectors, all in list order; it synchronises
+ * `stream`.  gbk_ivfpq_load reads such a file into a new index (*out; destroy with
+ * gbk_ivfpq_destroy) and rebuilds the term-1 tables and everything derived from them with
+ * the same kernels, so searches of the loaded index return exactly what the saved index
+ * returned; vectors may be added to it afterwards.  Errors: GBK_EINVAL (untrained index,
+ * unreadable, truncated or inconsistent file), GBK_ENOMEM, GBK_ECUDA. */
+gbk_status gbk_ivfpq_save(gbk_index* index, const char* path, void* stream);
+gbk_status gbk_ivfpq_load(const char* path, gbk_index** out, void* stream);
+
 /* OPQ pre-rotation (the optimized product quantization used by the paper's DEEP1B and
  * YFCC100M experiments, sections 1 and 6.4): with R [d][d] row-major (device or host
  * float32, typically orthogonal) every vector given to train, add, the searches and the
@@ -347,6 +360,12 @@ typedef struct gbk_mlp gbk_mlp;
 gbk_status gbk_mlp_create(int32_t n_in, int32_t h1, int32_t h2, int32_t n_out,
                           const float* init_params, gbk_mlp** out);
 void gbk_mlp_destroy(gbk_mlp* net);
+
+/* Seeded initialisation of the master parameters: each drawn from U(-1/sqrt(fan_in),
+ * 1/sqrt(fan_in)) of its layer (W1, b1: n_in; W2, b2: h1; W3, b3: h2) by the 24 high bits
+ * of a SplitMix64 hash of (seed, parameter index); Adam moments and step count reset.
+ * The same seed gives the same parameters on every device. */
+gbk_status gbk_mlp_init_uniform(gbk_mlp* net, uint64_t seed, void* stream);
 int64_t gbk_mlp_num_params(const gbk_mlp* net);
 
 /* Copy the master parameters and/or the gradients of the last train step (host or device
@@ -363,6 +382,51 @@ gbk_status gbk_mlp_forward(gbk_mlp* net, const float* X, int64_t B, float* logit
  * optional device float receiving the batch loss. */
 gbk_status gbk_mlp_train_step(gbk_mlp* net, const float* X, const int32_t* labels, int64_t B,
                               float lr, int32_t update, float* loss, void* stream);
+
+/* Training of the per-query nprobe network inside the library (not part of the paper; it
+ * chooses the nprobe of Eq. (5) per query).  Classes c = 0 .. n_classes-1 probe
+ * tau_c = min(2^c, nlist) lists.  Label of a training query: with r_c its k-recall@k at
+ * tau_c (|ADC top-k intersect exact top-k|), the smallest c with
+ * r_c >= min(ceil(target * k), r_{n_classes-1}) - the fewest lists reaching the target, or
+ * the query's own ceiling where no tau reaches it.  Zero fields select the defaults. */
+typedef struct gbk_nprobe_train_opts {
+  int32_t n_classes; /* 1..11 (default 9: nprobe 1..256)                                  */
+  int32_t k;         /* neighbours judged (default 10)                                    */
+  float target;      /* recall target in (0, 1] (default 0.95)                            */
+  int32_t kprime;    /* 0: labels from the ADC search; > k: from kprime ADC candidates    */
+                     /* re-ranked by exact distances (gbk_ivfpq_search_refine; the index  */
+                     /* must keep its vectors)                                            */
+  int32_t epochs;    /* passes over the training set (default 15)                         */
+  int32_t batch;     /* samples per Adam step (default 4096); the last partial batch of   */
+                     /* an epoch is left out                                              */
+  float lr;          /* Adam learning rate (default 1e-3)                                 */
+  uint64_t seed;     /* sample order: epoch e visits a Fisher-Yates permutation drawn     */
+                     /* from a SplitMix64 hash of (seed, e, i)                            */
+  int64_t chunk;     /* training queries searched per batch (default 20,000)              */
+} gbk_nprobe_train_opts;
+
+/* Labels [n] (device int32) of the training queries xq [n][d] (device) and, optionally,
+ * their recall counts counts [n_classes][n] (device int32, may be NULL).  gt [n][kgt]
+ * (device int64, kgt >= k): the exact nearest ids of each query (e.g. gbk_knn_brute over
+ * the database); NULL computes them inside from the index's kept vectors
+ * (gbk_ivfpq_keep_vectors).  Errors: GBK_EINVAL (options, sizes, neither gt nor kept
+ * vectors), GBK_ENOMEM, GBK_ECUDA. */
+gbk_status gbk_nprobe_labels(gbk_index* index, const float* xq, int64_t n, const int64_t* gt,
+                             int32_t kgt, const gbk_nprobe_train_opts* opts, int32_t* labels,
+                             int32_t* counts, void* stream);
+
+/* Trains `net` (d + 64 inputs, n_classes outputs; its current parameters are the starting
+ * point, e.g. from gbk_mlp_init_uniform) on the training queries xq [n][d]: features as
+ * in gbk_ivfpq_search_batched (the query and its 64 nearest coarse distances), labels
+ * given (labels [n] device int32) or, with labels NULL, built as by gbk_nprobe_labels
+ * from gt / the kept vectors; then `epochs` passes of Adam over seeded permutations of the
+ * samples with the library's own forward, backward and update kernels.  epoch_loss (host,
+ * may be NULL): [epochs] mean batch loss of each epoch (the call then synchronises
+ * `stream`).  Needs nlist >= 64 and batch <= n.  Errors as gbk_nprobe_labels. */
+gbk_status gbk_nprobe_mlp_train(gbk_index* index, gbk_mlp* net, const float* xq, int64_t n,
+                                const int32_t* labels, const int64_t* gt, int32_t kgt,
+                                const gbk_nprobe_train_opts* opts, float* epoch_loss,
+                                void* stream);
 
 /* ------------------------------------------------------------------ batched serving */
 
@@ -444,18 +508,30 @@ gbk_status gbk_merge_topk(const float* D_parts, const int64_t* I_parts, int32_t 
 /* ------------------------------------------------------------------ scan autotuning */
 
 /* Launch shape of the list scan (results never depend on it): codes each thread loads per
- * step (2, 4 or 8; default 4) and resident blocks per SM in the persistent mixed-batch mode
+ * step (2, 4 or 8; default 2) and resident blocks per SM in the persistent mixed-batch mode
  * (1..8; default 2).  GBK_EINVAL outside those sets. */
 gbk_status gbk_ivfpq_set_tuning(gbk_index* index, int32_t codes_per_thread,
                                 int32_t blocks_per_sm);
 gbk_status gbk_ivfpq_get_tuning(const gbk_index* index, int32_t* codes_per_thread,
                                 int32_t* blocks_per_sm);
 
-/* Times gbk_ivfpq_search_batched on this batch (arguments as there) for every codes per
- * thread in {2, 4, 8} x blocks per SM in {1..4}: one untimed run, then `reps` (< 1: 3) runs
- * timed with CUDA events on `stream`, and keeps the fastest shape in the index.  D and I
- * hold the batch's results afterwards.  Synchronises `stream`.  *best_ms (host, may be
- * NULL): mean milliseconds per batch of the chosen shape.  Not part of the paper. */
+/* Further scan options (results never depend on them; not part of the paper):
+ * threads_per_block of the precomputed-table scan, 256, 384 (default; applies with 2 or 4
+ * codes per thread) or 512 (with 2 codes per thread); by_list != 0 (default) makes gbk_ivfpq_search hand queries to
+ * the scan in the order of their nearest inverted list, so that queries probing the same
+ * lists are scanned at the same time and share those lists' codes in L2 (section 5.3 reads
+ * each probed list once per query), 0 scans them in input order, one block per query.
+ * GBK_EINVAL for another block size. */
+gbk_status gbk_ivfpq_set_scan_options(gbk_index* index, int32_t threads_per_block,
+                                      int32_t by_list);
+
+/* Times gbk_ivfpq_search_batched on this batch (arguments as there) for every scan shape -
+ * block size x codes per thread in {256 x 2, 256 x 4, 256 x 8, 384 x 2, 384 x 4, 512 x 2}
+ * (the direct-table scan: the 256-thread ones) x resident blocks per SM in {1, 2} - one
+ * untimed run, then `reps` (< 1: 3) runs timed with CUDA events on `stream`, and keeps the
+ * fastest shape in the index (gbk_ivfpq_get_tuning / the block size in gbk_ivfpq_save).
+ * D and I hold the batch's results afterwards.  Synchronises `stream`.  *best_ms (host,
+ * may be NULL): mean milliseconds per batch of the chosen shape.  Not part of the paper. */
 gbk_status gbk_ivfpq_autotune(gbk_index* index, const float* xq, int64_t nq,
                               const int32_t* k_per_q, int32_t max_k,
                               const int32_t* nprobe_per_q, int32_t max_nprobe, gbk_mlp* mlp,

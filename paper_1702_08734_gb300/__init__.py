@@ -368,6 +368,25 @@ class IVFPQIndex:
         _call("gbk_ivfpq_info", self._h, ctypes.byref(n), None, None, None, _stream())
         return n.value
 
+    def save(self, path: str):
+        """Write the index to a file (gbk_ivfpq_save)."""
+        _call("gbk_ivfpq_save", self._h, os.fsencode(path), _stream())
+        return self
+
+    @classmethod
+    def load(cls, path: str):
+        """A new index read from a file written by save()."""
+        h = ctypes.c_void_p()
+        _call("gbk_ivfpq_load", os.fsencode(path), ctypes.byref(h), _stream())
+        ix = cls.__new__(cls)
+        ix._h = h
+        n = ctypes.c_int64()
+        nl, d, M = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _call("gbk_ivfpq_info", h, ctypes.byref(n), ctypes.byref(nl), ctypes.byref(d),
+              ctypes.byref(M), _stream())
+        ix.d, ix.nlist, ix.M = d.value, nl.value, M.value
+        return ix
+
     def export(self):
         """Host copies: coarse [nlist][d], pq [M][256][d/M], list_off, codes, ids."""
         import numpy as np
@@ -465,7 +484,7 @@ class MLP:
     """f -> relu(W1 f + b1) -> relu(W2 . + b2) -> W3 . + b3, trained on the GPU (BF16 weights
     in the passes, float32 master copy and accumulation, Adam)."""
 
-    def __init__(self, n_in, h1, h2, n_out, params=None):
+    def __init__(self, n_in, h1, h2, n_out, params=None, seed=None):
         lib = load()
         lib.gbk_mlp_num_params.argtypes = [_vp]
         lib.gbk_mlp_num_params.restype = ctypes.c_int64
@@ -479,6 +498,15 @@ class MLP:
         _call("gbk_mlp_create", *self.sizes, _ptr(p) if p is not None else None, ctypes.byref(h))
         self._h = h
         self.nparam = int(lib.gbk_mlp_num_params(h))
+        if seed is not None:
+            if params is not None:
+                raise ValueError("give params or seed, not both")
+            self.init_uniform(seed)
+
+    def init_uniform(self, seed: int):
+        """U(-1/sqrt(fan_in), 1/sqrt(fan_in)) parameters from a seeded hash (library kernel)."""
+        _call("gbk_mlp_init_uniform", self._h, ctypes.c_uint64(int(seed)), _stream())
+        return self
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -513,7 +541,60 @@ class MLP:
         return loss
 
 
+class NprobeTrainOpts(ctypes.Structure):
+    _fields_ = [("n_classes", ctypes.c_int32), ("k", ctypes.c_int32), ("target", ctypes.c_float),
+                ("kprime", ctypes.c_int32), ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("lr", ctypes.c_float), ("seed", ctypes.c_uint64), ("chunk", ctypes.c_int64)]
+
+
+def _nprobe_opts(n_classes=9, k=10, target=0.95, kprime=0, epochs=15, batch=4096, lr=1e-3,
+                 seed=0, chunk=20000):
+    return NprobeTrainOpts(int(n_classes), int(k), float(target), int(kprime), int(epochs),
+                           int(batch), float(lr), int(seed), int(chunk))
+
+
+def nprobe_labels(index, xq, gt=None, counts=False, **opts):
+    """Labels of training queries for the nprobe network (smallest class reaching the recall
+    target), from exact neighbours gt [n][>=k] or the index's kept vectors.  Returns labels
+    [n] int32 (and the recall counts [n_classes][n] with counts=True)."""
+    _dev(xq, torch.float32, "xq")
+    o = _nprobe_opts(**opts)
+    n = xq.shape[0]
+    lab = torch.empty(n, dtype=torch.int32, device=xq.device)
+    cnt = torch.empty((o.n_classes, n), dtype=torch.int32, device=xq.device) if counts else None
+    kgt = 0
+    if gt is not None:
+        _dev(gt, torch.int64, "gt")
+        kgt = gt.shape[1]
+    _call("gbk_nprobe_labels", index._h, _ptr(xq), n, _ptr(gt), int(kgt), ctypes.byref(o),
+          _ptr(lab), _ptr(cnt), _stream())
+    return (lab, cnt) if counts else lab
+
+
+def nprobe_mlp_train(index, net, xq, labels=None, gt=None, **opts):
+    """Trains net on the training queries xq inside the library (features, labels if not
+    given, seeded epochs of Adam).  Returns the mean batch loss of each epoch."""
+    import numpy as np
+    _dev(xq, torch.float32, "xq")
+    if labels is not None:
+        _dev(labels, torch.int32, "labels")
+    kgt = 0
+    if gt is not None:
+        _dev(gt, torch.int64, "gt")
+        kgt = gt.shape[1]
+    o = _nprobe_opts(n_classes=net.sizes[3], **opts)
+    loss = np.zeros(o.epochs, np.float32)
+    _call("gbk_nprobe_mlp_train", index._h, net._h, _ptr(xq), xq.shape[0], _ptr(labels),
+          _ptr(gt), int(kgt), ctypes.byref(o), loss.ctypes.data_as(_vp), _stream())
+    return loss
+
+
 _SIGNATURES.update({
+    "gbk_mlp_init_uniform": [_vp, ctypes.c_uint64, _vp],
+    "gbk_ivfpq_save": [_vp, ctypes.c_char_p, _vp],
+    "gbk_ivfpq_load": [ctypes.c_char_p, _vp, _vp],
+    "gbk_nprobe_labels": [_vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp, _vp],
+    "gbk_nprobe_mlp_train": [_vp, _vp, _vp, _i64, _vp, _vp, _i32, _vp, _vp, _vp],
     "gbk_recall_counts": [_vp, _vp, _i64, _i32, _i32, _vp, _vp],
     "gbk_nprobe_features": [_vp, _i64, _i32, _vp, _i32, _i32, _vp, _vp],
     "gbk_ivfpq_search_batched": [_vp, _vp, _i64, _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp,
@@ -529,6 +610,7 @@ _SIGNATURES.update({
     "gbk_merge_topk": [_vp, _vp, _i32, _i64, _i32, _i32, _i32, _vp, _vp, _vp],
     "gbk_ivfpq_set_tuning": [_vp, _i32, _i32],
     "gbk_ivfpq_get_tuning": [_vp, _vp, _vp],
+    "gbk_ivfpq_set_scan_options": [_vp, _i32, _i32],
     "gbk_ivfpq_autotune": [_vp, _vp, _i64, _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _i32, _vp,
                            _vp],
 })
@@ -548,6 +630,12 @@ def merge_topk(D_parts: torch.Tensor, I_parts: torch.Tensor, k: int, largest: bo
 
 def ivfpq_set_tuning(index, codes_per_thread: int, blocks_per_sm: int):
     _call("gbk_ivfpq_set_tuning", index._h, int(codes_per_thread), int(blocks_per_sm))
+
+
+def ivfpq_set_scan_options(index, threads: int = 256, by_list: bool = True):
+    """Table-mode scan block size (256 or 512) and whether a plain search scans its queries
+    in the order of their nearest list (True) or as given."""
+    _call("gbk_ivfpq_set_scan_options", index._h, int(threads), int(bool(by_list)))
 
 
 def ivfpq_get_tuning(index):

@@ -3,7 +3,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -78,6 +80,23 @@ const DeviceInfo& device_info() {
     cache.smem_optin = pr.sharedMemPerBlockOptin;
   }
   return cache;
+}
+
+gbk_status set_smem_limit(const void* kern, size_t bytes, bool max_carveout) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;  // (kernel, device) -> limit set
+  int dev = 0;
+  GBK_CUDA_CHECK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find({kern, dev});
+  if (it != done.end() && it->second >= bytes) return GBK_OK;
+  GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)bytes));
+  if (max_carveout)
+    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared));
+  done[{kern, dev}] = bytes;
+  return GBK_OK;
 }
 
 namespace {

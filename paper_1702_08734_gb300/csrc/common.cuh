@@ -29,6 +29,15 @@ const DeviceInfo& device_info();
 // gave up).  Allocated and zeroed on first use for the current device.
 uint32_t* device_status();
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current device (and, with
+// max_carveout, prefer the largest shared-memory carveout).  Done once per (kernel, device)
+// and per larger request; safe to call from several host threads.
+gbk_status set_smem_limit(const void* kern, size_t bytes, bool max_carveout = false);
+template <class F>
+inline gbk_status set_smem_limit(F* kern, size_t bytes, bool max_carveout = false) {
+  return set_smem_limit(reinterpret_cast<const void*>(kern), bytes, max_carveout);
+}
+
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // Optional per-kernel timing (gbk_profile_*): when enabled, a scope records a CUDA event
@@ -78,6 +87,12 @@ struct Scratch {
     if (e_ != cudaSuccess)                                                                   \
       return ::gbk::set_error(GBK_ECUDA, "%s:%d launch: %s", __FILE__, __LINE__,            \
                               cudaGetErrorString(e_));                                       \
+  } while (0)
+
+#define GBK_TRY(expr)                                                                        \
+  do {                                                                                       \
+    const gbk_status s_ = (expr);                                                            \
+    if (s_ != GBK_OK) return s_;                                                             \
   } while (0)
 
 #define GBK_REQUIRE(cond, ...)                                                               \

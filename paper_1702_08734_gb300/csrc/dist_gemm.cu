@@ -164,12 +164,7 @@ gbk_status launch_knn_merge(const uint64_t* part, int64_t nq, int chunks, int kp
                             cudaStream_t st) {
   using Sel = BlockSelect<256, KP, 4096>;
   auto kern = knn_merge_kernel<KP>;
-  static bool attr = false;
-  if (!attr) {
-    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)sizeof(typename Sel::Smem)));
-    attr = true;
-  }
+  GBK_TRY(set_smem_limit(kern, sizeof(typename Sel::Smem)));
   kern<<<(unsigned)nq, 256, sizeof(typename Sel::Smem), st>>>(part, chunks, kp, k, xnorm,
                                                               largest, D, I);
   GBK_LAUNCH_CHECK();
@@ -267,12 +262,7 @@ gbk_status launch_merge_parts(const float* Dp, const int64_t* Ip, int nparts, in
                               int k, bool largest, float* D, int64_t* I, cudaStream_t st) {
   using Sel = BlockSelect<256, KP, 4096>;
   auto kern = merge_parts_kernel<KP>;
-  static bool attr = false;
-  if (!attr) {
-    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)sizeof(typename Sel::Smem)));
-    attr = true;
-  }
+  GBK_TRY(set_smem_limit(kern, sizeof(typename Sel::Smem)));
   kern<<<(unsigned)nq, 256, sizeof(typename Sel::Smem), st>>>(Dp, Ip, nparts, nq, kin, k,
                                                               largest ? 1 : 0, D, I);
   GBK_LAUNCH_CHECK();

@@ -2,17 +2,19 @@
 // q1 trained by k-means, product quantizer q2 on the residuals, inverted lists stored as
 // two arrays (codes, ids), and the batch search of Algorithm 4.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
 #include "common.cuh"
 #include "ivf.cuh"
+#include "ivf_index.cuh"
 #include "knn.cuh"
 
 namespace gbk {
 
 gbk_status ivf_scan_run(int M, int64_t nq, int nprobe, int k, const int64_t* cl_I,
-                        const float* cl_D, const float* T, const float* t3, const float* xq,
+                        const float* cl_D, const float* s1, const float* t3, const float* xq,
                         const float* coarse, const float* pq, int d, bool direct,
                         const int64_t* list_off, const uint8_t* codes, const int64_t* ids,
                         float* D, int64_t* I, cudaStream_t st, const int32_t* kq = nullptr,
@@ -27,59 +29,6 @@ gbk_status term1_run(const float* coarse, const float* pq, int nlist, int d, int
                      cudaStream_t st);
 gbk_status term3_run(const float* xq, int64_t nq, const float* pq, int d, int M, float* t3,
                      cudaStream_t st);
-
-}  // namespace gbk
-
-struct gbk_index {
-  int d = 0, nlist = 0, M = 0, dsub = 0;
-  bool trained = false;
-  int use_precomputed = 1;
-  gbk::DevBuf coarse, pq, T;
-  // insertion-order staging: every added vector's list, code and id
-  gbk::DevBuf st_list, st_codes, st_ids;
-  int64_t n_staged = 0, cap_staged = 0;
-  // inverted file (built from the staging arrays on demand)
-  gbk::DevBuf list_off, codes, ids;
-  // optional float32 copies of the added vectors (exact re-rank): staged, then list order
-  bool keep_vectors = false;
-  gbk::DevBuf st_vecs, vecs;
-  // optional OPQ pre-rotation R [d][d]: every input vector y is replaced by R y
-  gbk::DevBuf rot;
-  bool rotated = false;
-  // arithmetic of the coarse search of queries (Eq. 5); low precision over-fetches and
-  // re-ranks the candidate lists in float32, so term 2 stays exact
-  int coarse_prec = GBK_PREC_FP32;
-  int64_t ntotal = 0;
-  bool dirty = true;
-  int64_t max_list = 0;
-  gbk::ScanTuning tuning;  // list-scan launch shape (gbk_ivfpq_autotune / set_tuning)
-  ~gbk_index() {
-    coarse.release();
-    pq.release();
-    T.release();
-    st_list.release();
-    st_codes.release();
-    st_ids.release();
-    list_off.release();
-    codes.release();
-    ids.release();
-    st_vecs.release();
-    vecs.release();
-    rot.release();
-  }
-};
-
-namespace gbk {
-
-// Algorithm 4 for a validated, finalized index (below).
-gbk_status search_run(gbk_index* ix, const float* xq, int64_t nq, int k, int nprobe, float* D,
-                      int64_t* I, cudaStream_t st, bool positions = false,
-                      bool prerotated = false);
-
-// Rows of x replaced by R y (the OPQ pre-rotation) as the inner-product GEMM x R^T on the
-// tensor cores (float32-accurate), in chunks of 2^20 rows; without a rotation *out = x.
-gbk_status rotate_rows(const gbk_index* ix, const float* x, int64_t n, Scratch& buf,
-                       const float** out, cudaStream_t st);
 
 namespace {
 
@@ -108,21 +57,47 @@ __global__ void stage_ids_kernel(const int64_t* __restrict__ ids, int64_t n, int
     dst[i] = ids ? ids[i] : first + i;
 }
 
-// codes/ids in list order: out[j] = in[order[j]]
+// codes/ids in list order: position j takes staged vector order[j]; its code is stored
+// rotated by r = (j - start of its list) mod M (byte s = sub-quantizer (s + r) mod M, the
+// layout the scan's conflict-free look-ups need) and, with the term-1 table T [nlist][256][M]
+// given, s1[j] = sum_m T[L][code_m][m] is formed in sub-quantizer order.
 __global__ void gather_codes_kernel(const uint8_t* __restrict__ in, const int64_t* __restrict__ order,
-                                    int64_t n, int M, uint8_t* __restrict__ out,
-                                    const int64_t* __restrict__ ids_in, int64_t* __restrict__ ids_out) {
+                                    int64_t n, int M, const int32_t* __restrict__ st_list,
+                                    const int64_t* __restrict__ list_off,
+                                    const float* __restrict__ T, uint8_t* __restrict__ out,
+                                    float* __restrict__ s1, const int64_t* __restrict__ ids_in,
+                                    int64_t* __restrict__ ids_out) {
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     const int64_t src = order[j];
-    if ((M & 15) == 0) {
-      const uint4* s4 = reinterpret_cast<const uint4*>(in + src * M);
-      uint4* d4 = reinterpret_cast<uint4*>(out + j * M);
-      for (int w = 0; w < M / 16; w++) d4[w] = s4[w];
-    } else {
-      for (int m = 0; m < M; m++) out[j * M + m] = in[src * M + m];
+    const int64_t L = st_list[src];
+    const int r = (int)((j - list_off[L]) % M);
+    const uint8_t* c = in + src * M;
+    for (int m = 0; m < M; m++) out[j * M + m] = c[(m + r) % M];
+    if (T) {
+      const float* TL = T + L * 256 * M;
+      float acc = 0.f;
+      for (int m = 0; m < M; m++) acc += TL[(int)c[m] * M + m];
+      s1[j] = acc;
     }
     ids_out[j] = ids_in[src];
+  }
+}
+
+// Inverse of the rotation above: out[j] = the code of position j in sub-quantizer order.
+__global__ void unrotate_codes_kernel(const uint8_t* __restrict__ in, int64_t n, int M, int nlist,
+                                      const int64_t* __restrict__ list_off,
+                                      uint8_t* __restrict__ out) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nlist;  // list of position j: the last L with list_off[L] <= j
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) / 2;
+      if (list_off[mid] <= j) lo = mid;
+      else hi = mid;
+    }
+    const int r = (int)((j - list_off[lo]) % M);
+    for (int m = 0; m < M; m++) out[j * M + (m + r) % M] = in[j * M + m];
   }
 }
 
@@ -131,7 +106,9 @@ int grid_for(int64_t n) {
                                                      (int64_t)device_info().sm_count * 16));
 }
 
-gbk_status finalize(gbk_index* ix, cudaStream_t st) {
+}  // namespace
+
+gbk_status finalize_index(gbk_index* ix, cudaStream_t st) {
   if (!ix->dirty) return GBK_OK;
   gbk_status r;
   const int64_t n = ix->n_staged;
@@ -143,12 +120,15 @@ gbk_status finalize(gbk_index* ix, cudaStream_t st) {
   if ((r = bucket_stable(ix->st_list.as<int32_t>(), n, ix->nlist, ix->list_off.as<int64_t>(),
                          order.as<int64_t>(), st)) != GBK_OK)
     return r;
+  const bool tables = ix->use_precomputed && ix->T.p;
+  if (tables && (r = ix->s1.alloc(sizeof(float) * (size_t)std::max<int64_t>(n, 1))) != GBK_OK)
+    return r;
   if (n > 0) {
-    gather_codes_kernel<<<grid_for(n), 256, 0, st>>>(ix->st_codes.as<uint8_t>(),
-                                                     order.as<int64_t>(), n, ix->M,
-                                                     ix->codes.as<uint8_t>(),
-                                                     ix->st_ids.as<int64_t>(),
-                                                     ix->ids.as<int64_t>());
+    gather_codes_kernel<<<grid_for(n), 256, 0, st>>>(
+        ix->st_codes.as<uint8_t>(), order.as<int64_t>(), n, ix->M, ix->st_list.as<int32_t>(),
+        ix->list_off.as<int64_t>(), tables ? ix->T.as<float>() : nullptr,
+        ix->codes.as<uint8_t>(), tables ? ix->s1.as<float>() : nullptr,
+        ix->st_ids.as<int64_t>(), ix->ids.as<int64_t>());
     GBK_LAUNCH_CHECK();
   }
   if (ix->keep_vectors) {
@@ -162,8 +142,6 @@ gbk_status finalize(gbk_index* ix, cudaStream_t st) {
   ix->dirty = false;
   return GBK_OK;
 }
-
-}  // namespace
 
 }  // namespace gbk
 
@@ -253,6 +231,7 @@ gbk_status gbk_ivfpq_train(gbk_index* ix, const float* x_in, int64_t n,
       return r;
   }
   ix->trained = true;
+  ix->dirty = true;
   return GBK_OK;
 }
 
@@ -276,6 +255,7 @@ gbk_status gbk_ivfpq_set_quantizers(gbk_index* ix, const float* coarse, const fl
       return r;
   }
   ix->trained = true;
+  ix->dirty = true;
   return GBK_OK;
 }
 
@@ -287,7 +267,8 @@ gbk_status gbk_ivfpq_add(gbk_index* ix, const float* x_in, int64_t n, const int6
   GBK_REQUIRE(n >= 0, "gbk_ivfpq_add: n < 0");
   if (n == 0) return GBK_OK;
   GBK_REQUIRE(x_in, "gbk_ivfpq_add: NULL x");
-  GBK_REQUIRE(ix->n_staged + n < (int64_t(1) << 32) - 1, "gbk_ivfpq_add: index full (2^32)");
+  GBK_REQUIRE(ix->n_staged + n <= (int64_t(1) << 32) - (int64_t(1) << 16),
+              "gbk_ivfpq_add: index full (2^32 - 2^16 vectors)");
   cudaStream_t st = as_stream(stream);
   gbk_status r;
   Scratch xr;
@@ -343,7 +324,7 @@ gbk_status gbk_ivfpq_search(gbk_index* ix, const float* xq, int64_t nq, int32_t 
   GBK_REQUIRE(xq && D && I, "gbk_ivfpq_search: NULL pointer");
   cudaStream_t st = as_stream(stream);
   gbk_status r;
-  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  if ((r = finalize_index(ix, st)) != GBK_OK) return r;
   return gbk::search_run(ix, xq, nq, k, nprobe, D, I, st);
 }
 
@@ -417,7 +398,7 @@ gbk_status gbk_ivfpq_search_refine(gbk_index* ix, const float* xq, int64_t nq, i
   GBK_REQUIRE(xq && D && I, "gbk_ivfpq_search_refine: NULL pointer");
   cudaStream_t st = as_stream(stream);
   gbk_status r;
-  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  if ((r = finalize_index(ix, st)) != GBK_OK) return r;
   Scratch Dc, Ic;
   if ((r = Dc.alloc(sizeof(float) * (size_t)nq * kprime, st)) != GBK_OK) return r;
   if ((r = Ic.alloc(sizeof(int64_t) * (size_t)nq * kprime, st)) != GBK_OK) return r;
@@ -462,6 +443,13 @@ gbk_status rotate_rows(const gbk_index* ix, const float* x, int64_t n, Scratch& 
   return GBK_OK;
 }
 
+// key[q] = the nearest probed list of query q (0 when it has none)
+__global__ void first_list_kernel(const int64_t* __restrict__ cl_I, int64_t nq, int nprobe,
+                                  int32_t* __restrict__ key) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nq) key[q] = (int32_t)max(cl_I[q * nprobe], (int64_t)0);
+}
+
 gbk_status search_run(gbk_index* ix, const float* xq_in, int64_t nq, int k, int nprobe, float* D,
                       int64_t* I, cudaStream_t st, bool positions, bool prerotated) {
   gbk_status r;
@@ -482,11 +470,29 @@ gbk_status search_run(gbk_index* ix, const float* xq_in, int64_t nq, int k, int 
     if ((r = term3_run(xq, nq, ix->pq.as<float>(), ix->d, ix->M, t3.as<float>(), st)) != GBK_OK)
       return r;
   }
-  return ivf_scan_run(ix->M, nq, nprobe, k, clI.as<int64_t>(), clD.as<float>(), ix->T.as<float>(),
+  // queries taken in the order of their nearest list, so that queries probing the same
+  // lists run at the same time and share those lists' codes in L2
+  Scratch key, order, offs, counter;
+  const bool by_list = ix->tuning.list_order && nq > 1;
+  if (by_list) {
+    if ((r = key.alloc(sizeof(int32_t) * (size_t)nq, st)) != GBK_OK) return r;
+    if ((r = order.alloc(sizeof(int64_t) * (size_t)nq, st)) != GBK_OK) return r;
+    if ((r = offs.alloc(sizeof(int64_t) * (size_t)(ix->nlist + 1), st)) != GBK_OK) return r;
+    if ((r = counter.alloc(sizeof(unsigned long long), st)) != GBK_OK) return r;
+    first_list_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(clI.as<int64_t>(), nq, nprobe,
+                                                                     key.as<int32_t>());
+    GBK_LAUNCH_CHECK();
+    if ((r = bucket_stable(key.as<int32_t>(), nq, ix->nlist, offs.as<int64_t>(),
+                           order.as<int64_t>(), st)) != GBK_OK)
+      return r;
+    GBK_CUDA_CHECK(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), st));
+  }
+  return ivf_scan_run(ix->M, nq, nprobe, k, clI.as<int64_t>(), clD.as<float>(), ix->s1.as<float>(),
                       t3.as<float>(), xq, ix->coarse.as<float>(), ix->pq.as<float>(), ix->d,
                       direct, ix->list_off.as<int64_t>(), ix->codes.as<uint8_t>(),
                       positions ? nullptr : ix->ids.as<int64_t>(), D, I, st, nullptr, nullptr,
-                      nullptr, nullptr, nullptr, ix->tuning);
+                      nullptr, by_list ? order.as<int64_t>() : nullptr,
+                      by_list ? counter.as<unsigned long long>() : nullptr, ix->tuning);
 }
 }  // namespace gbk
 extern "C" {
@@ -496,7 +502,7 @@ gbk_status gbk_ivfpq_info(gbk_index* ix, int64_t* ntotal, int32_t* nlist, int32_
   clear_error();
   GBK_REQUIRE(ix, "gbk_ivfpq_info: NULL index");
   gbk_status r;
-  if (ix->trained && (r = finalize(ix, as_stream(stream))) != GBK_OK) return r;
+  if (ix->trained && (r = finalize_index(ix, as_stream(stream))) != GBK_OK) return r;
   if (ntotal) *ntotal = ix->n_staged;
   if (nlist) *nlist = ix->nlist;
   if (d) *d = ix->d;
@@ -510,19 +516,240 @@ gbk_status gbk_ivfpq_export(gbk_index* ix, float* coarse, float* pq, int64_t* li
   GBK_REQUIRE(ix && ix->trained, "gbk_ivfpq_export: index missing or not trained");
   cudaStream_t st = as_stream(stream);
   gbk_status r;
-  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  if ((r = finalize_index(ix, st)) != GBK_OK) return r;
   if (coarse)
     GBK_CUDA_CHECK(cudaMemcpyAsync(coarse, ix->coarse.p, ix->coarse.bytes, cudaMemcpyDefault, st));
   if (pq) GBK_CUDA_CHECK(cudaMemcpyAsync(pq, ix->pq.p, ix->pq.bytes, cudaMemcpyDefault, st));
   if (list_off)
     GBK_CUDA_CHECK(cudaMemcpyAsync(list_off, ix->list_off.p, sizeof(int64_t) * (ix->nlist + 1),
                                    cudaMemcpyDefault, st));
-  if (codes && ix->ntotal)
-    GBK_CUDA_CHECK(cudaMemcpyAsync(codes, ix->codes.p, (size_t)ix->ntotal * ix->M,
-                                   cudaMemcpyDefault, st));
+  if (codes && ix->ntotal) {
+    Scratch plain;
+    if ((r = plain.alloc((size_t)ix->ntotal * ix->M, st)) != GBK_OK) return r;
+    unrotate_codes_kernel<<<grid_for(ix->ntotal), 256, 0, st>>>(
+        ix->codes.as<uint8_t>(), ix->ntotal, ix->M, ix->nlist, ix->list_off.as<int64_t>(),
+        plain.as<uint8_t>());
+    GBK_LAUNCH_CHECK();
+    GBK_CUDA_CHECK(cudaMemcpyAsync(codes, plain.p, (size_t)ix->ntotal * ix->M, cudaMemcpyDefault,
+                                   st));
+  }
   if (ids && ix->ntotal)
     GBK_CUDA_CHECK(cudaMemcpyAsync(ids, ix->ids.p, sizeof(int64_t) * ix->ntotal, cudaMemcpyDefault,
                                    st));
+  return GBK_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ save / load
+
+namespace gbk {
+namespace {
+
+// File layout (little-endian): this header, then coarse f32 [nlist][d], pq f32 [M][256][d/M],
+// the rotation f32 [d][d] when `rotated`, list_off i64 [nlist+1], codes u8 [ntotal][M]
+// (sub-quantizer m in byte m), ids i64 [ntotal], and the kept vectors f32 [ntotal][d] when
+// `keep_vectors`.  Term-1 tables and sums, the rotated code layout and the staging arrays
+// are rebuilt on load from these, by the same kernels, so a loaded index searches exactly
+// as the saved one did.
+struct FileHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t d, nlist, M, nbits, use_precomputed, coarse_prec, keep_vectors, rotated;
+  int32_t codes_per_thread, blocks_per_sm, list_order, scan_threads;
+  int64_t ntotal;
+  int64_t reserved[4];
+};
+constexpr char kMagic[8] = {'G', 'B', 'K', 'I', 'V', 'F', 'P', 'Q'};
+
+struct File {
+  std::FILE* f = nullptr;
+  ~File() {
+    if (f) std::fclose(f);
+  }
+};
+
+gbk_status write_block(std::FILE* f, const void* dev, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return GBK_OK;
+  std::vector<unsigned char> h(bytes);
+  GBK_CUDA_CHECK(cudaMemcpyAsync(h.data(), dev, bytes, cudaMemcpyDeviceToHost, st));
+  GBK_CUDA_CHECK(cudaStreamSynchronize(st));
+  if (std::fwrite(h.data(), 1, bytes, f) != bytes)
+    return set_error(GBK_EINVAL, "gbk_ivfpq_save: write failed");
+  return GBK_OK;
+}
+
+gbk_status read_block(std::FILE* f, DevBuf& dst, size_t bytes, cudaStream_t st) {
+  gbk_status r;
+  if ((r = dst.alloc(std::max<size_t>(bytes, 1))) != GBK_OK) return r;
+  if (bytes == 0) return GBK_OK;
+  std::vector<unsigned char> h(bytes);
+  if (std::fread(h.data(), 1, bytes, f) != bytes)
+    return set_error(GBK_EINVAL, "gbk_ivfpq_load: file truncated");
+  GBK_CUDA_CHECK(cudaMemcpyAsync(dst.p, h.data(), bytes, cudaMemcpyHostToDevice, st));
+  GBK_CUDA_CHECK(cudaStreamSynchronize(st));
+  return GBK_OK;
+}
+
+// staged list of position j = the list whose range holds j (list-ordered input)
+__global__ void lists_of_positions_kernel(const int64_t* __restrict__ off, int nlist, int64_t n,
+                                          int32_t* __restrict__ lst) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nlist;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) / 2;
+      if (off[mid] <= j) lo = mid;
+      else hi = mid;
+    }
+    lst[j] = lo;
+  }
+}
+
+}  // namespace
+}  // namespace gbk
+
+extern "C" {
+
+gbk_status gbk_ivfpq_save(gbk_index* ix, const char* path, void* stream) {
+  clear_error();
+  GBK_REQUIRE(ix && ix->trained && path, "gbk_ivfpq_save: index missing, not trained, or no path");
+  cudaStream_t st = as_stream(stream);
+  gbk_status r;
+  if ((r = finalize_index(ix, st)) != GBK_OK) return r;
+  File file;
+  file.f = std::fopen(path, "wb");
+  if (!file.f) return set_error(GBK_EINVAL, "gbk_ivfpq_save: cannot open %s", path);
+  FileHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kMagic, 8);
+  h.version = 1;
+  h.d = ix->d;
+  h.nlist = ix->nlist;
+  h.M = ix->M;
+  h.nbits = 8;
+  h.use_precomputed = ix->use_precomputed;
+  h.coarse_prec = ix->coarse_prec;
+  h.keep_vectors = ix->keep_vectors ? 1 : 0;
+  h.rotated = ix->rotated ? 1 : 0;
+  h.codes_per_thread = ix->tuning.codes_per_thread;
+  h.blocks_per_sm = ix->tuning.blocks_per_sm;
+  h.list_order = ix->tuning.list_order;
+  h.scan_threads = ix->tuning.threads;
+  h.ntotal = ix->ntotal;
+  if (std::fwrite(&h, sizeof(h), 1, file.f) != 1)
+    return set_error(GBK_EINVAL, "gbk_ivfpq_save: write failed");
+  const size_t n = (size_t)ix->ntotal;
+  if ((r = write_block(file.f, ix->coarse.p, sizeof(float) * (size_t)ix->nlist * ix->d, st)) ||
+      (r = write_block(file.f, ix->pq.p, sizeof(float) * (size_t)ix->M * 256 * ix->dsub, st)) ||
+      (ix->rotated && (r = write_block(file.f, ix->rot.p, sizeof(float) * (size_t)ix->d * ix->d, st))) ||
+      (r = write_block(file.f, ix->list_off.p, sizeof(int64_t) * (size_t)(ix->nlist + 1), st)))
+    return r;
+  if (n) {
+    Scratch plain;
+    if ((r = plain.alloc(n * ix->M, st)) != GBK_OK) return r;
+    unrotate_codes_kernel<<<grid_for((int64_t)n), 256, 0, st>>>(
+        ix->codes.as<uint8_t>(), (int64_t)n, ix->M, ix->nlist, ix->list_off.as<int64_t>(),
+        plain.as<uint8_t>());
+    GBK_LAUNCH_CHECK();
+    if ((r = write_block(file.f, plain.p, n * ix->M, st)) ||
+        (r = write_block(file.f, ix->ids.p, sizeof(int64_t) * n, st)) ||
+        (ix->keep_vectors && (r = write_block(file.f, ix->vecs.p, sizeof(float) * n * ix->d, st))))
+      return r;
+  }
+  if (std::fflush(file.f) != 0) return set_error(GBK_EINVAL, "gbk_ivfpq_save: write failed");
+  return GBK_OK;
+}
+
+gbk_status gbk_ivfpq_load(const char* path, gbk_index** out, void* stream) {
+  clear_error();
+  GBK_REQUIRE(path && out, "gbk_ivfpq_load: NULL argument");
+  cudaStream_t st = as_stream(stream);
+  File file;
+  file.f = std::fopen(path, "rb");
+  if (!file.f) return set_error(GBK_EINVAL, "gbk_ivfpq_load: cannot open %s", path);
+  FileHeader h;
+  if (std::fread(&h, sizeof(h), 1, file.f) != 1 || std::memcmp(h.magic, kMagic, 8) != 0 ||
+      h.version != 1)
+    return set_error(GBK_EINVAL, "gbk_ivfpq_load: %s is not a gbknn IVFPQ file (version 1)", path);
+  gbk_index* ix = nullptr;
+  gbk_status r = gbk_ivfpq_create(h.d, h.nlist, h.M, h.nbits, GBK_METRIC_L2, &ix);
+  if (r != GBK_OK) return r;
+  struct Guard {
+    gbk_index* p;
+    ~Guard() { delete p; }
+  } guard{ix};
+  GBK_REQUIRE(h.ntotal >= 0 && h.ntotal <= (int64_t(1) << 32) - (int64_t(1) << 16),
+              "gbk_ivfpq_load: bad vector count");
+  GBK_REQUIRE(h.coarse_prec >= GBK_PREC_FP32 && h.coarse_prec <= GBK_PREC_FP8 &&
+                  (h.codes_per_thread == 2 || h.codes_per_thread == 4 || h.codes_per_thread == 8) &&
+                  h.blocks_per_sm >= 1 && h.blocks_per_sm <= 8 &&
+                  (h.scan_threads == 256 || h.scan_threads == 384 || h.scan_threads == 512),
+              "gbk_ivfpq_load: bad settings in the header");
+  const int64_t n = h.ntotal;
+  ix->use_precomputed = h.use_precomputed ? 1 : 0;
+  ix->coarse_prec = h.coarse_prec;
+  ix->keep_vectors = h.keep_vectors != 0;
+  ix->tuning.codes_per_thread = h.codes_per_thread;
+  ix->tuning.blocks_per_sm = h.blocks_per_sm;
+  ix->tuning.list_order = h.list_order ? 1 : 0;
+  ix->tuning.threads = h.scan_threads;
+  DevBuf off;
+  if ((r = read_block(file.f, ix->coarse, sizeof(float) * (size_t)h.nlist * h.d, st)) ||
+      (r = read_block(file.f, ix->pq, sizeof(float) * (size_t)h.M * 256 * (h.d / h.M), st)) ||
+      (h.rotated && (r = read_block(file.f, ix->rot, sizeof(float) * (size_t)h.d * h.d, st))) ||
+      (r = read_block(file.f, off, sizeof(int64_t) * (size_t)(h.nlist + 1), st))) {
+    off.release();
+    return r;
+  }
+  ix->rotated = h.rotated != 0;
+  std::vector<int64_t> offh(h.nlist + 1);
+  if (cudaMemcpy(offh.data(), off.p, sizeof(int64_t) * offh.size(), cudaMemcpyDeviceToHost) !=
+      cudaSuccess) {
+    off.release();
+    return set_error(GBK_ECUDA, "gbk_ivfpq_load: copy failed");
+  }
+  bool ok = offh[0] == 0 && offh[h.nlist] == n;
+  for (int L = 0; L < h.nlist && ok; L++) ok = offh[L] <= offh[L + 1];
+  if (!ok) {
+    off.release();
+    return set_error(GBK_EINVAL, "gbk_ivfpq_load: inconsistent list offsets");
+  }
+  // the lists become the staging arrays (insertion order = list order), rebuilt at first use
+  if ((r = read_block(file.f, ix->st_codes, (size_t)n * h.M, st)) ||
+      (r = read_block(file.f, ix->st_ids, sizeof(int64_t) * (size_t)n, st)) ||
+      (ix->keep_vectors &&
+       (r = read_block(file.f, ix->st_vecs, sizeof(float) * (size_t)n * h.d, st)))) {
+    off.release();
+    return r;
+  }
+  if ((r = ix->st_list.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1))) != GBK_OK) {
+    off.release();
+    return r;
+  }
+  if (n > 0) {
+    lists_of_positions_kernel<<<grid_for(n), 256, 0, st>>>(off.as<int64_t>(), h.nlist, n,
+                                                           ix->st_list.as<int32_t>());
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      off.release();
+      return set_error(GBK_ECUDA, "gbk_ivfpq_load: launch: %s", cudaGetErrorString(e));
+    }
+  }
+  off.release();
+  ix->n_staged = ix->cap_staged = n;
+  if (ix->use_precomputed) {
+    if ((r = ix->T.alloc(sizeof(float) * (size_t)ix->nlist * ix->M * 256)) != GBK_OK) return r;
+    if ((r = term1_run(ix->coarse.as<float>(), ix->pq.as<float>(), ix->nlist, ix->d, ix->M,
+                       ix->T.as<float>(), st)) != GBK_OK)
+      return r;
+  }
+  ix->trained = true;
+  ix->dirty = true;
+  if ((r = finalize_index(ix, st)) != GBK_OK) return r;
+  GBK_CUDA_CHECK(cudaStreamSynchronize(st));
+  guard.p = nullptr;
+  *out = ix;
   return GBK_OK;
 }
 
@@ -570,16 +797,21 @@ __global__ void recall_counts_kernel(const int64_t* __restrict__ I, const int64_
 
 }  // namespace
 
-gbk_status mlp_forward_classes(gbk_mlp* net, const float* X, int64_t B, int32_t* cls,
-                               cudaStream_t st);
-int mlp_inputs(const gbk_mlp* n);
+gbk_status nprobe_features_run(const float* xq, int64_t nq, int d, const float* clD, int tau,
+                               int nfeat, float* F, cudaStream_t st) {
+  if (nq == 0) return GBK_OK;
+  ProfScope prof("nprobe_features", st);
+  nprobe_features_kernel<<<(unsigned)nq, 128, 0, st>>>(xq, nq, d, clD, tau, nfeat, F);
+  GBK_LAUNCH_CHECK();
+  return GBK_OK;
+}
 
 // kq / out_off may be null (every query max_k results at q * max_k); positions: list
 // positions out instead of ids; prerotated: xq already in the index's rotated space.
 gbk_status batched_run(gbk_index* ix, const float* xq_in, int64_t nq, const int32_t* kq,
                        int max_k, const int32_t* npq_in, int max_nprobe, gbk_mlp* mlp,
                        const int64_t* out_off, float* D, int64_t* I, int32_t* np_used,
-                       cudaStream_t st, bool positions = false, bool prerotated = false) {
+                       cudaStream_t st, bool positions, bool prerotated) {
   gbk_status r;
   Scratch xr;
   const float* xq = xq_in;
@@ -601,12 +833,9 @@ gbk_status batched_run(gbk_index* ix, const float* xq_in, int64_t nq, const int3
     if ((r = npq_s.alloc(sizeof(int32_t) * (size_t)nq, st)) != GBK_OK) return r;
     if ((r = F.alloc(sizeof(float) * (size_t)nq * (ix->d + nfeat), st)) != GBK_OK) return r;
     if ((r = cls.alloc(sizeof(int32_t) * (size_t)nq, st)) != GBK_OK) return r;
-    {
-      ProfScope prof("nprobe_features", st);
-      nprobe_features_kernel<<<(unsigned)nq, 128, 0, st>>>(xq, nq, ix->d, clD.as<float>(), tau,
-                                                            std::min(nfeat, tau), F.as<float>());
-      GBK_LAUNCH_CHECK();
-    }
+    if ((r = nprobe_features_run(xq, nq, ix->d, clD.as<float>(), tau, std::min(nfeat, tau),
+                                 F.as<float>(), st)) != GBK_OK)
+      return r;
     if ((r = mlp_forward_classes(mlp, F.as<float>(), nq, cls.as<int32_t>(), st)) != GBK_OK) return r;
     class_to_nprobe_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(
         cls.as<int32_t>(), nq, max_nprobe, npq_s.as<int32_t>());
@@ -634,7 +863,7 @@ gbk_status batched_run(gbk_index* ix, const float* xq_in, int64_t nq, const int3
       GBK_OK)
     return r;
   GBK_CUDA_CHECK(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), st));
-  return ivf_scan_run(ix->M, nq, tau, max_k, clI.as<int64_t>(), clD.as<float>(), ix->T.as<float>(),
+  return ivf_scan_run(ix->M, nq, tau, max_k, clI.as<int64_t>(), clD.as<float>(), ix->s1.as<float>(),
                       t3.as<float>(), xq, ix->coarse.as<float>(), ix->pq.as<float>(), ix->d, direct,
                       ix->list_off.as<int64_t>(), ix->codes.as<uint8_t>(),
                       positions ? nullptr : ix->ids.as<int64_t>(), D, I, st, kq, npq, out_off,
@@ -682,7 +911,7 @@ gbk_status gbk_ivfpq_search_batched(gbk_index* ix, const float* xq, int64_t nq,
                                out_offsets, D, I);
   if (r != GBK_OK || nq == 0) return r;
   cudaStream_t st = as_stream(stream);
-  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  if ((r = finalize_index(ix, st)) != GBK_OK) return r;
   return batched_run(ix, xq, nq, k_per_q, max_k, nprobe_per_q, max_nprobe, mlp, out_offsets, D, I,
                      nprobe_used, st);
 }
@@ -710,7 +939,7 @@ gbk_status gbk_ivfpq_search_batched_refine(gbk_index* ix, const float* xq, int64
   GBK_REQUIRE(xq && D && I, "batched refine: NULL pointer");
   cudaStream_t st = as_stream(stream);
   gbk_status r;
-  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  if ((r = finalize_index(ix, st)) != GBK_OK) return r;
   Scratch xr, Dc, Ic;
   const float* xqr = xq;
   if ((r = rotate_rows(ix, xq, nq, xr, &xqr, st)) != GBK_OK) return r;
@@ -739,7 +968,7 @@ gbk_status gbk_ivfpq_batched_graph(gbk_index* ix, const float* xq, int64_t nq,
   if (r != GBK_OK) return r;
   GBK_REQUIRE(nq > 0, "gbk_ivfpq_batched_graph: empty batch");
   cudaStream_t st = as_stream(stream);
-  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  if ((r = finalize_index(ix, st)) != GBK_OK) return r;
   if (!device_status()) return set_error(GBK_ECUDA, "device status word unavailable");
   GBK_CUDA_CHECK(cudaStreamSynchronize(st));
   cudaStream_t cs;
@@ -860,7 +1089,7 @@ static gbk_status knn_graph_run(gbk_index* ix, const float* x, int64_t n, const 
   batch = std::min<int64_t>(batch, std::min<int64_t>(n, (int64_t(1) << 31) / (kc + 1) - 1));
   cudaStream_t st = as_stream(stream);
   gbk_status r;
-  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  if ((r = finalize_index(ix, st)) != GBK_OK) return r;
   Scratch D1, I1, Dc, Ic, kq, off;
   if ((r = D1.alloc(sizeof(float) * (size_t)batch * kk, st)) != GBK_OK) return r;
   if ((r = I1.alloc(sizeof(int64_t) * (size_t)batch * kk, st)) != GBK_OK) return r;
@@ -947,6 +1176,16 @@ gbk_status gbk_ivfpq_set_tuning(gbk_index* ix, int32_t codes_per_thread, int32_t
   return GBK_OK;
 }
 
+gbk_status gbk_ivfpq_set_scan_options(gbk_index* ix, int32_t threads_per_block, int32_t by_list) {
+  clear_error();
+  GBK_REQUIRE(ix, "gbk_ivfpq_set_scan_options: NULL index");
+  GBK_REQUIRE(threads_per_block == 256 || threads_per_block == 384 || threads_per_block == 512,
+              "gbk_ivfpq_set_scan_options: threads per block must be 256, 384 or 512");
+  ix->tuning.threads = threads_per_block;
+  ix->tuning.list_order = by_list ? 1 : 0;
+  return GBK_OK;
+}
+
 gbk_status gbk_ivfpq_get_tuning(const gbk_index* ix, int32_t* codes_per_thread,
                                 int32_t* blocks_per_sm) {
   clear_error();
@@ -967,7 +1206,7 @@ gbk_status gbk_ivfpq_autotune(gbk_index* ix, const float* xq, int64_t nq, const 
   GBK_REQUIRE(nq > 0, "gbk_ivfpq_autotune: empty batch");
   if (reps < 1) reps = 3;
   cudaStream_t st = as_stream(stream);
-  if ((r = finalize(ix, st)) != GBK_OK) return r;
+  if ((r = finalize_index(ix, st)) != GBK_OK) return r;
   cudaEvent_t e0, e1;
   GBK_CUDA_CHECK(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -977,10 +1216,13 @@ gbk_status gbk_ivfpq_autotune(gbk_index* ix, const float* xq, int64_t nq, const 
   const gbk::ScanTuning keep = ix->tuning;
   gbk::ScanTuning best = keep;
   float best_t = -1.f;
-  static const int U[3] = {2, 4, 8};
-  for (int ui = 0; ui < 3 && r == GBK_OK; ui++) {
-    for (int bps = 1; bps <= 4 && r == GBK_OK; bps++) {
-      ix->tuning.codes_per_thread = U[ui];
+  // block size x codes per thread (the shapes that keep two blocks per SM) x blocks per SM
+  static const int SHAPES[6][2] = {{256, 2}, {256, 4}, {256, 8}, {384, 2}, {384, 4}, {512, 2}};
+  const int nshape = ix->use_precomputed ? 6 : 3;  // the direct-table scan has 256 threads
+  for (int si = 0; si < nshape && r == GBK_OK; si++) {
+    for (int bps = 1; bps <= 2 && r == GBK_OK; bps++) {
+      ix->tuning.threads = SHAPES[si][0];
+      ix->tuning.codes_per_thread = SHAPES[si][1];
       ix->tuning.blocks_per_sm = bps;
       // one untimed run (first-use set-up), then `reps` timed runs of the whole batch
       r = gbk::batched_run(ix, xq, nq, k_per_q, max_k, nprobe_per_q, max_nprobe, mlp,

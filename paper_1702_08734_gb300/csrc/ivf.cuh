@@ -51,11 +51,15 @@ struct DevBuf {
 
 
 // Launch shape of the IVFADC list scan, chosen by gbk_ivfpq_autotune or set by the caller:
-// codes each thread loads per step (2, 4 or 8) and, in the persistent mixed-batch mode,
-// resident blocks per SM (1..8).  Results do not depend on it.
+// codes each thread loads per step (2, 4 or 8), resident blocks per SM (1..8) of the
+// persistent mode, and whether a plain search takes its queries in the order of their
+// nearest list (persistent mode) or in input order (block per query).  Results do not
+// depend on it.
 struct ScanTuning {
-  int codes_per_thread = 4;
+  int codes_per_thread = 2;
   int blocks_per_sm = 2;
+  int list_order = 1;  // plain search: queries in the order of their nearest list
+  int threads = 384;   // table-mode scan block size: 256, 384 (U <= 4) or 512 (U = 2)
 };
 
 // Stable counting sort by key in [0, nb): offsets[nb+1], order[n] (positions grouped by

@@ -4,21 +4,25 @@
 // Distance of query x to database vector y in list L (Eq. 11):
 //   ||x - q(y)||^2 = sum_m T[L][m][code_m]  +  ||x - c_L||^2  -  2 sum_m <x^m, C_m[code_m]>
 // with T[L][m][c] = ||C_m[c]||^2 + 2 <c_L^m, C_m[c]> (term 1, query independent), term 2
-// the coarse distance, term 3 computed once per query.  The scan builds, per (query, list),
-// LUT[m][c] = T[L][m][c] - 2 term3[m][c] in shared memory and sums b look-ups per code.
+// the coarse distance, term 3 computed once per query.  Term 1 depends on the stored vector
+// only, so its sum over the code, s1[j] = sum_m T[L][m][code_jm], is formed once per vector
+// when the lists are built; the scan then adds, per code, M look-ups into the query's
+// term-3 table Q_x[m][c] = -2 <x^m, C_m[c]>, which is built once per query (not once per
+// (query, list) as the tables of section 5.3 are).  Without precomputed tables (the direct
+// mode) the scan builds LUT[m][c] = ||(x - c_L)^m - C_m[c]||^2 per (query, list).
 //
-// Shared-memory LUT layout: entry (c, m) is stored at c*32 + h*M + m for every copy
-// h < 32/M, and lane l of a warp reads sub-table m = (s + l) mod M at step s from copy
-// h = l / M.  The 32 lanes of a warp then always hit 32 distinct banks (conflict-free),
-// instead of the ~3.5-way conflicts of random look-ups into LUT[m][c].  Each lane rotates
-// its 16-byte code by (l mod M) bytes once so that step s reads byte s.
+// Bank-conflict-free look-ups: the 32 lanes of a warp look up 32 different codes at once.
+// Stored codes are rotated per list position: the code at position r of its list holds
+// sub-quantizer (s + r) mod M in byte s.  A warp scans 32 consecutive positions of one
+// list, so lane l (= r mod 32) reads sub-table (s + l) mod M at step s, and the tables are
+// laid out so that those 32 reads fall in 32 different banks whatever the codes are.
 #include <algorithm>
 
 #include "common.cuh"
 #include "ivf.cuh"
+#include "ivf_scan_kernels.cuh"
 #include "knn.cuh"
 #include "select_core.cuh"
-#include "sm100.cuh"
 
 namespace gbk {
 
@@ -125,302 +129,8 @@ __global__ void expand_codebooks_kernel(const float* __restrict__ pq, int d, int
   }
 }
 
-// --------------------------------------------------------------------- scan
-
-template <int M>
-struct CodeWords {
-  static constexpr int NW = M / 4;
-};
-
-// Rotate the M-byte code right by `rot` bytes (byte s of the result = byte (s+rot) mod M).
-template <int M>
-__device__ __forceinline__ void rotate_code(uint32_t (&w)[M / 4], int rot) {
-  constexpr int NW = M / 4;
-  const int q = rot >> 2, r8 = (rot & 3) * 8;
-  uint32_t t[NW];
-#pragma unroll
-  for (int b = 1; b < NW; b <<= 1) {
-    if (q & b) {
-#pragma unroll
-      for (int j = 0; j < NW; j++) t[j] = w[(j + b) % NW];
-#pragma unroll
-      for (int j = 0; j < NW; j++) w[j] = t[j];
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < NW; j++) t[j] = __funnelshift_r(w[j], w[(j + 1) % NW], r8);
-#pragma unroll
-  for (int j = 0; j < NW; j++) w[j] = t[j];
-}
-
-template <int M>
-__device__ __forceinline__ void load_code(const uint8_t* codes, int64_t i, uint32_t (&w)[M / 4]) {
-  if constexpr (M == 4) {
-    w[0] = __ldg(reinterpret_cast<const uint32_t*>(codes) + i);
-  } else if constexpr (M == 8) {
-    const uint2 v = __ldg(reinterpret_cast<const uint2*>(codes) + i);
-    w[0] = v.x;
-    w[1] = v.y;
-  } else if constexpr (M == 16) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(codes) + i);
-    w[0] = v.x;
-    w[1] = v.y;
-    w[2] = v.z;
-    w[3] = v.w;
-  } else {
-    const uint4 a = __ldg(reinterpret_cast<const uint4*>(codes) + 2 * i);
-    const uint4 b = __ldg(reinterpret_cast<const uint4*>(codes) + 2 * i + 1);
-    w[0] = a.x;
-    w[1] = a.y;
-    w[2] = a.z;
-    w[3] = a.w;
-    w[4] = b.x;
-    w[5] = b.y;
-    w[6] = b.z;
-    w[7] = b.w;
-  }
-}
-
-struct ScanArgs {
-  int64_t nq;
-  int nprobe, k;
-  const int64_t* cl_I;   // [nq][nprobe] probed lists, nearest first (-1 = none)
-  const float* cl_D;     // [nq][nprobe] term 2 = ||x - c_L||^2
-  const float* T;        // [nlist][256][M] term 1 (precomputed tables)
-  const float* t3;       // [nq][256][M] term 3
-  const float* xq;       // direct tables: queries
-  const float* coarse;   // direct tables: coarse centroids
-  const float* pq;       // direct tables: codebooks [M][256][dsub]
-  int d;
-  int direct;            // 1: LUT[m][c] = ||(x - c_L)^m - C_m[c]||^2 computed in place
-  const int64_t* list_off;
-  const uint8_t* codes;
-  const int64_t* ids;    // null: list positions out instead of ids
-  float* D;
-  int64_t* I;
-  // mixed batches (all optional): per-query k and nprobe (<= k, nprobe above), output
-  // offsets (results of query q at D/I + out_off[q]); persistent mode takes queries from
-  // `order` (longest first) through the atomic `counter`.
-  const int32_t* kq;
-  const int32_t* npq;
-  const int64_t* out_off;
-  const int64_t* order;
-  unsigned long long* counter;
-  uint32_t* status;      // device status word (bounded waits record a timeout here)
-};
-
-// Block per query: for each probed list, build the LUT, stream the codes (U 16-byte codes
-// per thread per step), form the distance and keep the k best (block selection, section 4
-// goal of a single pass); ids are looked up only for the winners (section 5.3).
-template <int M, int KP, int U>
-__global__ void __launch_bounds__(256)
-    ivf_scan_kernel(const ScanArgs a) {
-  constexpr int THREADS = 256, CAP = 4096;
-  using Sel = BlockSelect<THREADS, KP, CAP>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* lut = reinterpret_cast<float*>(smem_raw);                  // [256][32]
-  float* t3s = lut + 256 * 32;                                       // [256][M]
-  float* tst = t3s + M * 256;                                        // [256][M] term 1 of a list
-  typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(tst + M * 256);
-  __shared__ int64_t q_sh;
-  __shared__ uint64_t t_bar;  // completion of the term-1 bulk copy
-  __shared__ int abort_flag;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int rot = lane % M, h = lane / M;
-  constexpr uint32_t TBYTES = M * 256 * sizeof(float);
-  uint32_t t_phase = 0;
-  if (tid == 0) {
-    sm100::mbar_init(&t_bar, 1);
-    abort_flag = 0;
-    sm100::fence_mbar_init();
-  }
-  __syncthreads();
-  // one thread starts the copy of list L's term-1 table into tst
-  auto copy_T = [&](int64_t L) {
-    if (tid == 0) {
-      sm100::fence_proxy_async_smem();
-      sm100::mbar_arrive_expect_tx(&t_bar, TBYTES);
-      sm100::bulk_load(tst, a.T + L * M * 256, TBYTES, &t_bar);
-    }
-  };
-  for (int64_t it = blockIdx.x;; it += gridDim.x) {
-    // next query: static (one block per query) or from the persistent work queue
-    if (a.counter) {
-      __syncthreads();
-      if (tid == 0) {
-        const unsigned long long w = atomicAdd(a.counter, 1ull);
-        q_sh = w < (unsigned long long)a.nq ? a.order[w] : -1;
-      }
-      __syncthreads();
-    }
-    const int64_t q = a.counter ? q_sh : (it < a.nq ? it : -1);
-    if (q < 0) break;
-    const int kq = a.kq ? a.kq[q] : a.k;
-    const int npq = a.npq ? min(a.npq[q], a.nprobe) : a.nprobe;
-    const int64_t ob = a.out_off ? a.out_off[q] : q * (int64_t)a.k;
-    __syncthreads();
-    if (!a.direct)
-      for (int e = tid; e < M * 256; e += THREADS) t3s[e] = a.t3[q * M * 256 + e];
-    Sel::init(s);
-    __syncthreads();
-    ValueFilter f;
-    f.set(NAN_KEY, false);
-    // Software pipeline across the probed lists: the term-1 table of list p+1 is copied
-    // into shared memory (bulk copy) and the first codes of each list are loaded into
-    // registers while earlier work proceeds, so no global-memory latency is exposed once
-    // per list.
-    int64_t Lc = -1, o0c = 0, o1c = 0;  // current list
-    auto fetch_list = [&](int p, int64_t& L, int64_t& o0, int64_t& o1) {
-      L = p < npq ? a.cl_I[q * a.nprobe + p] : -1;
-      if (L >= 0) {
-        o0 = a.list_off[L];
-        o1 = a.list_off[L + 1];
-      } else {
-        o0 = o1 = 0;
-      }
-    };
-    constexpr int STEP = THREADS * U;
-    uint32_t wn[U][M / 4];               // codes of the next step, in flight
-    auto fetch_codes = [&](int64_t b0, int64_t o1) {
-#pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int64_t i = b0 + u * THREADS + tid;
-        if (i < o1) load_code<M>(a.codes, i, wn[u]);
-      }
-    };
-    fetch_list(0, Lc, o0c, o1c);
-    if (Lc >= 0 && !a.direct) copy_T(Lc);
-    bool ok = true;
-    for (int p = 0; p < npq && ok; p++) {
-      const int64_t L = Lc, o0 = o0c, o1 = o1c;
-      if (L >= 0) fetch_codes(o0, o1);
-      __syncthreads();  // previous list's look-ups are done
-      if (L >= 0) {
-        // LUT[c][h*M + m] = T[L][c][m] - 2 term3[c][m]: warp w fills rows c of its 32; lane l
-        // writes word c*32 + l (copy h = l / M of sub-table m = l % M): conflict-free.
-        if (!a.direct) {
-          ok = sm100::mbar_wait(&t_bar, t_phase, a.status, (volatile int*)&abort_flag);
-          t_phase ^= 1u;
-          if (ok) {
-#pragma unroll 4
-            for (int i = 0; i < 32; i++) {
-              const int c = warp * 32 + i;
-              const int e = c * M + rot;
-              lut[c * 32 + lane] = fmaf(-2.f, t3s[e], tst[e]);
-            }
-          }
-        } else {
-          const int dsub = a.d / M;
-          for (int i = 0; i < 32; i++) {
-            const int c = warp * 32 + i, m = rot;
-            const float* C = a.pq + ((int64_t)m * 256 + c) * dsub;
-            float v = 0.f;
-            for (int t = 0; t < dsub; t++) {
-              const float r = a.xq[q * a.d + m * dsub + t] - a.coarse[L * a.d + m * dsub + t];
-              const float e2 = r - C[t];
-              v = fmaf(e2, e2, v);
-            }
-            lut[c * 32 + lane] = v;
-          }
-        }
-      }
-      const float term2 = L >= 0 ? a.cl_D[q * a.nprobe + p] : 0.f;
-      fetch_list(p + 1, Lc, o0c, o1c);  // next list's extent
-      __syncthreads();                   // LUT complete, tst consumed
-      if (Lc >= 0 && !a.direct && ok) copy_T(Lc);
-      if (L < 0 || !ok) continue;        // uniform across the block
-      const float base = a.direct ? 0.f : term2;
-      for (int64_t b0 = o0; b0 < o1; b0 += STEP) {
-        uint32_t w[U][M / 4];
-#pragma unroll
-        for (int u = 0; u < U; u++)
-#pragma unroll
-          for (int j = 0; j < M / 4; j++) w[u][j] = wn[u][j];
-        if (b0 + STEP < o1) fetch_codes(b0 + STEP, o1);
-        uint32_t mask = 0;
-        uint64_t cc[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int64_t i = b0 + u * THREADS + tid;
-          cc[u] = ~0ull;
-          if (i < o1) {
-            rotate_code<M>(w[u], rot);
-            float acc = 0.f;
-#pragma unroll
-            for (int st = 0; st < M; st++) {
-              const uint32_t c = (w[u][st >> 2] >> ((st & 3) * 8)) & 255u;
-              const int m = (st + rot) & (M - 1);
-              acc += lut[c * 32 + h * M + m];
-            }
-            const float dist = base + acc;
-            if (f.pass(dist)) {
-              mask |= 1u << u;
-              cc[u] = composite(ordered_key(dist, false), (uint32_t)i);
-            }
-          }
-        }
-        Sel::template push<U>(s, mask, cc);
-        __syncthreads();
-        if (s.n_buf > CAP - STEP) {
-          Sel::compact(s, kq);
-          f.set((uint32_t)(s.thr >> 32), false);
-        }
-      }
-    }
-    Sel::finish(s, kq);
-    for (int j = tid; j < kq; j += THREADS) {
-      const uint64_t e = s.top[j];
-      if (e == ~0ull) {
-        a.D[ob + j] = __int_as_float(0x7f800000);
-        a.I[ob + j] = -1;
-      } else {
-        a.D[ob + j] = key_value((uint32_t)(e >> 32), false);
-        a.I[ob + j] = a.ids ? a.ids[(uint32_t)e] : (int64_t)(uint32_t)e;
-      }
-    }
-  }
-}
-
-template <int M, int KP, int U>
-static gbk_status launch_scan(const ScanArgs& a, const ScanTuning& tun, cudaStream_t st) {
-  using Sel = BlockSelect<256, KP, 4096>;
-  const size_t smem = sizeof(float) * (256 * 32 + 2 * M * 256) + sizeof(typename Sel::Smem);
-  auto kern = ivf_scan_kernel<M, KP, U>;
-  static bool attr = false;
-  if (!attr) {
-    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-    attr = true;
-  }
-  // persistent mode: blocks_per_sm resident blocks per SM pull queries from the counter
-  const int64_t grid =
-      a.counter ? std::min<int64_t>(a.nq, (int64_t)tun.blocks_per_sm * device_info().sm_count)
-                : a.nq;
-  kern<<<(unsigned)grid, 256, smem, st>>>(a);
-  GBK_LAUNCH_CHECK();
-  return GBK_OK;
-}
-
-template <int M, int KP>
-static gbk_status scan_u(const ScanArgs& a, const ScanTuning& tun, cudaStream_t st) {
-  switch (tun.codes_per_thread) {
-    case 2: return launch_scan<M, KP, 2>(a, tun, st);
-    case 4: return launch_scan<M, KP, 4>(a, tun, st);
-    case 8: return launch_scan<M, KP, 8>(a, tun, st);
-    default: return set_error(GBK_EINVAL, "scan tuning: codes per thread must be 2, 4 or 8");
-  }
-}
-
-template <int M>
-static gbk_status scan_k(const ScanArgs& a, const ScanTuning& tun, cudaStream_t st) {
-  if (a.k <= 32) return scan_u<M, 32>(a, tun, st);  // a.k = largest k
-  if (a.k <= 128) return scan_u<M, 128>(a, tun, st);
-  if (a.k <= 256) return scan_u<M, 256>(a, tun, st);
-  return scan_u<M, 1024>(a, tun, st);
-}
-
 gbk_status ivf_scan_run(int M, int64_t nq, int nprobe, int k, const int64_t* cl_I,
-                        const float* cl_D, const float* T, const float* t3, const float* xq,
+                        const float* cl_D, const float* s1, const float* t3, const float* xq,
                         const float* coarse, const float* pq, int d, bool direct,
                         const int64_t* list_off, const uint8_t* codes, const int64_t* ids,
                         float* D, int64_t* I, cudaStream_t st, const int32_t* kq,
@@ -429,9 +139,8 @@ gbk_status ivf_scan_run(int M, int64_t nq, int nprobe, int k, const int64_t* cl_
   if (nq == 0) return GBK_OK;
   if (tun.blocks_per_sm < 1 || tun.blocks_per_sm > 8)
     return set_error(GBK_EINVAL, "scan tuning: blocks per SM must be in [1, 8]");
-  ScanArgs a{nq, nprobe, k, cl_I, cl_D, T, t3, xq, coarse, pq, d, direct ? 1 : 0, list_off,
-             codes, ids, D, I, kq, npq, out_off, order, counter, device_status()};
-  if (!a.status) return set_error(GBK_ECUDA, "device status word unavailable");
+  ScanArgs a{nq,     nprobe, k,     cl_I, cl_D, s1,      t3,   xq,      coarse, pq, d,
+             direct ? 1 : 0, list_off, codes, ids, D, I, kq, npq, out_off, order, counter};
   ProfScope prof("ivf_scan", st);
   if (M == 4) return scan_k<4>(a, tun, st);
   if (M == 8) return scan_k<8>(a, tun, st);

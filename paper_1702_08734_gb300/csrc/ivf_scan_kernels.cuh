@@ -1,0 +1,420 @@
+// List-scan kernels of the IVFADC search (section 5.3, Algorithm 4): the per-query
+// table scan and the direct-table scan with their fused k-selection, and the launch
+// templates.  Each ivf_scan_m<M>.cu instantiates them for one code size M; the layout
+// of tables and codes is described in ivf_scan.cu.
+#pragma once
+#include <algorithm>
+
+#include "common.cuh"
+#include "ivf.cuh"
+#include "select_core.cuh"
+
+namespace gbk {
+
+// --------------------------------------------------------------------- scan
+
+template <int M>
+__device__ __forceinline__ void load_code(const uint8_t* codes, int64_t i, uint32_t (&w)[M / 4]) {
+  if constexpr (M == 4) {
+    w[0] = __ldg(reinterpret_cast<const uint32_t*>(codes) + i);
+  } else if constexpr (M == 8) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(codes) + i);
+    w[0] = v.x;
+    w[1] = v.y;
+  } else if constexpr (M == 16) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(codes) + i);
+    w[0] = v.x;
+    w[1] = v.y;
+    w[2] = v.z;
+    w[3] = v.w;
+  } else {
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(codes) + 2 * i);
+    const uint4 b = __ldg(reinterpret_cast<const uint4*>(codes) + 2 * i + 1);
+    w[0] = a.x;
+    w[1] = a.y;
+    w[2] = a.z;
+    w[3] = a.w;
+    w[4] = b.x;
+    w[5] = b.y;
+    w[6] = b.z;
+    w[7] = b.w;
+  }
+}
+
+struct ScanArgs {
+  int64_t nq;
+  int nprobe, k;
+  const int64_t* cl_I;   // [nq][nprobe] probed lists, nearest first (-1 = none)
+  const float* cl_D;     // [nq][nprobe] term 2 = ||x - c_L||^2
+  const float* s1;       // table mode: [ntotal] term 1 summed over each stored code
+  const float* t3;       // table mode: [nq][256][M] term 3
+  const float* xq;       // direct tables: queries
+  const float* coarse;   // direct tables: coarse centroids
+  const float* pq;       // direct tables: codebooks [M][256][dsub]
+  int d;
+  int direct;            // 1: LUT[m][c] = ||(x - c_L)^m - C_m[c]||^2 computed per list
+  const int64_t* list_off;
+  const uint8_t* codes;  // list order, rotated by list position (see the file comment)
+  const int64_t* ids;    // null: list positions out instead of ids
+  float* D;
+  int64_t* I;
+  // mixed batches (all optional): per-query k and nprobe (<= k, nprobe above), output
+  // offsets (results of query q at D/I + out_off[q]); persistent mode takes queries from
+  // `order` through the atomic `counter`.
+  const int32_t* kq;
+  const int32_t* npq;
+  const int64_t* out_off;
+  const int64_t* order;
+  unsigned long long* counter;
+};
+
+// Next query of a block: static (block b serves queries b, b + grid, ...) or from the
+// persistent work queue.  Uniform across the block; -1 when none is left.
+__device__ __forceinline__ int64_t next_query(const ScanArgs& a, int64_t it, int64_t* q_sh) {
+  if (!a.counter) return it < a.nq ? it : -1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long w = atomicAdd(a.counter, 1ull);
+    *q_sh = w < (unsigned long long)a.nq ? a.order[w] : -1;
+  }
+  __syncthreads();
+  return *q_sh;
+}
+
+// Sorted k best of a query (after the scan) to D/I at offset ob; ids of the winners only
+// (section 5.3), (+inf, -1) padding.
+template <class Sel>
+__device__ __forceinline__ void write_results(const ScanArgs& a, typename Sel::Smem& s, int kq,
+                                              int64_t ob) {
+  Sel::finish(s, kq);
+  for (int j = threadIdx.x; j < kq; j += (int)blockDim.x) {
+    const uint64_t e = s.top[j];
+    if (e == ~0ull) {
+      a.D[ob + j] = __int_as_float(0x7f800000);
+      a.I[ob + j] = -1;
+    } else {
+      a.D[ob + j] = key_value((uint32_t)(e >> 32), false);
+      a.I[ob + j] = a.ids ? a.ids[(uint32_t)e] : (int64_t)(uint32_t)e;
+    }
+  }
+}
+
+// Table mode.  Block per query.  Its term-3 table sits in shared memory as 256 rows of 64
+// words: word s of row c holds Q_x[s mod M][c] (s < 31 + M used), so lane l at step s reads
+// word l + s: bank (l + s) mod 32, distinct across the warp.  The probed lists are laid end
+// to end in a virtual range, each padded to a multiple of 32 positions, and the block walks
+// that range STEP = THREADS U positions at a time: every warp-chunk of 32 positions lies in
+// one list (lane = list position mod 32) and no step is left short by a list's end.  Each
+// thread keeps the record of the list its positions are in (virtual start and end, offset
+// to the stored position, term 2) in registers and reads the next one only at a list
+// boundary.  Codes and term-1 sums of the next step are loaded (into the other of two
+// register buffers) while the current step is scored; the k best are kept by the block
+// selection (a single pass, section 4) and ids looked up for the winners only (5.3).
+template <int M, int U>
+struct TableStep {
+  uint32_t w[U][M / 4];  // codes
+  uint32_t pos[U];       // stored positions (0xffffffff: padding)
+  float s1[U];           // term-1 sums (added when scored: the load is not waited for here)
+  float base[U];         // term 2 of the list
+};
+
+// Byte offset of the table kernel's list records in dynamic shared memory: after the
+// term-3 table and the selection state, rounded up to 16 bytes for the 16-byte records.
+template <int KP>
+constexpr size_t table_rec_offset() {
+  return (sizeof(float) * 256 * 64 + sizeof(typename BlockSelect<256, KP, 4096>::Smem) + 15) /
+         16 * 16;
+}
+
+template <int M, int KP, int U, int THREADS>
+__global__ void __launch_bounds__(THREADS, 2)
+    ivf_scan_table_kernel(const ScanArgs a) {
+  constexpr int CAP = 4096, LW = 64;
+  constexpr int STEP = THREADS * U;
+  constexpr uint32_t NONE = 0xffffffffu;
+  using Sel = BlockSelect<THREADS, KP, CAP>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* lut = reinterpret_cast<float*>(smem_raw);  // [256][64]
+  typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(lut + 256 * LW);
+  // per probed list p: {virtual start, stored position - virtual position, virtual end,
+  // term 2}; record npq holds {virtual total, ...}
+  uint4* rec = reinterpret_cast<uint4*>(smem_raw + table_rec_offset<KP>());  // [nprobe + 1]
+  __shared__ int64_t q_sh;
+  __shared__ uint32_t wsum[THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lane4 = (uint32_t)lane * 4u;
+  for (int64_t it = blockIdx.x;; it += gridDim.x) {
+    const int64_t q = next_query(a, it, &q_sh);
+    if (q < 0) break;
+    const int kq = a.kq ? a.kq[q] : a.k;
+    const int npq = a.npq ? min(a.npq[q], a.nprobe) : a.nprobe;
+    const int64_t ob = a.out_off ? a.out_off[q] : q * (int64_t)a.k;
+    __syncthreads();  // the previous query's tables are no longer read
+    {
+      const float4* t3q = reinterpret_cast<const float4*>(a.t3 + q * M * 256);
+      float4* l4 = reinterpret_cast<float4*>(lut);
+      for (int e = tid; e < 256 * LW / 4; e += THREADS) {
+        const int c = e / (LW / 4), w4 = e % (LW / 4);  // words 4 w4 .. 4 w4 + 3 of row c
+        const float4 t = __ldg(t3q + (c * M + ((4 * w4) & (M - 1))) / 4);
+        l4[e] = make_float4(-2.f * t.x, -2.f * t.y, -2.f * t.z, -2.f * t.w);
+      }
+    }
+    {  // list records: lengths rounded up to 32 laid end to end (block-wide exclusive scan)
+      const int ppt = (npq + THREADS - 1) / THREADS;
+      uint32_t loc = 0;
+      for (int j = 0; j < ppt; j++) {
+        const int p = tid * ppt + j;
+        if (p < npq) {
+          const int64_t L = a.cl_I[q * a.nprobe + p];
+          uint32_t st = 0, sz = 0, b = 0;
+          if (L >= 0) {
+            const int64_t o0 = a.list_off[L];
+            st = (uint32_t)o0;
+            sz = (uint32_t)(a.list_off[L + 1] - o0);
+            b = __float_as_uint(a.cl_D[q * a.nprobe + p]);
+          }
+          rec[p] = make_uint4(sz, st, 0u, b);
+          loc += (sz + 31u) & ~31u;
+        }
+      }
+      uint32_t inc = loc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL_MASK, inc, o);
+        if (lane >= o) inc += t;
+      }
+      if (lane == 31) wsum[warp] = inc;
+      __syncthreads();
+      uint32_t run = inc - loc;
+      for (int w2 = 0; w2 < warp; w2++) run += wsum[w2];
+      for (int j = 0; j < ppt; j++) {
+        const int p = tid * ppt + j;
+        if (p < npq) {
+          const uint4 r0 = rec[p];  // {length, first stored position, -, term 2}
+          rec[p] = make_uint4(run, r0.y - run, run + r0.x, r0.w);
+          run += (r0.x + 31u) & ~31u;
+        }
+      }
+      if (tid == THREADS - 1) rec[npq] = make_uint4(run, 0u, 0u, 0u);
+    }
+    Sel::init(s);
+    __syncthreads();
+    const uint32_t total = rec[npq].x;
+    float thr = __int_as_float(0x7f800000);  // filter: pass unless above (NaN always passes)
+    // this thread's list: record fields in registers; n_start = start of the next list
+    int pw = -1;
+    uint32_t c_off = 0, c_end = 0, c_base = 0, n_start = 0;
+    auto fetch = [&](TableStep<M, U>& b, uint32_t v0) {
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const uint32_t v = v0 + (uint32_t)(u * THREADS + tid);
+        b.pos[u] = NONE;
+        if (v < total) {
+          while (v >= n_start) {  // list boundary (rare): the next non-empty list's record
+            pw++;
+            const uint4 r = rec[pw];
+            c_off = r.y;
+            c_end = r.z;
+            c_base = r.w;
+            n_start = rec[pw + 1].x;
+          }
+          if (v < c_end) {
+            const uint32_t i = v + c_off;
+            b.pos[u] = i;
+            load_code<M>(a.codes, i, b.w[u]);
+            b.s1[u] = __ldg(a.s1 + i);
+            b.base[u] = __uint_as_float(c_base);
+          }
+        }
+      }
+    };
+    auto score = [&](const TableStep<M, U>& b) {
+      uint32_t mask = 0;
+      uint64_t cc[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        cc[u] = ~0ull;
+        if (b.pos[u] != NONE) {
+          // all M look-ups first, then a pairwise sum: the loads overlap instead of each
+          // waiting on the previous add
+          float t[M];
+#pragma unroll
+          for (int st = 0; st < M; st++) {
+            // (code byte st) * 256 + 4 lane: row of the code, word lane (+ st below)
+            const uint32_t addr = __byte_perm(b.w[u][st >> 2], lane4, 0x6504u | ((st & 3) << 4));
+            t[st] = *reinterpret_cast<const float*>(smem_raw + addr + st * 4);
+          }
+#pragma unroll
+          for (int h = M / 2; h >= 1; h >>= 1)
+#pragma unroll
+            for (int j = 0; j < h; j++) t[j] += t[j + h];
+          const float dist = b.base[u] + (b.s1[u] + t[0]);
+          if (!(dist > thr)) {  // exact order is settled at compaction
+            mask |= 1u << u;
+            cc[u] = composite(ordered_key(dist, false), b.pos[u]);
+          }
+        }
+      }
+      Sel::template push<U>(s, mask, cc);
+      __syncthreads();
+      if (s.n_buf > CAP - STEP) {
+        Sel::compact(s, kq);
+        const uint32_t tk = (uint32_t)(s.thr >> 32);
+        thr = tk == NAN_KEY ? __int_as_float(0x7f800000) : key_value(tk, false);
+      }
+    };
+    TableStep<M, U> A, B;
+    if (total > 0) fetch(A, 0);
+    for (uint32_t v0 = 0; v0 < total; v0 += 2 * STEP) {  // ping-pong between A and B
+      if (v0 + STEP < total) fetch(B, v0 + STEP);
+      score(A);
+      if (v0 + STEP >= total) break;
+      if (v0 + 2 * STEP < total) fetch(A, v0 + 2 * STEP);
+      score(B);
+    }
+    write_results<Sel>(a, s, kq, ob);
+  }
+}
+
+// Direct mode (no precomputed tables).  Block per query; for each probed list the LUT
+// [256][32] holds LUT[m][c] = ||(x - c_L)^m - C_m[c]||^2 at word c*32 + h*M + m for every
+// copy h < 32/M, and lane l (copy h = l / M) reads sub-table (s + l) mod M at step s: 32
+// distinct banks.  Codes are streamed U per thread per step from the list's start, so lane
+// l always holds a position r = l (mod 32) of the list.
+template <int M, int KP, int U>
+__global__ void __launch_bounds__(256)
+    ivf_scan_direct_kernel(const ScanArgs a) {
+  constexpr int THREADS = 256, CAP = 4096, STEP = THREADS * U;
+  using Sel = BlockSelect<THREADS, KP, CAP>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* lut = reinterpret_cast<float*>(smem_raw);  // [256][32]
+  typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(lut + 256 * 32);
+  __shared__ int64_t q_sh;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rot = lane % M, h = lane / M;
+  const int dsub = a.d / M;
+  for (int64_t it = blockIdx.x;; it += gridDim.x) {
+    const int64_t q = next_query(a, it, &q_sh);
+    if (q < 0) break;
+    const int kq = a.kq ? a.kq[q] : a.k;
+    const int npq = a.npq ? min(a.npq[q], a.nprobe) : a.nprobe;
+    const int64_t ob = a.out_off ? a.out_off[q] : q * (int64_t)a.k;
+    __syncthreads();
+    Sel::init(s);
+    __syncthreads();
+    ValueFilter f;
+    f.set(NAN_KEY, false);
+    for (int p = 0; p < npq; p++) {
+      const int64_t L = a.cl_I[q * a.nprobe + p];
+      if (L < 0) continue;  // uniform across the block
+      const int64_t o0 = a.list_off[L], o1 = a.list_off[L + 1];
+      __syncthreads();  // the previous list's look-ups are done
+      // warp w fills rows c of its 32; lane l computes entry (c, m = l mod M) of copy l / M
+      for (int i = 0; i < 32; i++) {
+        const int c = warp * 32 + i, m = rot;
+        const float* C = a.pq + ((int64_t)m * 256 + c) * dsub;
+        float v = 0.f;
+        for (int t = 0; t < dsub; t++) {
+          const float r = a.xq[q * a.d + m * dsub + t] - a.coarse[L * a.d + m * dsub + t];
+          const float e2 = r - C[t];
+          v = fmaf(e2, e2, v);
+        }
+        lut[c * 32 + lane] = v;
+      }
+      __syncthreads();
+      for (int64_t b0 = o0; b0 < o1; b0 += STEP) {
+        uint32_t mask = 0;
+        uint64_t cc[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int64_t i = b0 + u * THREADS + tid;
+          cc[u] = ~0ull;
+          if (i < o1) {
+            uint32_t w[M / 4];
+            load_code<M>(a.codes, i, w);
+            float acc = 0.f;
+#pragma unroll
+            for (int st = 0; st < M; st++) {
+              const uint32_t c = (w[st >> 2] >> ((st & 3) * 8)) & 255u;
+              const int m = (st + rot) & (M - 1);
+              acc += lut[c * 32 + h * M + m];
+            }
+            if (f.pass(acc)) {
+              mask |= 1u << u;
+              cc[u] = composite(ordered_key(acc, false), (uint32_t)i);
+            }
+          }
+        }
+        Sel::template push<U>(s, mask, cc);
+        __syncthreads();
+        if (s.n_buf > CAP - STEP) {
+          Sel::compact(s, kq);
+          f.set((uint32_t)(s.thr >> 32), false);
+        }
+      }
+    }
+    write_results<Sel>(a, s, kq, ob);
+  }
+}
+
+template <int M, int KP, int U>
+static gbk_status launch_scan(const ScanArgs& a, const ScanTuning& tun, cudaStream_t st) {
+  using Sel = BlockSelect<256, KP, 4096>;
+  size_t smem;
+  void (*kern)(const ScanArgs);
+  int threads = 256;
+  if (a.direct) {
+    kern = ivf_scan_direct_kernel<M, KP, U>;
+    smem = sizeof(float) * 256 * 32 + sizeof(typename Sel::Smem);
+  } else {
+    // the selection's shared state does not depend on the block size
+    static_assert(sizeof(typename BlockSelect<512, KP, 4096>::Smem) == sizeof(typename Sel::Smem),
+                  "selection state independent of the block size");
+    // two resident blocks per SM bound the registers: 128 (256 threads, any U), 85 (384
+    // threads, U <= 4), 64 (512 threads, U = 2)
+    if (tun.threads == 512 && U == 2) {
+      kern = ivf_scan_table_kernel<M, KP, 2, 512>;
+      threads = 512;
+    } else if (tun.threads == 384 && U <= 4) {
+      kern = ivf_scan_table_kernel<M, KP, (U <= 4 ? U : 4), 384>;
+      threads = 384;
+    } else {
+      kern = ivf_scan_table_kernel<M, KP, U, 256>;
+    }
+    smem = table_rec_offset<KP>() + sizeof(uint4) * ((size_t)a.nprobe + 1);
+  }
+  GBK_TRY(set_smem_limit(kern, smem));
+  // persistent mode: blocks_per_sm resident blocks per SM pull queries from the counter
+  const int64_t grid =
+      a.counter ? std::min<int64_t>(a.nq, (int64_t)tun.blocks_per_sm * device_info().sm_count)
+                : a.nq;
+  kern<<<(unsigned)grid, threads, smem, st>>>(a);
+  GBK_LAUNCH_CHECK();
+  return GBK_OK;
+}
+
+template <int M, int KP>
+static gbk_status scan_u(const ScanArgs& a, const ScanTuning& tun, cudaStream_t st) {
+  switch (tun.codes_per_thread) {
+    case 2: return launch_scan<M, KP, 2>(a, tun, st);
+    case 4: return launch_scan<M, KP, 4>(a, tun, st);
+    case 8: return launch_scan<M, KP, 8>(a, tun, st);
+    default: return set_error(GBK_EINVAL, "scan tuning: codes per thread must be 2, 4 or 8");
+  }
+}
+
+template <int M>
+gbk_status scan_k(const ScanArgs& a, const ScanTuning& tun, cudaStream_t st) {
+  if (a.k <= 32) return scan_u<M, 32>(a, tun, st);  // a.k = largest k
+  if (a.k <= 128) return scan_u<M, 128>(a, tun, st);
+  if (a.k <= 256) return scan_u<M, 256>(a, tun, st);
+  return scan_u<M, 1024>(a, tun, st);
+}
+
+// one instantiation per code size (ivf_scan_m4.cu ... ivf_scan_m32.cu)
+extern template gbk_status scan_k<4>(const ScanArgs&, const ScanTuning&, cudaStream_t);
+extern template gbk_status scan_k<8>(const ScanArgs&, const ScanTuning&, cudaStream_t);
+extern template gbk_status scan_k<16>(const ScanArgs&, const ScanTuning&, cudaStream_t);
+extern template gbk_status scan_k<32>(const ScanArgs&, const ScanTuning&, cudaStream_t);
+
+}  // namespace gbk

@@ -658,14 +658,7 @@ gbk_status launch_rows(const float* vals, int64_t rows, int64_t len, int k, int 
   constexpr int THREADS = 128;
   using C = KselCfg<THREADS, KP, UNROLL, LARGEST>;
   auto kern = kselect_rows_kernel<THREADS, KP, UNROLL, LARGEST>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)C::SMEM));
-    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                        (int)cudaSharedmemCarveoutMaxShared));
-    attr_set = true;
-  }
+  GBK_TRY(set_smem_limit(kern, C::SMEM, true));
   kern<<<(unsigned)(rows * segs), THREADS, C::SMEM, stream>>>(vals, len, k, segs, seg_len, D, I,
                                                                 part);
   GBK_LAUNCH_CHECK();
@@ -678,12 +671,7 @@ gbk_status launch_ring(const float* vals, int64_t rows, int64_t len, int k, int 
   constexpr int THREADS = 256;
   using C = RingCfg<THREADS, KP>;
   auto kern = kselect_ring_kernel<THREADS, KP, LARGEST>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)C::SMEM));
-    attr_set = true;
-  }
+  GBK_TRY(set_smem_limit(kern, C::SMEM));
   uint32_t* status = device_status();
   if (!status) return set_error(GBK_ECUDA, "device status word unavailable");
   kern<<<(unsigned)(rows * segs), THREADS, C::SMEM, stream>>>(vals, len, k, segs, seg_len, D, I,
@@ -726,12 +714,7 @@ gbk_status launch_merge(const uint64_t* part, int64_t rows, int64_t nper, int k,
   constexpr int THREADS = 256;
   using Sel = BlockSelect<THREADS, KP, 4096>;
   auto kern = kselect_merge_kernel<THREADS, KP>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    GBK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)sizeof(typename Sel::Smem)));
-    attr_set = true;
-  }
+  GBK_TRY(set_smem_limit(kern, sizeof(typename Sel::Smem)));
   kern<<<(unsigned)rows, THREADS, sizeof(typename Sel::Smem), stream>>>(part, nper, k, vals, len,
                                                                          D, I);
   GBK_LAUNCH_CHECK();

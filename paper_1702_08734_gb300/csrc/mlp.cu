@@ -172,6 +172,22 @@ void mm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, f
 
 // Parameter layout (one float array, in this order): W1 [h1][in], b1 [h1], W2 [h2][h1],
 // b2 [h2], W3 [out][h2], b3 [out].
+// Parameter e drawn from U(-bound, bound), bound = 1/sqrt(fan-in) of its layer (W1, b1:
+// n_in; W2, b2: h1; W3, b3: h2), from the 24 high bits of a SplitMix64 hash of (seed, e).
+__global__ void init_uniform_kernel(float* __restrict__ p, int64_t n, int64_t off2, int64_t off4,
+                                    float bound1, float bound2, float bound3, uint64_t seed) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed * 0x9e3779b97f4a7c15ull + (uint64_t)(e + 1) * 0xd1b54a32d192ed03ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    z ^= z >> 31;
+    const float u = (float)(z >> 40) * (1.f / 16777216.f);
+    const float bound = e < off2 ? bound1 : (e < off4 ? bound2 : bound3);
+    p[e] = (2.f * u - 1.f) * bound;
+  }
+}
+
 struct gbk_mlp {
   int n_in, h1, h2, n_out;
   int64_t nparam;
@@ -304,6 +320,23 @@ gbk_status gbk_mlp_create(int32_t n_in, int32_t h1, int32_t h2, int32_t n_out,
   else
     cudaMemset(n->p, 0, b);
   *out = n;
+  return GBK_OK;
+}
+
+gbk_status gbk_mlp_init_uniform(gbk_mlp* n, uint64_t seed, void* stream) {
+  clear_error();
+  GBK_REQUIRE(n, "gbk_mlp_init_uniform: NULL network");
+  cudaStream_t st = as_stream(stream);
+  const int64_t fan[3] = {n->n_in, n->h1, n->h2};
+  init_uniform_kernel<<<grid1(n->nparam), 256, 0, st>>>(n->p, n->nparam, n->off[2], n->off[4],
+                                                        1.f / sqrtf((float)fan[0]),
+                                                        1.f / sqrtf((float)fan[1]),
+                                                        1.f / sqrtf((float)fan[2]), seed);
+  GBK_LAUNCH_CHECK();
+  const size_t b = sizeof(float) * (size_t)n->nparam;
+  GBK_CUDA_CHECK(cudaMemsetAsync(n->m, 0, b, st));
+  GBK_CUDA_CHECK(cudaMemsetAsync(n->v, 0, b, st));
+  n->step = 0;
   return GBK_OK;
 }
 

@@ -235,3 +235,57 @@ def test_orthogonal_rotation_preserves_distances():
     D0 = ((x[:, None].astype(np.float64) - x[None]) ** 2).sum(-1)
     D1 = ((y[:, None].astype(np.float64) - y[None]) ** 2).sum(-1)
     np.testing.assert_allclose(D1, D0, rtol=1e-5, atol=1e-5)
+
+
+def _block_tagged_residuals(M, dsub, n, seed):
+    """Residuals whose sub-block m holds exactly 256 distinct sub-vectors V[m] (tagged by
+    an offset of 100 m, so that a sub-vector read from the wrong block is far from every
+    codeword); rows 0..255 carry V[m][j] in every block m, later rows a seeded choice."""
+    rng = np.random.default_rng(seed)
+    V = (rng.normal(size=(M, 256, dsub)) + 100.0 * np.arange(M)[:, None, None]).astype(np.float32)
+    r = np.empty((n, M * dsub), np.float32)
+    for m in range(M):
+        j = np.concatenate([np.arange(256), rng.integers(0, 256, n - 256)])
+        r[:, m * dsub:(m + 1) * dsub] = V[m][j]
+    return r, V
+
+
+@pytest.mark.parametrize("M,dsub", [(4, 3), (8, 2), (16, 8)])
+def test_train_pq_lossless_books_in_dimension_order(M, dsub):
+    # section 2 "Product quantizer": one 256-centroid codebook per block of d/M consecutive
+    # dimensions.  With exactly 256 distinct sub-vectors per block and every one of them
+    # among the initial rows, Lloyd's iterations keep them: codebook m, row j = V[m][j]
+    # exactly (a strided or shifted slice, or blocks mixed up, lands elsewhere).
+    r, V = _block_tagged_residuals(M, dsub, 3000, 11 + M)
+    books = oracle.train_pq(r, M, np.arange(256), 4)
+    np.testing.assert_array_equal(books, V)
+    # and the codes are lossless: every residual is reconstructed exactly
+    coarse = np.zeros((1, M * dsub), np.float32)
+    _, codes = oracle.ivfpq_encode(r, coarse, books)
+    rec = np.concatenate([books[m][codes[:, m]] for m in range(M)], axis=1)
+    np.testing.assert_array_equal(rec, r)
+
+
+def test_train_pq_follows_a_block_permutation():
+    # permuting whole blocks of dimensions permutes the codebooks the same way
+    M, dsub = 4, 3
+    r, V = _block_tagged_residuals(M, dsub, 2000, 21)
+    perm = [2, 0, 3, 1]
+    rp = np.concatenate([r[:, p * dsub:(p + 1) * dsub] for p in perm], axis=1)
+    books = oracle.train_pq(r, M, np.arange(256), 3)
+    books_p = oracle.train_pq(rp, M, np.arange(256), 3)
+    np.testing.assert_array_equal(books_p, books[perm])
+
+
+def test_residual_training_set_is_offset_from_nearest_centroid():
+    # Eq. 3's residual r = y - q1(y): rows built as centroid j + a small known offset give
+    # that offset (in double) and centroid rows give zero
+    rng = np.random.default_rng(3)
+    cen = (rng.normal(size=(5, 6)) * 50).astype(np.float32)
+    off = (rng.normal(size=(40, 6)) * 0.1).astype(np.float32)
+    j = rng.integers(0, 5, 40)
+    x = (cen[j] + off).astype(np.float32)
+    res = oracle.residual_training_set(x, cen)
+    np.testing.assert_allclose(res, x.astype(np.float64) - cen[j].astype(np.float64), rtol=0,
+                               atol=0)
+    np.testing.assert_array_equal(oracle.residual_training_set(cen, cen), np.zeros((5, 6)))
