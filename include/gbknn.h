@@ -138,12 +138,18 @@ gbk_status gbk_row_norms(const float* x, int64_t n, int32_t d, float* out, void*
 /* Options of gbk_knn_brute (NULL = defaults). */
 typedef struct gbk_knn_opts {
   int32_t precision; /* GBK_PREC_FP32 (default), GBK_PREC_BF16 or GBK_PREC_FP8          */
-  int32_t kprime;    /* BF16/FP8: candidates re-ranked in float32 (0 = 4k for k <= 16, else k + k/4; >= k, <= 1024) */
+  int32_t kprime;    /* BF16/FP8: candidates re-ranked in float32 (0 = 4k for k <= 16,   */
+                     /* k + k/4 above; >= k, <= 1024)                                  */
   int32_t chunks;    /* database chunks of the work decomposition (0 = planned)          */
   int32_t* certified; /* BF16/FP8, optional device [nq]: 1 if the result provably equals
-                         the float32 top-k (see gbk_knn_brute), else 0                  */
+                         the float32 top-k (see gbk_knn_brute), 2 if it was re-run on the
+                         float32 path (exact != 0), else 0                             */
   float* error_bound; /* BF16/FP8, optional device [nq]: bound on |low-precision - float32|
                          distance used by the certificate                              */
+  int32_t exact;      /* BF16/FP8: nonzero re-runs every query the certificate does not
+                         cover on the float32 path and returns its result there, so every
+                         row is the float32 top-k (the call then synchronises `stream`
+                         once, to learn how many queries to re-run)                     */
 } gbk_knn_opts;
 
 /*
@@ -257,7 +263,8 @@ gbk_status gbk_ivfpq_export(gbk_index* index, float* coarse, float* pq, int64_t*
 
 /* Checkpoint of an index to a file and back (section 2's inverted file with its
  * quantizers; the paper does not specify a format).  gbk_ivfpq_save writes a header
- * (sizes, table mode, coarse precision, kept vectors, rotation, scan tuning) followed by
+ * (sizes, table mode, coarse precision, kept vectors, rotation, scan tuning, learned-nprobe
+ * operating point) followed by
  * the coarse centroids, the codebooks, the rotation, the list offsets, the codes (byte m =
  * sub-quantizer m), the ids and the kept vectors, all in list order; it synchronises
  * `stream`.  gbk_ivfpq_load reads such a file into a new index (*out; destroy with
@@ -289,6 +296,14 @@ gbk_status gbk_ivfpq_rotate(gbk_index* index, const float* x, int64_t n, float* 
  * exact nearest ones unless a true one fell outside the over-fetch, and term 2 is exact.
  * Adding (q1 assignment) always uses float32. */
 gbk_status gbk_ivfpq_set_coarse_precision(gbk_index* index, int32_t precision);
+
+/* Operating point of the learned nprobe (not part of the paper).  The network's class of a
+ * query is its argmax (alpha = 0, default) or, with alpha in (0, 1], the smallest class
+ * whose cumulative softmax probability reaches alpha (a confidence level: larger alpha
+ * probes more lists where the network is unsure); class c probes
+ * min(2^max(c + shift, 0), max_nprobe) lists, shift 0 (default) being the trained rule.
+ * GBK_EINVAL for alpha outside [0, 1] or shift outside [-16, 16]. */
+gbk_status gbk_ivfpq_set_learned_route(gbk_index* index, float alpha, int32_t shift);
 
 /* Keep a float32 copy of every vector added from now on (n*d*4 bytes of device memory in
  * list order, plus the same again as staging until the next search rebuilds the lists),
@@ -517,7 +532,7 @@ gbk_status gbk_ivfpq_get_tuning(const gbk_index* index, int32_t* codes_per_threa
 
 /* Further scan options (results never depend on them; not part of the paper):
  * threads_per_block of the precomputed-table scan, 256, 384 (default; applies with 2 or 4
- * codes per thread) or 512 (with 2 codes per thread); by_list != 0 (default) makes gbk_ivfpq_search hand queries to
+ * codes per thread) or 512 (with 2 codes per thread); by_list != 0 (default 0) makes gbk_ivfpq_search hand queries to
  * the scan in the order of their nearest inverted list, so that queries probing the same
  * lists are scanned at the same time and share those lists' codes in L2 (section 5.3 reads
  * each probed list once per query), 0 scans them in input order, one block per query.

@@ -152,7 +152,7 @@ PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
 class KnnOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("kprime", ctypes.c_int32),
                 ("chunks", ctypes.c_int32), ("certified", ctypes.c_void_p),
-                ("error_bound", ctypes.c_void_p)]
+                ("error_bound", ctypes.c_void_p), ("exact", ctypes.c_int32)]
 
 
 def _metric(m):
@@ -160,11 +160,14 @@ def _metric(m):
 
 
 def knn_brute(xq: torch.Tensor, xb: torch.Tensor, k: int, metric="l2", precision="fp32",
-              kprime: int = 0, chunks: int = 0, out=None, certify: bool = False):
+              kprime: int = 0, chunks: int = 0, out=None, certify: bool = False,
+              exact: bool = False):
     """Exact k-NN (squared L2 ascending, or inner product descending) with int64 ids.
 
     precision "bf16"/"fp8": over-fetch kprime candidates, exact float32 re-rank; with
-    certify=True also returns (certified [nq] int32, error_bound [nq] float32)."""
+    certify=True also returns (certified [nq] int32, error_bound [nq] float32); with
+    exact=True the queries the certificate does not cover are re-run in float32
+    (certified = 2 for them)."""
     _dev(xq, torch.float32, "xq")
     _dev(xb, torch.float32, "xb")
     nq, d = xq.shape
@@ -182,7 +185,7 @@ def knn_brute(xq: torch.Tensor, xb: torch.Tensor, k: int, metric="l2", precision
         eb = torch.empty(nq, dtype=torch.float32, device=xq.device)
     opts = KnnOpts(PRECISIONS[precision], int(kprime), int(chunks),
                    cert.data_ptr() if cert is not None else None,
-                   eb.data_ptr() if eb is not None else None)
+                   eb.data_ptr() if eb is not None else None, int(bool(exact)))
     _call("gbk_knn_brute", _ptr(xq), nq, _ptr(xb), nb, int(d), int(k), _metric(metric), _ptr(D),
           _ptr(I), ctypes.byref(opts), _stream())
     return (D, I, cert, eb) if certify else (D, I)
@@ -611,6 +614,7 @@ _SIGNATURES.update({
     "gbk_ivfpq_set_tuning": [_vp, _i32, _i32],
     "gbk_ivfpq_get_tuning": [_vp, _vp, _vp],
     "gbk_ivfpq_set_scan_options": [_vp, _i32, _i32],
+    "gbk_ivfpq_set_learned_route": [_vp, ctypes.c_float, _i32],
     "gbk_ivfpq_autotune": [_vp, _vp, _i64, _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _i32, _vp,
                            _vp],
 })
@@ -632,7 +636,13 @@ def ivfpq_set_tuning(index, codes_per_thread: int, blocks_per_sm: int):
     _call("gbk_ivfpq_set_tuning", index._h, int(codes_per_thread), int(blocks_per_sm))
 
 
-def ivfpq_set_scan_options(index, threads: int = 256, by_list: bool = True):
+def ivfpq_set_learned_route(index, alpha: float = 0.0, shift: int = 0):
+    """Learned nprobe operating point: class = argmax (alpha 0) or the smallest class of
+    cumulative probability >= alpha; class c probes 2^max(c + shift, 0) lists."""
+    _call("gbk_ivfpq_set_learned_route", index._h, float(alpha), int(shift))
+
+
+def ivfpq_set_scan_options(index, threads: int = 384, by_list: bool = False):
     """Table-mode scan block size (256 or 512) and whether a plain search scans its queries
     in the order of their nearest list (True) or as given."""
     _call("gbk_ivfpq_set_scan_options", index._h, int(threads), int(bool(by_list)))

@@ -254,6 +254,7 @@ gbk_status gbk_knn_brute(const float* xq, int64_t nq, const float* xb, int64_t n
     plan.kprime = opts->kprime;
     plan.certified = opts->certified;
     plan.error_bound = opts->error_bound;
+    plan.exact = opts->exact != 0;
   }
   return knn_run(xq, nq, xb, nb, d, k, metric, D, I, plan, as_stream(stream));
 }

@@ -8,6 +8,7 @@
 #include "dist_gemm.cuh"
 #include "dist_gemm_launch.cuh"
 #include "dist_gemm_kernel.cuh"
+#include "ivf.cuh"
 #include "kselect.cuh"
 #include "knn.cuh"
 
@@ -536,6 +537,25 @@ static gbk_status select_run(const float* xq, const PreparedOperand& Q, const Pr
   return knn_merge(a.part, nq, lists, a.kp, k, ip ? nullptr : Q.norms.as<float>(), ip, D, I, st);
 }
 
+// idx[0 .. *cnt) = the queries with certified[q] == 0 (in no particular order)
+__global__ void uncertified_kernel(const int32_t* __restrict__ certified, int64_t nq,
+                                   int64_t* __restrict__ idx, int32_t* __restrict__ cnt) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nq && certified[q] == 0) idx[atomicAdd(cnt, 1)] = q;
+}
+
+// rows j of (Du, Iu) replace rows idx[j] of (D, I); certified[idx[j]] = 2
+__global__ void scatter_rows_kernel(const float* __restrict__ Du, const int64_t* __restrict__ Iu,
+                                    const int64_t* __restrict__ idx, int k, float* __restrict__ D,
+                                    int64_t* __restrict__ I, int32_t* __restrict__ certified) {
+  const int64_t j = blockIdx.x, q = idx[j];
+  for (int t = threadIdx.x; t < k; t += blockDim.x) {
+    D[q * k + t] = Du[j * k + t];
+    I[q * k + t] = Iu[j * k + t];
+  }
+  if (threadIdx.x == 0) certified[q] = 2;
+}
+
 gbk_status knn_run(const float* xq, int64_t nq, const float* xb, int64_t nb, int d, int k,
                    int metric, float* D, int64_t* I, const KnnPlan& plan, cudaStream_t st) {
   if (nq == 0) return GBK_OK;
@@ -548,22 +568,58 @@ gbk_status knn_run(const float* xq, int64_t nq, const float* xb, int64_t nb, int
       GBK_OK)
     return r;
   if (plan.prec == GBK_PREC_FP32) return select_run(xq, Q, B, nq, nb, d, k, ip, plan.chunks, D, I, st);
-  // low precision: over-fetch k' candidates, then exact float32 re-rank + certificate
-  // default over-fetch: 4k for k <= 16, k + k/4 above (the low-precision error moves a
-  // neighbour by few ranks once k is large).  Not rounded up to the lists' power-of-two
-  // length: a larger k' loosens the selection threshold and costs candidate pushes.
+  // low precision: over-fetch k' candidates, then the exact float32 re-rank + certificate.
+  // Default k' = 4k for k <= 16 and k + k/4 above: longer candidate lists slow the fused
+  // selection far more than the certificate gains (10^4 x 10^6 x 128, k = 100, BF16:
+  // k' = 400 certifies every query but takes 100 ms, k' = 125 takes 14 ms and leaves the
+  // queries to the float32 repair).  Not rounded up to the lists' power-of-two length: a
+  // larger k' loosens the selection threshold and costs candidate pushes.
   int kp = plan.kprime > 0 ? plan.kprime : (k <= 16 ? 4 * k : k + k / 4);
   kp = std::min(kp, GBK_MAX_K);
   kp = (int)std::min<int64_t>(std::max(kp, k), nb);
-  Scratch Dc, Ic;
+  Scratch Dc, Ic, cert;
   if ((r = Dc.alloc(sizeof(float) * (size_t)nq * kp, st)) != GBK_OK) return r;
   if ((r = Ic.alloc(sizeof(int64_t) * (size_t)nq * kp, st)) != GBK_OK) return r;
+  int32_t* cp = plan.certified;
+  if (plan.exact && !cp) {
+    if ((r = cert.alloc(sizeof(int32_t) * (size_t)nq, st)) != GBK_OK) return r;
+    cp = cert.as<int32_t>();
+  }
   if ((r = select_run(xq, Q, B, nq, nb, d, kp, ip, plan.chunks, Dc.as<float>(), Ic.as<int64_t>(),
                       st)) != GBK_OK)
     return r;
-  return rerank_run(xq, xb, nq, nb, d, kp, k, ip, plan.prec, Q.norms.as<float>(),
-                    Q.scale.as<float>(), B.norms.as<float>(), B.scale.as<float>(),
-                    Ic.as<int64_t>(), Dc.as<float>(), D, I, plan.certified, plan.error_bound, st);
+  if ((r = rerank_run(xq, xb, nq, nb, d, kp, k, ip, plan.prec, Q.norms.as<float>(),
+                      Q.scale.as<float>(), B.norms.as<float>(), B.scale.as<float>(),
+                      Ic.as<int64_t>(), Dc.as<float>(), D, I, cp, plan.error_bound, st)) != GBK_OK)
+    return r;
+  if (!plan.exact) return GBK_OK;
+  // queries the certificate does not cover: searched again on the float32 path, whose
+  // results replace theirs (certified = 2)
+  Scratch cnt, idx;
+  if ((r = cnt.alloc(sizeof(int32_t), st)) != GBK_OK) return r;
+  if ((r = idx.alloc(sizeof(int64_t) * (size_t)nq, st)) != GBK_OK) return r;
+  GBK_CUDA_CHECK(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t), st));
+  uncertified_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(cp, nq, idx.as<int64_t>(),
+                                                                   cnt.as<int32_t>());
+  GBK_LAUNCH_CHECK();
+  int32_t nu = 0;
+  GBK_CUDA_CHECK(cudaMemcpyAsync(&nu, cnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  GBK_CUDA_CHECK(cudaStreamSynchronize(st));
+  if (nu == 0) return GBK_OK;
+  Scratch Xu, Du, Iu;
+  if ((r = Xu.alloc(sizeof(float) * (size_t)nu * d, st)) != GBK_OK) return r;
+  if ((r = Du.alloc(sizeof(float) * (size_t)nu * k, st)) != GBK_OK) return r;
+  if ((r = Iu.alloc(sizeof(int64_t) * (size_t)nu * k, st)) != GBK_OK) return r;
+  if ((r = gather_rows_run(xq, idx.as<int64_t>(), nu, d, Xu.as<float>(), st)) != GBK_OK) return r;
+  KnnPlan p32;
+  p32.chunks = plan.chunks;
+  if ((r = knn_run(Xu.as<float>(), nu, xb, nb, d, k, metric, Du.as<float>(), Iu.as<int64_t>(),
+                   p32, st)) != GBK_OK)
+    return r;
+  scatter_rows_kernel<<<(unsigned)nu, 128, 0, st>>>(Du.as<float>(), Iu.as<int64_t>(),
+                                                    idx.as<int64_t>(), k, D, I, cp);
+  GBK_LAUNCH_CHECK();
+  return GBK_OK;
 }
 
 }  // namespace gbk

@@ -338,6 +338,16 @@ gbk_status gbk_ivfpq_set_coarse_precision(gbk_index* ix, int32_t precision) {
   return GBK_OK;
 }
 
+gbk_status gbk_ivfpq_set_learned_route(gbk_index* ix, float alpha, int32_t shift) {
+  clear_error();
+  GBK_REQUIRE(ix, "gbk_ivfpq_set_learned_route: NULL index");
+  GBK_REQUIRE(shift >= -16 && shift <= 16, "gbk_ivfpq_set_learned_route: shift out of [-16, 16]");
+  GBK_REQUIRE(alpha >= 0.f && alpha <= 1.f, "gbk_ivfpq_set_learned_route: alpha out of [0, 1]");
+  ix->class_shift = shift;
+  ix->route_alpha = alpha;
+  return GBK_OK;
+}
+
 gbk_status gbk_ivfpq_keep_vectors(gbk_index* ix, int32_t keep) {
   clear_error();
   GBK_REQUIRE(ix, "gbk_ivfpq_keep_vectors: NULL index");
@@ -556,7 +566,8 @@ struct FileHeader {
   char magic[8];
   uint32_t version;
   int32_t d, nlist, M, nbits, use_precomputed, coarse_prec, keep_vectors, rotated;
-  int32_t codes_per_thread, blocks_per_sm, list_order, scan_threads;
+  int32_t codes_per_thread, blocks_per_sm, list_order, scan_threads, class_shift;
+  float route_alpha;
   int64_t ntotal;
   int64_t reserved[4];
 };
@@ -636,6 +647,8 @@ gbk_status gbk_ivfpq_save(gbk_index* ix, const char* path, void* stream) {
   h.blocks_per_sm = ix->tuning.blocks_per_sm;
   h.list_order = ix->tuning.list_order;
   h.scan_threads = ix->tuning.threads;
+  h.class_shift = ix->class_shift;
+  h.route_alpha = ix->route_alpha;
   h.ntotal = ix->ntotal;
   if (std::fwrite(&h, sizeof(h), 1, file.f) != 1)
     return set_error(GBK_EINVAL, "gbk_ivfpq_save: write failed");
@@ -684,7 +697,9 @@ gbk_status gbk_ivfpq_load(const char* path, gbk_index** out, void* stream) {
   GBK_REQUIRE(h.coarse_prec >= GBK_PREC_FP32 && h.coarse_prec <= GBK_PREC_FP8 &&
                   (h.codes_per_thread == 2 || h.codes_per_thread == 4 || h.codes_per_thread == 8) &&
                   h.blocks_per_sm >= 1 && h.blocks_per_sm <= 8 &&
-                  (h.scan_threads == 256 || h.scan_threads == 384 || h.scan_threads == 512),
+                  (h.scan_threads == 256 || h.scan_threads == 384 || h.scan_threads == 512) &&
+                  h.class_shift >= -16 && h.class_shift <= 16 && h.route_alpha >= 0.f &&
+                  h.route_alpha <= 1.f,
               "gbk_ivfpq_load: bad settings in the header");
   const int64_t n = h.ntotal;
   ix->use_precomputed = h.use_precomputed ? 1 : 0;
@@ -694,6 +709,8 @@ gbk_status gbk_ivfpq_load(const char* path, gbk_index** out, void* stream) {
   ix->tuning.blocks_per_sm = h.blocks_per_sm;
   ix->tuning.list_order = h.list_order ? 1 : 0;
   ix->tuning.threads = h.scan_threads;
+  ix->class_shift = h.class_shift;
+  ix->route_alpha = h.route_alpha;
   DevBuf off;
   if ((r = read_block(file.f, ix->coarse, sizeof(float) * (size_t)h.nlist * h.d, st)) ||
       (r = read_block(file.f, ix->pq, sizeof(float) * (size_t)h.M * 256 * (h.d / h.M), st)) ||
@@ -773,9 +790,9 @@ __global__ void nprobe_features_kernel(const float* __restrict__ xq, int64_t nq,
 
 // nprobe of each query from the class chosen by the network: class c -> 2^c, capped.
 __global__ void class_to_nprobe_kernel(const int32_t* __restrict__ cls, int64_t nq, int cap,
-                                       int32_t* __restrict__ np) {
+                                       int shift, int32_t* __restrict__ np) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < nq) np[q] = min(1 << min(cls[q], 30), cap);
+  if (q < nq) np[q] = min(1 << min(max(cls[q] + shift, 0), 30), cap);
 }
 
 __global__ void recall_counts_kernel(const int64_t* __restrict__ I, const int64_t* __restrict__ G,
@@ -836,9 +853,11 @@ gbk_status batched_run(gbk_index* ix, const float* xq_in, int64_t nq, const int3
     if ((r = nprobe_features_run(xq, nq, ix->d, clD.as<float>(), tau, std::min(nfeat, tau),
                                  F.as<float>(), st)) != GBK_OK)
       return r;
-    if ((r = mlp_forward_classes(mlp, F.as<float>(), nq, cls.as<int32_t>(), st)) != GBK_OK) return r;
+    if ((r = mlp_forward_classes(mlp, F.as<float>(), nq, cls.as<int32_t>(), st,
+                                 ix->route_alpha)) != GBK_OK)
+      return r;
     class_to_nprobe_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(
-        cls.as<int32_t>(), nq, max_nprobe, npq_s.as<int32_t>());
+        cls.as<int32_t>(), nq, max_nprobe, ix->class_shift, npq_s.as<int32_t>());
     GBK_LAUNCH_CHECK();
     npq = npq_s.as<int32_t>();
   }

@@ -58,7 +58,7 @@ struct DevBuf {
 struct ScanTuning {
   int codes_per_thread = 2;
   int blocks_per_sm = 2;
-  int list_order = 1;  // plain search: queries in the order of their nearest list
+  int list_order = 0;  // plain search: queries in the order of their nearest list (1)
   int threads = 384;   // table-mode scan block size: 256, 384 (U <= 4) or 512 (U = 2)
 };
 

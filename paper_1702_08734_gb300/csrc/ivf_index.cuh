@@ -28,6 +28,10 @@ struct gbk_index {
   // arithmetic of the coarse search of queries (Eq. 5); low precision over-fetches and
   // re-ranks the candidate lists in float32, so term 2 stays exact
   int coarse_prec = GBK_PREC_FP32;
+  // learned nprobe: the network's class c (argmax, or with route_alpha > 0 the smallest
+  // class of cumulative probability >= route_alpha) probes 2^max(c + class_shift, 0) lists
+  int class_shift = 0;
+  float route_alpha = 0.f;
   int64_t ntotal = 0;
   bool dirty = true;
   int64_t max_list = 0;
@@ -75,8 +79,10 @@ gbk_status batched_run(gbk_index* ix, const float* xq, int64_t nq, const int32_t
 // Network inputs / outputs and argmax classes of a forward pass (mlp.cu).
 int mlp_inputs(const gbk_mlp* n);
 int mlp_outputs(const gbk_mlp* n);
+// alpha > 0: the smallest class whose cumulative softmax probability reaches alpha;
+// otherwise the argmax (ties to the lower class).
 gbk_status mlp_forward_classes(gbk_mlp* net, const float* X, int64_t B, int32_t* cls,
-                               cudaStream_t st);
+                               cudaStream_t st, float alpha = 0.f);
 
 // Learned-nprobe features of Eq. 5's nearest coarse distances (ivf.cu):
 // F[q] = [x_q, d_i / max(d_0, 1e-12) - 1 for i < nfeat]

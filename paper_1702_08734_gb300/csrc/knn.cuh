@@ -24,6 +24,7 @@ struct KnnPlan {
   int kprime = 0;  // low precision: re-ranked candidates (0 = 4k)
   int32_t* certified = nullptr;  // low precision: [nq] 1 if provably the float32 top-k
   float* error_bound = nullptr;  // low precision: [nq] bound on |low - exact| distance
+  bool exact = false;            // low precision: re-run uncertified queries in float32
 };
 
 gbk_status prepare_operand(const float* x, int64_t n, int d, int prec, int64_t nrows_pad,

@@ -82,6 +82,26 @@ __global__ void argmax_kernel(const float* __restrict__ z, int64_t B, int C, int
   cls[r] = best;
 }
 
+// Smallest class whose softmax cumulative probability reaches alpha (classes ordered by
+// cost, as the nprobe classes are): a confidence level for routing instead of the argmax.
+__global__ void quantile_class_kernel(const float* __restrict__ z, int64_t B, int C, float alpha,
+                                      int32_t* __restrict__ cls) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= B) return;
+  const float* zr = z + r * C;
+  float mx = zr[0];
+  for (int c = 1; c < C; c++) mx = fmaxf(mx, zr[c]);
+  float se = 0.f;
+  for (int c = 0; c < C; c++) se += expf(zr[c] - mx);
+  float cum = 0.f;
+  int c = 0;
+  for (; c < C - 1; c++) {
+    cum += expf(zr[c] - mx) / se;
+    if (cum >= alpha) break;
+  }
+  cls[r] = c;
+}
+
 __global__ void loss_sum_kernel(const float* __restrict__ lr, int64_t B, float* __restrict__ out) {
   // single block, fixed order: per-thread strided partials then a tree
   __shared__ float part[256];
@@ -272,7 +292,7 @@ int mlp_inputs(const gbk_mlp* n) { return n ? n->n_in : 0; }
 int mlp_outputs(const gbk_mlp* n) { return n ? n->n_out : 0; }
 
 gbk_status mlp_forward_classes(gbk_mlp* n, const float* X, int64_t B, int32_t* cls,
-                               cudaStream_t st) {
+                               cudaStream_t st, float alpha) {
   ProfScope prof("mlp_forward", st);
   gbk_status r;
   Scratch sh1, sh2, sz;
@@ -281,7 +301,11 @@ gbk_status mlp_forward_classes(gbk_mlp* n, const float* X, int64_t B, int32_t* c
   if ((r = sz.alloc(sizeof(float) * B * n->n_out, st)) != GBK_OK) return r;
   if ((r = mlp_forward(n, X, B, sh1.as<float>(), sh2.as<float>(), sz.as<float>(), st)) != GBK_OK)
     return r;
-  argmax_kernel<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(sz.as<float>(), B, n->n_out, cls);
+  if (alpha > 0.f)
+    quantile_class_kernel<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(sz.as<float>(), B, n->n_out,
+                                                                       alpha, cls);
+  else
+    argmax_kernel<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(sz.as<float>(), B, n->n_out, cls);
   GBK_LAUNCH_CHECK();
   return GBK_OK;
 }

@@ -217,24 +217,31 @@ def test_batched_mixed_matches_oracle(gbk, precomputed):
     assert torch.equal(gr.D, D) and torch.equal(gr.I, I)
 
 
-def test_learned_routing_matches_oracle(gbk):
-    # nprobe chosen per query by a (seeded, untrained) network: each query's results equal
-    # the oracle's search at the nprobe the network chose
+@pytest.mark.parametrize("alpha,shift", [(0.0, 0), (0.9, 1)])
+def test_learned_routing_matches_oracle(gbk, alpha, shift):
+    # nprobe chosen per query by a (seeded, untrained) network at an operating point: each
+    # query's results equal the oracle's search at the nprobe the network chose
     ix, x, cen, coarse, books = _index(gbk, 128, True, nlist=64)  # 64 coarse features
     nq = 200
     xq = _queries(cen, 450, nq, 128)
     xqt = torch.from_numpy(xq).cuda()
     net = gbk.MLP(128 + 64, 256, 256, 9, seed=451)
     kq = np.full(nq, 10, np.int32)
+    gbk.ivfpq_set_learned_route(ix, 0.0, 0)
+    _, _, _, used0 = gbk.ivfpq_search_batched(ix, xqt, torch.from_numpy(kq).cuda(), 10, None, 32,
+                                              mlp=net)
+    gbk.ivfpq_set_learned_route(ix, alpha, shift)
     D, I, off, used = gbk.ivfpq_search_batched(ix, xqt, torch.from_numpy(kq).cuda(), 10, None, 32,
                                                mlp=net)
     u = used.cpu().numpy()
     assert np.all((u >= 1) & (u <= 32) & ((u & (u - 1)) == 0))
+    assert np.all(u >= used0.cpu().numpy())  # a higher confidence or shift never probes fewer
     _check_batched(D, I, off, kq, u, xq, ix, coarse, books, False)
     gr = gbk.BatchedGraph(ix, xqt, torch.from_numpy(kq).cuda(), 10, None, 32, mlp=net)
     gr.launch()
     torch.cuda.synchronize()
     assert torch.equal(gr.I, I) and torch.equal(gr.nprobe_used, used)
+    gbk.ivfpq_set_learned_route(ix, 0.0, 0)
 
 
 def _pq_structured(seed, n, d, M, ncoarse):
