@@ -80,6 +80,14 @@ int32_t gbk_profile_read(char* names, float* ms, int32_t max_records);
  * skipped its remaining work; its outputs are undefined), GBK_EDEVICE for other flags. */
 gbk_status gbk_device_status(void* stream);
 
+/* Self-test of that path (not part of the paper): launches one thread that waits on a
+ * shared-memory mbarrier nobody arrives at, bounded by limit_ns (1 us .. 2 s) of GPU
+ * time, as every mbarrier wait of the library is bounded.  The wait gives up, sets the
+ * timeout flag of the status word and the kernel returns: the next gbk_device_status on
+ * that stream reports GBK_ETIMEOUT, and the context stays usable.  GBK_EINVAL for a limit
+ * outside that range. */
+gbk_status gbk_selftest_wait_timeout(int64_t limit_ns, void* stream);
+
 /*
  * Row-wise k-selection (section 2, "k-selection"; batched over rows as in "Batching").
  *   vals    [rows][len] float32 input

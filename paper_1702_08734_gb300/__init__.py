@@ -42,6 +42,7 @@ _SIGNATURES = {
     "gbk_kselect_ex": [_vp, _i64, _i64, _i32, _i32, _vp, _vp, _vp, _vp],
     "gbk_row_norms": [_vp, _i64, _i32, _vp, _vp],
     "gbk_device_status": [_vp],
+    "gbk_selftest_wait_timeout": [_i64, _vp],
     "gbk_knn_brute": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
     "gbk_pairwise_distances": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _vp, _i64, _vp],
 }
@@ -110,6 +111,55 @@ class KselectOpts(ctypes.Structure):
 def device_status():
     """Synchronise the current stream and raise if a kernel flagged an error."""
     _call("gbk_device_status", _stream())
+
+
+def selftest_wait_timeout(limit_ns: int = 1000000):
+    """Launch the bounded-wait self-test: the next device_status() raises GBK_ETIMEOUT."""
+    _call("gbk_selftest_wait_timeout", int(limit_ns), _stream())
+
+
+_ALLOC_CB = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_CB = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("alloc", _ALLOC_CB), ("free", _FREE_CB)]
+
+
+_installed_allocator = None
+
+
+def set_allocator(alloc=None, free=None):
+    """Install alloc(nbytes, stream) -> device pointer (int; 0 = failure) and
+    free(ptr, stream) as the library's scratch allocator; alloc=None restores the default
+    (cudaMallocAsync on the call's stream)."""
+    global _installed_allocator
+    lib = load()
+    lib.gbk_set_allocator.argtypes = [ctypes.c_void_p]
+    if alloc is None:
+        _call("gbk_set_allocator", None)
+        _installed_allocator = None
+        return
+
+    def a(ctx, n, st):
+        try:
+            return int(alloc(int(n), st) or 0) or None
+        except Exception:
+            return None
+
+    def f(ctx, p, st):
+        if free is not None and p:
+            free(int(p), st)
+
+    cb = _Allocator(None, _ALLOC_CB(a), _FREE_CB(f))
+    _call("gbk_set_allocator", ctypes.cast(ctypes.pointer(cb), ctypes.c_void_p))
+    _installed_allocator = cb  # keeps the callbacks alive
+
+
+def use_torch_allocator():
+    """Scratch memory from PyTorch's caching allocator (on the current stream)."""
+    set_allocator(lambda n, st: torch.cuda.caching_allocator_alloc(n),
+                  lambda p, st: torch.cuda.caching_allocator_delete(p))
 
 
 def kselect(vals: torch.Tensor, k: int, largest: bool = False, out=None, segments: int = 0,
