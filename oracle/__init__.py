@@ -20,6 +20,8 @@ marshals numpy arrays.  Functions and the passages they follow:
   the probed lists, then Eq. (1) directly for their vectors
 * ``ivfadc_refine`` - Algorithm 4 for k' candidates, then Eq. (1) for those and the k best
 * ``rotate``        - the OPQ pre-rotation y -> R y (sections 1 and 6.4), in double
+* ``procrustes``    - the orthogonal R minimising ||x R^T - y||_F (numpy SVD)
+* ``opq_train``     - non-parametric OPQ: alternating ``train_pq`` and ``procrustes``
 """
 from __future__ import annotations
 
@@ -278,3 +280,29 @@ def rotate(x, R):
     x = np.asarray(x, dtype=np.float64)
     R = np.asarray(R, dtype=np.float64)
     return (x @ R.T).astype(np.float32)
+
+
+def procrustes(x, y):
+    """The orthogonal R minimising ||x R^T - y||_F over the rows: U V^T for the SVD
+    y^T x = U S V^T, in double (the library routine numpy.linalg.svd as the step)."""
+    A = np.asarray(y, np.float64).T @ np.asarray(x, np.float64)
+    U, _, Vt = np.linalg.svd(A)
+    return U @ Vt
+
+
+def opq_train(x, M: int, init_idx, niter: int, pq_niter: int, threads: int = 0):
+    """OPQ, non-parametric form (cited, not specified, by the paper): from R = I, niter
+    times train the product quantizer of x R^T (train_pq from the rows init_idx), encode
+    and reconstruct every row, and replace R by procrustes(x, reconstruction).  Returns
+    (R float32 [d][d], the last codebooks)."""
+    x = _c(x, np.float32)
+    n, d = x.shape
+    R = np.eye(d)
+    books = None
+    for _ in range(niter):
+        xr = rotate(x, R)
+        books = train_pq(xr, M, init_idx, pq_niter, threads)
+        _, codes = ivfpq_encode(xr, np.zeros((1, d), np.float32), books, threads)
+        y = np.concatenate([books[m][codes[:, m]] for m in range(M)], axis=1)
+        R = procrustes(x, y)
+    return R.astype(np.float32), books

@@ -322,6 +322,11 @@ class TrainOpts(ctypes.Structure):
                 ("use_precomputed", ctypes.c_int32)]
 
 
+class OpqOpts(ctypes.Structure):
+    _fields_ = [("niter", ctypes.c_int32), ("pq_niter", ctypes.c_int32),
+                ("polar_iters", ctypes.c_int32), ("pq_init", ctypes.c_void_p)]
+
+
 class IVFPQIndex:
     """IVFADC index on the GPU (coarse quantizer + 8-bit product quantizer, inverted lists)."""
 
@@ -383,6 +388,19 @@ class IVFPQIndex:
             _dev(R, torch.float32, "R")
         _call("gbk_ivfpq_set_rotation", self._h, _ptr(R), _stream())
         return self
+
+    def train_rotation(self, x: torch.Tensor, niter: int = 10, pq_niter: int = 4, pq_init=None,
+                       polar_iters: int = 40):
+        """Train the OPQ rotation on x (before train/add) and install it; returns R [d][d]."""
+        _dev(x, torch.float32, "x")
+        pi = pip = None
+        if pq_init is not None:
+            pi, pip = _host_i64(pq_init)
+        o = OpqOpts(int(niter), int(pq_niter), int(polar_iters), pip)
+        R = torch.empty((self.d, self.d), dtype=torch.float32, device=x.device)
+        _call("gbk_ivfpq_train_rotation", self._h, _ptr(x), x.shape[0], ctypes.byref(o), _ptr(R),
+              _stream())
+        return R
 
     def rotate(self, x: torch.Tensor):
         """x rotated by the index's R (the space of its quantizers)."""
@@ -645,6 +663,7 @@ def nprobe_mlp_train(index, net, xq, labels=None, gt=None, **opts):
 _SIGNATURES.update({
     "gbk_mlp_init_uniform": [_vp, ctypes.c_uint64, _vp],
     "gbk_ivfpq_save": [_vp, ctypes.c_char_p, _vp],
+    "gbk_ivfpq_train_rotation": [_vp, _vp, _i64, _vp, _vp, _vp],
     "gbk_ivfpq_load": [ctypes.c_char_p, _vp, _vp],
     "gbk_nprobe_labels": [_vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp, _vp],
     "gbk_nprobe_mlp_train": [_vp, _vp, _vp, _i64, _vp, _vp, _i32, _vp, _vp, _vp],

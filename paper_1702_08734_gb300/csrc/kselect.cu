@@ -297,9 +297,10 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
   Sel::finish(s, k);
   if (segs == 1) {
     for (int j = tid; j < k; j += THREADS) {
-      const uint32_t idx = (uint32_t)s.top[j];
+      const uint64_t e = s.top[j];
+      const uint32_t idx = (uint32_t)e;
       if (idx < (uint32_t)len) {
-        outD[row * k + j] = rowp[idx];
+        outD[row * k + j] = selected_value(e, LARGEST, rowp);
         outI[row * k + j] = (int64_t)idx;
       }
     }
@@ -521,9 +522,10 @@ __global__ void __launch_bounds__(THREADS, 2)
   Sel::finish(s, k);
   if (segs == 1) {
     for (int j = tid; j < k; j += THREADS) {
-      const uint32_t idx = (uint32_t)s.top[j];
+      const uint64_t e = s.top[j];
+      const uint32_t idx = (uint32_t)e;
       if (idx < (uint32_t)len) {
-        outD[row * k + j] = rowp[idx];
+        outD[row * k + j] = selected_value(e, LARGEST, rowp);
         outI[row * k + j] = (int64_t)idx;
       }
     }
@@ -600,7 +602,7 @@ __global__ void __launch_bounds__(THREADS)
     if (tid == 0) {
       if (segs == 1) {
         const uint32_t idx = (uint32_t)best;
-        outD[row] = rowp[idx];
+        outD[row] = selected_value(best, LARGEST, rowp);
         outI[row] = (int64_t)idx;
       } else {
         part[row * segs + seg] = best;
@@ -613,8 +615,8 @@ __global__ void __launch_bounds__(THREADS)
 template <int THREADS, int KP>
 __global__ void __launch_bounds__(THREADS)
     kselect_merge_kernel(const uint64_t* __restrict__ part, int64_t nper, int k,
-                         const float* __restrict__ vals, int64_t len, float* __restrict__ outD,
-                         int64_t* __restrict__ outI) {
+                         const float* __restrict__ vals, int64_t len, int largest,
+                         float* __restrict__ outD, int64_t* __restrict__ outI) {
   constexpr int CAP = 4096;
   using Sel = BlockSelect<THREADS, KP, CAP>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -644,7 +646,7 @@ __global__ void __launch_bounds__(THREADS)
   for (int j = threadIdx.x; j < k; j += THREADS) {
     const uint64_t e = s.top[j];
     const uint32_t idx = (uint32_t)e;
-    outD[row * k + j] = rowp[idx];
+    outD[row * k + j] = selected_value(e, largest != 0, rowp);
     outI[row * k + j] = (int64_t)idx;
   }
 }
@@ -709,27 +711,27 @@ gbk_status dispatch_rows(const float* vals, int64_t rows, int64_t len, int k, in
 
 template <int KP>
 gbk_status launch_merge(const uint64_t* part, int64_t rows, int64_t nper, int k,
-                        const float* vals, int64_t len, float* D, int64_t* I,
+                        const float* vals, int64_t len, bool largest, float* D, int64_t* I,
                         cudaStream_t stream) {
   constexpr int THREADS = 256;
   using Sel = BlockSelect<THREADS, KP, 4096>;
   auto kern = kselect_merge_kernel<THREADS, KP>;
   GBK_TRY(set_smem_limit(kern, sizeof(typename Sel::Smem)));
   kern<<<(unsigned)rows, THREADS, sizeof(typename Sel::Smem), stream>>>(part, nper, k, vals, len,
-                                                                         D, I);
+                                                                         largest ? 1 : 0, D, I);
   GBK_LAUNCH_CHECK();
   return GBK_OK;
 }
 
 gbk_status dispatch_merge(const uint64_t* part, int64_t rows, int64_t nper, int k,
-                          const float* vals, int64_t len, float* D, int64_t* I,
+                          const float* vals, int64_t len, bool largest, float* D, int64_t* I,
                           cudaStream_t st) {
-  if (k <= 32) return launch_merge<32>(part, rows, nper, k, vals, len, D, I, st);
-  if (k <= 64) return launch_merge<64>(part, rows, nper, k, vals, len, D, I, st);
-  if (k <= 128) return launch_merge<128>(part, rows, nper, k, vals, len, D, I, st);
-  if (k <= 256) return launch_merge<256>(part, rows, nper, k, vals, len, D, I, st);
-  if (k <= 512) return launch_merge<512>(part, rows, nper, k, vals, len, D, I, st);
-  return launch_merge<1024>(part, rows, nper, k, vals, len, D, I, st);
+  if (k <= 32) return launch_merge<32>(part, rows, nper, k, vals, len, largest, D, I, st);
+  if (k <= 64) return launch_merge<64>(part, rows, nper, k, vals, len, largest, D, I, st);
+  if (k <= 128) return launch_merge<128>(part, rows, nper, k, vals, len, largest, D, I, st);
+  if (k <= 256) return launch_merge<256>(part, rows, nper, k, vals, len, largest, D, I, st);
+  if (k <= 512) return launch_merge<512>(part, rows, nper, k, vals, len, largest, D, I, st);
+  return launch_merge<1024>(part, rows, nper, k, vals, len, largest, D, I, st);
 }
 
 }  // namespace
@@ -782,7 +784,7 @@ gbk_status kselect_launch(const float* vals, int64_t rows, int64_t len, int k, b
   }
   if (r != GBK_OK || segs == 1) return r;
   const int64_t nper = segs * (k == 1 ? 1 : k);
-  return dispatch_merge(pp, rows, nper, k, vals, len, D, I, st);
+  return dispatch_merge(pp, rows, nper, k, vals, len, largest, D, I, st);
 }
 
 }  // namespace

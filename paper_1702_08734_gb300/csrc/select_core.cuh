@@ -43,6 +43,17 @@ __device__ __forceinline__ float key_value(uint32_t k, bool largest) {
   return largest ? -v : v;
 }
 
+// The input value of a selected composite e (index in its low word into `row`).  The key
+// is a bijection of the float's bits except that -0 and +0 share a key and every NaN maps
+// to NAN_KEY: only those are read back from the input (the sign of a zero, a NaN's
+// payload); every other value is rebuilt from the key, which saves a scattered read per
+// selected element.
+__device__ __forceinline__ float selected_value(uint64_t e, bool largest, const float* row) {
+  const uint32_t key = (uint32_t)(e >> 32);
+  if (key == NAN_KEY || key == 0x80000000u) return row[(uint32_t)e];
+  return key_value(key, largest);
+}
+
 __device__ __forceinline__ uint64_t composite(uint32_t key, uint32_t idx) {
   return ((uint64_t)key << 32) | (uint64_t)idx;
 }

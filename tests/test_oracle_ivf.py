@@ -289,3 +289,49 @@ def test_residual_training_set_is_offset_from_nearest_centroid():
     np.testing.assert_allclose(res, x.astype(np.float64) - cen[j].astype(np.float64), rtol=0,
                                atol=0)
     np.testing.assert_array_equal(oracle.residual_training_set(cen, cen), np.zeros((5, 6)))
+
+
+def test_procrustes_recovers_a_known_rotation():
+    # y = x Q^T with Q orthogonal: the minimiser is Q itself (the SVD formula's orientation
+    # - R, not R^T - is what this pins)
+    rng = np.random.default_rng(8)
+    x = rng.normal(size=(500, 12))
+    Q, _ = np.linalg.qr(rng.normal(size=(12, 12)))
+    np.testing.assert_allclose(oracle.procrustes(x, x @ Q.T), Q, atol=1e-10)
+    # a reflection-free case and a case with noise: still orthogonal, and optimal against
+    # random orthogonal alternatives
+    y = x @ Q.T + 0.05 * rng.normal(size=x.shape)
+    R = oracle.procrustes(x, y)
+    np.testing.assert_allclose(R @ R.T, np.eye(12), atol=1e-10)
+    err = np.linalg.norm(x @ R.T - y)
+    for s in range(20):
+        W, _ = np.linalg.qr(np.random.default_rng(100 + s).normal(size=(12, 12)))
+        assert err <= np.linalg.norm(x @ W.T - y)
+
+
+def test_opq_keeps_identity_when_pq_is_lossless():
+    # every row exactly representable by the product quantizer: the reconstruction is x,
+    # A = x^T x is symmetric positive definite and its polar factor is the identity
+    r, V = _block_tagged_residuals(4, 3, 2000, 31)
+    R, books = oracle.opq_train(r, 4, np.arange(256), 2, 3)
+    np.testing.assert_allclose(R, np.eye(12), atol=1e-5)
+    np.testing.assert_array_equal(books, V)
+
+
+def test_opq_lowers_quantization_error_of_rotated_data():
+    # block-structured data mixed by a hidden rotation: the trained rotation reconstructs
+    # better than the plain product quantizer of the unrotated data
+    r, V = _block_tagged_residuals(4, 3, 3000, 41)
+    r = r + np.random.default_rng(42).normal(size=r.shape).astype(np.float32) * 0.05
+    Q, _ = np.linalg.qr(np.random.default_rng(43).normal(size=(12, 12)))
+    x = (r.astype(np.float64) @ Q.T).astype(np.float32)
+
+    def mse(xr, books):
+        _, codes = oracle.ivfpq_encode(xr, np.zeros((1, 12), np.float32), books)
+        y = np.concatenate([books[m][codes[:, m]] for m in range(4)], axis=1)
+        return float(((xr.astype(np.float64) - y) ** 2).sum(1).mean())
+
+    plain = oracle.train_pq(x, 4, np.arange(256), 4)
+    R, books = oracle.opq_train(x, 4, np.arange(256), 6, 4)
+    np.testing.assert_allclose(R @ R.T, np.eye(12), atol=1e-5)
+    assert mse(oracle.rotate(x, R), books) < mse(x, plain)
