@@ -298,7 +298,7 @@ gbk_status gbk_ivfpq_set_rotation(gbk_index* index, const float* R, void* stream
 typedef struct gbk_opq_opts {
   int32_t niter;             /* alternations of PQ training and Procrustes (0 = 10)       */
   int32_t pq_niter;          /* k-means iterations per PQ training (0 = 4)               */
-  int32_t polar_iters;       /* Newton-Schulz iterations of the polar factor (0 = 40)    */
+  int32_t polar_iters;       /* scaled Newton iterations of the polar factor (0 = 12)    */
   const int64_t* pq_init;    /* HOST [256] rows of x that seed every sub-quantizer's      */
                              /* k-means (NULL = 0..255)                                   */
 } gbk_opq_opts;
@@ -309,9 +309,11 @@ typedef struct gbk_opq_opts {
  * block of d/M dimensions, seeded from the rows pq_init, pq_niter iterations), encode and
  * reconstruct every row (Y^), then set R to the orthogonal matrix minimising
  * ||x R^T - Y^||_F: the polar factor U V^T of A = Y^T x = U S V^T (A summed in double;
- * the polar factor by Newton-Schulz iterations in double from A / ||A||_F).  Must run
+ * the polar factor by scaled Newton iterations X <- (g X + X^-T / g) / 2 in double, the
+ * inverse by Gauss-Jordan elimination, then two Newton-Schulz steps).  Must run
  * before gbk_ivfpq_train and gbk_ivfpq_add (GBK_EINVAL otherwise).  R_out (host or
- * device, may be NULL): the trained R [d][d] row-major.  256 <= n < 2^31, d <= 1024. */
+ * device, may be NULL): the trained R [d][d] row-major.  256 <= n < 2^31, d <= 1024.
+ * GBK_EINVAL also when the cross-covariance A is singular (degenerate training data). */
 gbk_status gbk_ivfpq_train_rotation(gbk_index* index, const float* x, int64_t n,
                                     const gbk_opq_opts* opts, float* R_out, void* stream);
 

@@ -390,7 +390,7 @@ class IVFPQIndex:
         return self
 
     def train_rotation(self, x: torch.Tensor, niter: int = 10, pq_niter: int = 4, pq_init=None,
-                       polar_iters: int = 40):
+                       polar_iters: int = 12):
         """Train the OPQ rotation on x (before train/add) and install it; returns R [d][d]."""
         _dev(x, torch.float32, "x")
         pi = pip = None

@@ -5,8 +5,11 @@
 //      k-means per block of d/M dimensions, and every rotated vector's reconstruction y^;
 //   2. with the reconstructions fixed, the orthogonal R minimising ||x R^T - Y^||_F: the
 //      orthogonal Procrustes solution R = U V^T for A = Y^T x = U S V^T (the polar factor
-//      of A), computed here by Newton-Schulz iterations Z <- Z (3 I - Z^T Z) / 2 from
-//      Z = A / ||A||_F, in double precision.
+//      of A), computed here in double precision by the scaled Newton iteration
+//      X <- (g X + X^{-T} / g) / 2, g = (||X^{-1}||_F / ||X||_F)^(1/2) (Higham), which
+//      converges quadratically whatever the conditioning of A, the inverse by Gauss-Jordan
+//      elimination with partial pivoting; two Newton-Schulz steps
+//      X <- X (3 I - X^T X) / 2 polish the orthogonality at the end.
 // The result is installed as the index's rotation (as gbk_ivfpq_set_rotation does).
 #include <algorithm>
 #include <cmath>
@@ -81,25 +84,6 @@ __global__ void cross_reduce_kernel(const double* __restrict__ part, int splits,
   }
 }
 
-__global__ void frobenius_kernel(const double* __restrict__ A, int n, double* __restrict__ out) {
-  __shared__ double red[256];
-  double s = 0.0;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) s += A[e] * A[e];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = sqrt(red[0]);
-}
-
-__global__ void scale_kernel(const double* __restrict__ A, const double* __restrict__ norm, int n,
-                             double* __restrict__ Z) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-    Z[e] = A[e] / *norm;
-}
-
 // C = alpha * op(A) B + beta * Cin for d x d row-major doubles, op(A) = A or A^T; 16 x 16 tiles
 __global__ void gemm_f64_kernel(const double* __restrict__ A, const double* __restrict__ B, int d,
                                 bool transA, double alpha, const double* __restrict__ Cin,
@@ -123,6 +107,116 @@ __global__ void gemm_f64_kernel(const double* __restrict__ A, const double* __re
   }
 }
 
+// One block: inverse of the d x d matrix X (row-major doubles) by Gauss-Jordan elimination
+// with partial pivoting on the workspace W [d][2d] = [X | I]; Xinv out.  *singular = 1 when
+// a pivot is zero (Xinv then undefined).
+__global__ void __launch_bounds__(1024) gauss_jordan_kernel(const double* __restrict__ X, int d,
+                                                          double* __restrict__ W,
+                                                          double* __restrict__ Xinv,
+                                                          int* __restrict__ singular) {
+  const int tid = threadIdx.x, nt = blockDim.x, w2 = 2 * d;
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int piv;
+  __shared__ double pval;
+  for (int e = tid; e < d * w2; e += nt) {
+    const int r = e / w2, c = e % w2;
+    W[e] = c < d ? X[(int64_t)r * d + c] : (c - d == r ? 1.0 : 0.0);
+  }
+  if (tid == 0) *singular = 0;
+  __syncthreads();
+  for (int c = 0; c < d; c++) {
+    // pivot: the row r >= c with the largest |W[r][c]| (lowest r on ties)
+    double bv = -1.0;
+    int bi = c;
+    for (int r = c + tid; r < d; r += nt) {
+      const double v = fabs(W[(int64_t)r * w2 + c]);
+      if (v > bv) {
+        bv = v;
+        bi = r;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if ((tid & 31) == 0) {
+      red_v[tid >> 5] = bv;
+      red_i[tid >> 5] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double v = red_v[0];
+      int i = red_i[0];
+      for (int w = 1; w < (nt + 31) / 32; w++)
+        if (red_v[w] > v || (red_v[w] == v && red_i[w] < i)) {
+          v = red_v[w];
+          i = red_i[w];
+        }
+      piv = i;
+      if (!(v > 0.0)) *singular = 1;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != c)
+      for (int j = tid; j < w2; j += nt) {
+        const double t = W[(int64_t)c * w2 + j];
+        W[(int64_t)c * w2 + j] = W[(int64_t)p * w2 + j];
+        W[(int64_t)p * w2 + j] = t;
+      }
+    __syncthreads();
+    if (tid == 0) pval = W[(int64_t)c * w2 + c];
+    __syncthreads();
+    const double inv = pval != 0.0 ? 1.0 / pval : 0.0;
+    for (int j = tid; j < w2; j += nt) W[(int64_t)c * w2 + j] *= inv;
+    __syncthreads();
+    // eliminate column c from every other row (factors read before any row changes)
+    for (int e = tid; e < d * w2; e += nt) {
+      const int r = e / w2, j = e % w2;
+      if (r == c || j == c) continue;
+      W[e] -= W[(int64_t)r * w2 + c] * W[(int64_t)c * w2 + j];
+    }
+    __syncthreads();
+    for (int r = tid; r < d; r += nt)
+      if (r != c) W[(int64_t)r * w2 + c] = 0.0;
+    __syncthreads();
+  }
+  for (int e = tid; e < d * d; e += nt) {
+    const int r = e / d, j = e % d;
+    Xinv[e] = W[(int64_t)r * w2 + d + j];
+  }
+}
+
+// X <- (g X + Xinv^T / g) / 2 with g = sqrt(||Xinv||_F / ||X||_F) (one block)
+__global__ void newton_step_kernel(double* __restrict__ X, const double* __restrict__ Xinv, int d) {
+  __shared__ double sa[256], sb[256];
+  double a = 0.0, b = 0.0;
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
+    a += X[e] * X[e];
+    b += Xinv[e] * Xinv[e];
+  }
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sa[threadIdx.x] += sa[threadIdx.x + o];
+      sb[threadIdx.x] += sb[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  const double g = sqrt(sqrt(sb[0]) / sqrt(sa[0]));
+  __syncthreads();
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
+    const int r = e / d, c = e % d;
+    X[e] = 0.5 * (g * X[e] + Xinv[(int64_t)c * d + r] / g);
+  }
+}
+
 __global__ void to_float_kernel(const double* __restrict__ Z, int n, float* __restrict__ R) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
     R[e] = (float)Z[e];
@@ -133,28 +227,37 @@ __global__ void identity_kernel(int d, float* __restrict__ R) {
     R[e] = (e / d == e % d) ? 1.f : 0.f;
 }
 
-// Polar factor of the d x d matrix A (device doubles) into R (float): Newton-Schulz
-// Z <- 1.5 Z - 0.5 Z (Z^T Z) from Z = A / ||A||_F (all singular values in (0, 1]).
+// Polar factor of the d x d matrix A (device doubles) into R (float): `iters` scaled
+// Newton steps from X = A, then two Newton-Schulz steps.  GBK_EINVAL if A is singular.
 gbk_status polar_run(const double* A, int d, int iters, float* R, cudaStream_t st) {
   gbk_status r;
-  Scratch Z, Z2, T, nrm;
+  Scratch X, Xi, W, T, X2, sing;
   const size_t b = sizeof(double) * (size_t)d * d;
-  if ((r = Z.alloc(b, st)) != GBK_OK || (r = Z2.alloc(b, st)) != GBK_OK ||
-      (r = T.alloc(b, st)) != GBK_OK || (r = nrm.alloc(sizeof(double), st)) != GBK_OK)
+  if ((r = X.alloc(b, st)) != GBK_OK || (r = Xi.alloc(b, st)) != GBK_OK ||
+      (r = W.alloc(2 * b, st)) != GBK_OK || (r = T.alloc(b, st)) != GBK_OK ||
+      (r = X2.alloc(b, st)) != GBK_OK || (r = sing.alloc(sizeof(int), st)) != GBK_OK)
     return r;
-  frobenius_kernel<<<1, 256, 0, st>>>(A, d * d, nrm.as<double>());
-  scale_kernel<<<(d * d + 255) / 256, 256, 0, st>>>(A, nrm.as<double>(), d * d, Z.as<double>());
-  GBK_LAUNCH_CHECK();
-  const dim3 grid((d + 15) / 16, (d + 15) / 16);
-  double* z = Z.as<double>();
-  double* z2 = Z2.as<double>();
+  GBK_CUDA_CHECK(cudaMemcpyAsync(X.p, A, b, cudaMemcpyDeviceToDevice, st));
   for (int it = 0; it < iters; it++) {
-    gemm_f64_kernel<<<grid, 256, 0, st>>>(z, z, d, true, 1.0, nullptr, 0.0, T.as<double>());
-    gemm_f64_kernel<<<grid, 256, 0, st>>>(z, T.as<double>(), d, false, -0.5, z, 1.5, z2);
-    std::swap(z, z2);
+    gauss_jordan_kernel<<<1, 1024, 0, st>>>(X.as<double>(), d, W.as<double>(), Xi.as<double>(),
+                                            sing.as<int>());
+    newton_step_kernel<<<1, 256, 0, st>>>(X.as<double>(), Xi.as<double>(), d);
   }
   GBK_LAUNCH_CHECK();
-  to_float_kernel<<<(d * d + 255) / 256, 256, 0, st>>>(z, d * d, R);
+  int singular = 0;
+  GBK_CUDA_CHECK(cudaMemcpyAsync(&singular, sing.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GBK_CUDA_CHECK(cudaStreamSynchronize(st));
+  if (singular)
+    return set_error(GBK_EINVAL, "gbk_ivfpq_train_rotation: singular cross-covariance (degenerate training data)");
+  const dim3 grid((d + 15) / 16, (d + 15) / 16);
+  double* x = X.as<double>();
+  double* x2 = X2.as<double>();
+  for (int it = 0; it < 2; it++) {
+    gemm_f64_kernel<<<grid, 256, 0, st>>>(x, x, d, true, 1.0, nullptr, 0.0, T.as<double>());
+    gemm_f64_kernel<<<grid, 256, 0, st>>>(x, T.as<double>(), d, false, -0.5, x, 1.5, x2);
+    std::swap(x, x2);
+  }
+  to_float_kernel<<<(d * d + 255) / 256, 256, 0, st>>>(x, d * d, R);
   GBK_LAUNCH_CHECK();
   return GBK_OK;
 }
@@ -176,7 +279,7 @@ gbk_status gbk_ivfpq_train_rotation(gbk_index* ix, const float* x, int64_t n,
   GBK_REQUIRE(ix->d <= 1024, "gbk_ivfpq_train_rotation: d <= 1024");
   const int niter = opts && opts->niter > 0 ? opts->niter : 10;
   const int pq_niter = opts && opts->pq_niter > 0 ? opts->pq_niter : 4;
-  const int ns_iters = opts && opts->polar_iters > 0 ? opts->polar_iters : 40;
+  const int ns_iters = opts && opts->polar_iters > 0 ? opts->polar_iters : 12;
   std::vector<int64_t> pinit(256);
   for (int i = 0; i < 256; i++) pinit[i] = opts && opts->pq_init ? opts->pq_init[i] : i;
   for (int64_t v : pinit)
