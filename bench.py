@@ -880,7 +880,7 @@ def main():
     hbm, bf16, bf16s, src = peaks()
     ks_ms = by.get("kselect_rows", [])
     k1_ms = by.get("kselect_k1", [])
-    gemm_ms = by.get("dist_gemm_tf32x3", [])
+    gemm_ms = by.get("dist_gemm_fp16x3", [])
     ksel_bytes = KSEL_ROWS * KSEL_LEN * 4
     ks_detail = {}
     if k1_ms:
@@ -891,23 +891,19 @@ def main():
             ks_detail["k%d" % k] = ksel_bytes / (sum(sel) / len(sel) / 1e3) / 1e9
     gemm_avg = sum(gemm_ms) / len(gemm_ms) if gemm_ms else None
     flops = 2.0 * NQ * NB * D
-    # TF32 denominator: the nominal TF32:BF16 ratio (1/2) of the measured BF16 rate, or the
-    # TF32 rate the library's own GEMM reached in the probe, whichever is larger
-    tp = tensor_peaks()
-    tf32_probe = tp.get("tf32_tflops")
-    tf32_peak = max(bf16 / 2.0, tf32_probe or 0.0)
-    # DRAM bytes per launch: not proportional to nq x nb (database chunks are re-read per
-    # query wave), so the small-case ncu figure is not scaled up (profiles/)
-    traffic = None
-    roof = {"bound": "tensor", "kernel": "dist_gemm_tf32x3 (3 TF32 passes per product)",
-            "achieved": flops / (gemm_avg / 1e3) / 1e12 if gemm_avg else None,
-            "peak": tf32_peak, "unit": "TFLOP/s",
-            "frac": (flops / (gemm_avg / 1e3) / 1e12) / tf32_peak if gemm_avg else None,
+    # the float32-accurate GEMM issues 3 FP16 MMAs per product (FP16 split of power-of-two
+    # scaled rows); its denominator is the measured dense FP16/BF16 rate (the same
+    # tensor-core rate for both 16-bit types), against algorithmic flops
+    fp16_peak = bf16
+    traffic = None  # not proportional to nq x nb (chunks re-read per query wave): profiles/
+    achieved = flops / (gemm_avg / 1e3) / 1e12 if gemm_avg else None
+    roof = {"bound": "tensor", "kernel": "dist_gemm_fp16x3 (float32-accurate: 3 FP16 MMAs per product)",
+            "achieved": achieved, "peak": fp16_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp16_peak if achieved else None,
+            "frac_executed": 3 * achieved / fp16_peak if achieved else None,
             "traffic": traffic,
-            "peak_source": "max(%s bf16 %.0f TFLOP/s x 1/2 (TF32:BF16 nominal ratio), the library's "
-                           "own TF32 GEMM rate %s TFLOP/s in profiles/tensor_peaks.json)" % (
-                               src, bf16, "%.0f" % tf32_probe if tf32_probe else "n/a"),
-            "frac_executed": 3 * (flops / (gemm_avg / 1e3) / 1e12) / tf32_peak if gemm_avg else None}
+            "peak_source": "%s bf16 %.0f TFLOP/s (dense 16-bit tensor rate)" % (src, bf16),
+            "kernel_store_mode_tflops": tensor_peaks().get("fp16_tflops")}
     kselect_obj = {"unit": "GB/s", "peak_hbm_gbs": hbm, "peak_source": src,
                    "gbs": ks_detail, "frac": {k: v / hbm for k, v in ks_detail.items()}}
 
@@ -982,7 +978,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded N(0,1) database/queries, U[0,1) k-select rows)",
-            "config": {"workload": "exact k-NN nb=%d nq=%d d=%d k in {10,100} (TF32x3, float32-accurate) + k-select %d x %d k in {1,32,256,1024}" % (NB, NQ, D, KSEL_ROWS, KSEL_LEN),
+            "config": {"workload": "exact k-NN nb=%d nq=%d d=%d k in {10,100} (float32-accurate: FP16 hi/lo split, 3 passes) + k-select %d x %d k in {1,32,256,1024}" % (NB, NQ, D, KSEL_ROWS, KSEL_LEN),
                        "l2_flush": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU",
                        "knn_ms_per_step": knn_ms / args.steps, "kselect_ms_per_step": ksel_ms / args.steps},
             "roofline": roof, "kselect": kselect_obj, "cpu_baseline": cpu, "e2e": e2e,

@@ -44,9 +44,12 @@ typedef int32_t gbk_status;
 #define GBK_METRIC_IP 1 /* inner product, descending              */
 
 /* Arithmetic of the distance GEMM (the -2<x,y> term of Eq. (2)). */
-#define GBK_PREC_FP32 0 /* float32-accurate: TF32 hi/lo split, 3 tensor-core passes */
-#define GBK_PREC_BF16 1 /* one BF16 pass, float32 accumulation                      */
-#define GBK_PREC_FP8 2  /* one FP8 E4M3 pass with per-row scales, float32 accumulation */
+#define GBK_PREC_FP32 0   /* float32-accurate: each row scaled by a power of two s >= max|x|, */
+                          /* split into FP16 pieces hi + lo (22 significand bits), 3 passes  */
+                          /* (hi hi + hi lo + lo hi) at the FP16 rate, float32 accumulation   */
+#define GBK_PREC_BF16 1   /* one BF16 pass, float32 accumulation                              */
+#define GBK_PREC_FP8 2    /* one FP8 E4M3 pass with per-row scales, float32 accumulation      */
+#define GBK_PREC_TF32X3 3 /* float32-accurate: TF32 hi/lo split, 3 passes at the TF32 rate    */
 
 #define GBK_MAX_K 1024 /* largest k any selection accepts (the paper's WarpSelect bound, section 4.2) */
 

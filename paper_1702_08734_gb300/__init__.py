@@ -196,7 +196,7 @@ def row_norms(x: torch.Tensor, out=None):
     return o
 
 
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "tf32x3": 3}
 
 
 class KnnOpts(ctypes.Structure):

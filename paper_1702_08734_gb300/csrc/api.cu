@@ -244,7 +244,7 @@ gbk_status gbk_knn_brute(const float* xq, int64_t nq, const float* xb, int64_t n
   GBK_REQUIRE(xq && xb && D && I, "gbk_knn_brute: NULL pointer");
   KnnPlan plan;
   if (opts) {
-    GBK_REQUIRE(opts->precision >= GBK_PREC_FP32 && opts->precision <= GBK_PREC_FP8,
+    GBK_REQUIRE(opts->precision >= GBK_PREC_FP32 && opts->precision <= GBK_PREC_TF32X3,
                 "gbk_knn_brute: bad precision");
     GBK_REQUIRE(opts->chunks >= 0, "gbk_knn_brute: chunks < 0");
     GBK_REQUIRE(opts->kprime == 0 || (opts->kprime >= k && opts->kprime <= GBK_MAX_K),
@@ -282,7 +282,7 @@ gbk_status gbk_pairwise_distances(const float* xq, int64_t nq, const float* xb, 
   GBK_REQUIRE(d >= 1 && ldo >= nb, "gbk_pairwise_distances: bad d or ldo");
   GBK_REQUIRE(metric == GBK_METRIC_L2 || metric == GBK_METRIC_IP,
               "gbk_pairwise_distances: bad metric");
-  GBK_REQUIRE(precision >= GBK_PREC_FP32 && precision <= GBK_PREC_FP8,
+  GBK_REQUIRE(precision >= GBK_PREC_FP32 && precision <= GBK_PREC_TF32X3,
               "gbk_pairwise_distances: bad precision");
   if (nq == 0) return GBK_OK;
   GBK_REQUIRE(xq && xb && out, "gbk_pairwise_distances: NULL pointer");

@@ -62,6 +62,46 @@ __global__ void prep_bf16_kernel(const float* __restrict__ x, int64_t n, int d, 
   if (lane == 0) norms[row] = s;
 }
 
+__global__ void prep_fp16x3_kernel(const float* __restrict__ x, int64_t n, int d, int dpad,
+                                   __half* __restrict__ hi, __half* __restrict__ lo,
+                                   float* __restrict__ scale, float* __restrict__ norms,
+                                   int64_t nrows_pad, float pad_norm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (row >= nrows_pad) return;
+  if (row >= n) {
+    if (lane == 0) {
+      norms[row] = pad_norm;
+      scale[row] = 0.f;
+    }
+    return;
+  }
+  float s = 0.f, amax = 0.f;
+  for (int t = lane; t < dpad; t += 32) {
+    const float v = t < d ? x[row * d + t] : 0.f;
+    s = fmaf(v, v, s);
+    amax = fmaxf(amax, fabsf(v));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(FULL_MASK, s, o);
+    amax = fmaxf(amax, __shfl_xor_sync(FULL_MASK, amax, o));
+  }
+  // s = 2^e with amax / s in [0.5, 1): the scaled row is exact and within FP16's range
+  int e = 0;
+  if (amax > 0.f) frexpf(amax, &e);
+  for (int t = lane; t < dpad; t += 32) {
+    const float v = t < d ? ldexpf(x[row * d + t], -e) : 0.f;
+    const __half h = __float2half_rn(v);
+    hi[row * dpad + t] = h;
+    lo[row * dpad + t] = __float2half_rn(v - __half2float(h));
+  }
+  if (lane == 0) {
+    norms[row] = s;
+    scale[row] = ldexpf(1.f, e);
+  }
+}
+
 __global__ void prep_fp8_kernel(const float* __restrict__ x, int64_t n, int d, int dpad,
                                 __nv_fp8_e4m3* __restrict__ out, float* __restrict__ scale,
                                 float* __restrict__ norms, int64_t nrows_pad, float pad_norm) {
@@ -329,8 +369,18 @@ gbk_status make_operand_map(CUtensorMap* m, const void* base, int64_t rows, int 
   return GBK_OK;
 }
 
-int elem_bytes_of(int prec) { return prec == GBK_PREC_BF16 ? 2 : prec == GBK_PREC_FP8 ? 1 : 4; }
-int pieces_of(int prec) { return prec == GBK_PREC_FP32 ? 2 : 1; }
+int elem_bytes_of(int prec) {
+  const int kd = gemm_kind(prec);
+  return kd == KIND_TF32X3 ? 4 : kd == KIND_FP8 ? 1 : 2;
+}
+int pieces_of(int prec) {
+  const int kd = gemm_kind(prec);
+  return kd == KIND_TF32X3 || kd == KIND_FP16X3 ? 2 : 1;
+}
+bool scaled_of(int prec) {
+  const int kd = gemm_kind(prec);
+  return kd == KIND_FP8 || kd == KIND_FP16X3;
+}
 
 }  // namespace
 
@@ -350,24 +400,29 @@ gbk_status prepare_operand(const float* x, int64_t n, int d, int prec, int64_t n
   if (r != GBK_OK) return r;
   r = out->norms.alloc(sizeof(float) * (size_t)nrows_pad, st);
   if (r != GBK_OK) return r;
-  if (prec == GBK_PREC_FP8) {
+  if (scaled_of(prec)) {
     r = out->scale.alloc(sizeof(float) * (size_t)nrows_pad, st);
     if (r != GBK_OK) return r;
   }
   unsigned char* base = out->data.as<unsigned char>();
   out->piece[0] = base;
-  out->piece[1] = prec == GBK_PREC_FP32 ? base + piece : nullptr;
+  out->piece[1] = pieces_of(prec) > 1 ? base + piece : nullptr;
   const int warps = 8;
   const unsigned blocks = (unsigned)((nrows_pad + warps - 1) / warps);
   if (nrows_pad == 0) return GBK_OK;
   ProfScope prof("prep_operand", st);
-  if (prec == GBK_PREC_FP32)
+  const int kind = gemm_kind(prec);
+  if (kind == KIND_TF32X3)
     prep_tf32x3_kernel<<<blocks, warps * 32, 0, st>>>(
         x, n, d, dpad, (float*)out->piece[0], (float*)out->piece[1], out->norms.as<float>(),
         nrows_pad, pad_norm);
-  else if (prec == GBK_PREC_BF16)
+  else if (kind == KIND_BF16)
     prep_bf16_kernel<<<blocks, warps * 32, 0, st>>>(x, n, d, dpad, (__nv_bfloat16*)out->piece[0],
                                                    out->norms.as<float>(), nrows_pad, pad_norm);
+  else if (kind == KIND_FP16X3)
+    prep_fp16x3_kernel<<<blocks, warps * 32, 0, st>>>(
+        x, n, d, dpad, (__half*)out->piece[0], (__half*)out->piece[1], out->scale.as<float>(),
+        out->norms.as<float>(), nrows_pad, pad_norm);
   else
     prep_fp8_kernel<<<blocks, warps * 32, 0, st>>>(x, n, d, dpad, (__nv_fp8_e4m3*)out->piece[0],
                                                   out->scale.as<float>(), out->norms.as<float>(),
@@ -446,11 +501,17 @@ gbk_status gemm_launch(int mode, int kpr, bool largest, const PreparedOperand& Q
   const int grid = std::min(nitems, di.sm_count);
   a.status = device_status();
   if (!a.status) return set_error(GBK_ECUDA, "device status word unavailable");
-  ProfScope prof(prec == GBK_PREC_FP32 ? "dist_gemm_tf32x3"
-                 : prec == GBK_PREC_BF16 ? "dist_gemm_bf16" : "dist_gemm_fp8", st);
-  if (prec == GBK_PREC_FP32)
+  const int kind = gemm_kind(prec);
+  ProfScope prof(kind == KIND_TF32X3   ? "dist_gemm_tf32x3"
+                 : kind == KIND_FP16X3 ? "dist_gemm_fp16x3"
+                 : kind == KIND_BF16   ? "dist_gemm_bf16"
+                                       : "dist_gemm_fp8",
+                 st);
+  if (kind == KIND_TF32X3)
     return launch_dist_gemm_tf32x3(mode, kpr, largest, maps, a, grid, smem, st);
-  if (prec == GBK_PREC_BF16)
+  if (kind == KIND_FP16X3)
+    return launch_dist_gemm_fp16x3(mode, kpr, largest, maps, a, grid, smem, st);
+  if (kind == KIND_BF16)
     return launch_dist_gemm_bf16(mode, kpr, largest, maps, a, grid, smem, st);
   return launch_dist_gemm_fp8(mode, kpr, largest, maps, a, grid, smem, st);
 }
@@ -567,7 +628,8 @@ gbk_status knn_run(const float* xq, int64_t nq, const float* xb, int64_t nb, int
   if ((r = prepare_operand(xb, nb, d, plan.prec, (int64_t)ntiles * GEMM_BN, 0.f, &B, st)) !=
       GBK_OK)
     return r;
-  if (plan.prec == GBK_PREC_FP32) return select_run(xq, Q, B, nq, nb, d, k, ip, plan.chunks, D, I, st);
+  if (plan.prec == GBK_PREC_FP32 || plan.prec == GBK_PREC_TF32X3)  // float32-accurate kinds
+    return select_run(xq, Q, B, nq, nb, d, k, ip, plan.chunks, D, I, st);
   // low precision: over-fetch k' candidates, then the exact float32 re-rank + certificate.
   // Default k' = 4k for k <= 16 and k + k/4 above: longer candidate lists slow the fused
   // selection far more than the certificate gains (10^4 x 10^6 x 128, k = 100, BF16:

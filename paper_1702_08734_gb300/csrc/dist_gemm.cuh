@@ -26,10 +26,15 @@
 // Precision variants (KIND): TF32X3 keeps float32 accuracy by splitting each operand
 // x = hi + lo into TF32 pieces and accumulating hi*hi + hi*lo + lo*hi (Ootomo & Yokota,
 // "Recovering single precision accuracy from Tensor Cores while surpassing the FP32
-// theoretical peak performance", IJHPCA 2022); BF16 and FP8 (E4M3) are one-pass.
+// theoretical peak performance", IJHPCA 2022); FP16X3 applies the same split to FP16
+// pieces of the row scaled by a power of two s = 2^e >= max|x| (x / s exact, hi = fp16(x/s),
+// lo = fp16(x/s - hi): 22 significand bits, the absolute error of lo below 2^-25 of the
+// row's largest element) at the FP16 MMA rate, s_x s_y applied in the epilogue; BF16 and
+// FP8 (E4M3, per-row scale) are one-pass.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <cstdint>
 
@@ -39,7 +44,7 @@
 
 namespace gbk {
 
-enum GemmKind : int { KIND_TF32X3 = 0, KIND_BF16 = 1, KIND_FP8 = 2 };
+enum GemmKind : int { KIND_TF32X3 = 0, KIND_BF16 = 1, KIND_FP8 = 2, KIND_FP16X3 = 3 };
 enum GemmMode : int { MODE_SELECT = 0, MODE_STORE = 1 };
 
 constexpr int GEMM_BM = 128;          // queries per tile (TMEM lanes)
@@ -69,8 +74,23 @@ struct KindTraits<KIND_FP8> {
   static constexpr int ELEM = 1, PIECES = 1, EPI = 2;
   static constexpr uint32_t FMT = sm100::FMT_E4M3;
 };
+template <>
+struct KindTraits<KIND_FP16X3> {
+  static constexpr int ELEM = 2, PIECES = 2, EPI = 2;
+  static constexpr uint32_t FMT = sm100::FMT_F16;
+};
 __host__ __device__ constexpr int gemm_threads(int epi) { return 64 + 128 * epi; }
-__host__ __device__ constexpr int gemm_epi(int prec) { return prec == 0 ? 1 : 2; }
+// Kernel kind of a public precision: float32 accuracy comes from the FP16 split (the
+// faster of the two float32-accurate kinds), GBK_PREC_TF32X3 asks for the TF32 split.
+__host__ __device__ constexpr int gemm_kind(int prec) {
+  return prec == GBK_PREC_FP32     ? KIND_FP16X3
+         : prec == GBK_PREC_TF32X3 ? KIND_TF32X3
+         : prec == GBK_PREC_BF16   ? KIND_BF16
+                                   : KIND_FP8;
+}
+__host__ __device__ constexpr int gemm_epi(int prec) {
+  return gemm_kind(prec) == KIND_TF32X3 ? 1 : 2;
+}
 
 struct GemmArgs {
   int nq, nb;            // queries, database rows
@@ -169,6 +189,12 @@ __global__ void prep_tf32x3_kernel(const float* __restrict__ x, int64_t n, int d
 __global__ void prep_bf16_kernel(const float* __restrict__ x, int64_t n, int d, int dpad,
                                  __nv_bfloat16* __restrict__ out, float* __restrict__ norms,
                                  int64_t nrows_pad, float pad_norm);
+// x -> fp16 hi, lo [n][dpad] of x / s with the per-row power of two s >= max|x|, scale[n]
+// = s, norms from the float32 input.
+__global__ void prep_fp16x3_kernel(const float* __restrict__ x, int64_t n, int d, int dpad,
+                                   __half* __restrict__ hi, __half* __restrict__ lo,
+                                   float* __restrict__ scale, float* __restrict__ norms,
+                                   int64_t nrows_pad, float pad_norm);
 // x -> e4m3 [n][dpad] with a per-row scale s = max|x| / 448 (x ~ s * q), norms.
 __global__ void prep_fp8_kernel(const float* __restrict__ x, int64_t n, int d, int dpad,
                                 __nv_fp8_e4m3* __restrict__ out, float* __restrict__ scale,

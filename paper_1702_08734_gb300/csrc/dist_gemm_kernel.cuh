@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
   constexpr int PIECES = T::PIECES;
   constexpr int EPI = T::EPI;
   constexpr bool QUEUES = (MODE == MODE_SELECT) && (KPR > 0);
+  constexpr bool SCALED = (KIND == KIND_FP8 || KIND == KIND_FP16X3);  // per-row scales
   constexpr uint32_t IDESC = sm100::idesc_f32acc(T::FMT, GEMM_BM, GEMM_BN);
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -275,6 +276,12 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
                 sm100::mma_tf32(d_tmem, a0, b0, IDESC, accum);
                 sm100::mma_tf32(d_tmem, a0, b1, IDESC, 1u);
                 sm100::mma_tf32(d_tmem, a1, b0, IDESC, 1u);
+              } else if (KIND == KIND_FP16X3) {
+                const uint64_t a1 = sm100::sdesc_k_sw128(a_kb1 + koff);
+                const uint64_t b1 = sm100::sdesc_k_sw128(b_base + GEMM_TILE_BYTES + koff);
+                sm100::mma_f16(d_tmem, a0, b0, IDESC, accum);
+                sm100::mma_f16(d_tmem, a0, b1, IDESC, 1u);
+                sm100::mma_f16(d_tmem, a1, b0, IDESC, 1u);
               } else if (KIND == KIND_BF16) {
                 sm100::mma_f16(d_tmem, a0, b0, IDESC, accum);
               } else {
@@ -309,8 +316,8 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       const int t0 = ch * args.tpc, t1 = min(args.ntiles, t0 + args.tpc);
       const int q = qt * GEMM_BM + qrow;
       const bool qvalid = q < args.nq;
-      const float qs = (KIND == KIND_FP8 && qvalid) ? args.qscale[q] : 1.f;
-      const float m2 = -2.f * qs;  // L2: ||y||^2 - 2 <x, y>, FP8 row scale folded in
+      const float qs = (SCALED && qvalid) ? args.qscale[q] : 1.f;
+      const float m2 = -2.f * qs;  // L2: ||y||^2 - 2 <x, y>, the query's row scale folded in
       const float xn_store = (MODE == MODE_STORE && args.xnorm && qvalid) ? args.xnorm[q] : -1.f;
       // Value-space threshold: keep dist <= thr (L2) or dist >= thr (inner product).  An
       // empty list passes every (finite) value; rows past nq get one that nothing passes.
@@ -353,7 +360,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
         if (lane < CW / 4) {
           if (!LARGEST)
             pre_y = __ldg(reinterpret_cast<const float4*>(args.ynorm + t * GEMM_BN + co) + lane);
-          if (KIND == KIND_FP8)  // the row scale is applied below
+          if (SCALED)  // the row scale is applied below
             pre_s = __ldg(reinterpret_cast<const float4*>(args.bscale + t * GEMM_BN + co) + lane);
         }
       };
@@ -364,7 +371,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
         __syncwarp();
         if (lane < CW / 4) {
           if (!LARGEST) reinterpret_cast<float4*>(sY)[lane] = pre_y;
-          if (KIND == KIND_FP8) reinterpret_cast<float4*>(sY + 128)[lane] = pre_s;
+          if (SCALED) reinterpret_cast<float4*>(sY + 128)[lane] = pre_s;
         }
         __syncwarp();
         if (t + 1 < t1) prefetch(t + 1);
@@ -376,7 +383,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
         // One batch = 32 accumulator columns of this lane's row, already in registers.
         auto batch = [&](float (&dist)[32], const int cb) {
           const int cbase = col0 + cb;  // database row of dist[0]
-          if (KIND == KIND_FP8) {
+          if (SCALED) {
             const float4* bs4 = reinterpret_cast<const float4*>(sY + 128 + cb);
 #pragma unroll
             for (int j4 = 0; j4 < 8; j4++) {
@@ -397,7 +404,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
               dist[j4 * 4 + 2] = fmaf(m2, dist[j4 * 4 + 2], y.z);
               dist[j4 * 4 + 3] = fmaf(m2, dist[j4 * 4 + 3], y.w);
             }
-          } else if (KIND == KIND_FP8) {
+          } else if (SCALED) {
 #pragma unroll
             for (int j = 0; j < 32; j++) dist[j] *= qs;
           }

@@ -11,6 +11,8 @@ gbk_status launch_dist_gemm_tf32x3(int mode, int kpr, bool largest, const CUtens
                                    const GemmArgs& a, int grid, size_t smem, cudaStream_t st);
 gbk_status launch_dist_gemm_bf16(int mode, int kpr, bool largest, const CUtensorMap* maps,
                                  const GemmArgs& a, int grid, size_t smem, cudaStream_t st);
+gbk_status launch_dist_gemm_fp16x3(int mode, int kpr, bool largest, const CUtensorMap* maps,
+                                   const GemmArgs& a, int grid, size_t smem, cudaStream_t st);
 gbk_status launch_dist_gemm_fp8(int mode, int kpr, bool largest, const CUtensorMap* maps,
                                 const GemmArgs& a, int grid, size_t smem, cudaStream_t st);
 

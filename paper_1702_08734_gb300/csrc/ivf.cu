@@ -332,7 +332,7 @@ gbk_status gbk_ivfpq_set_coarse_precision(gbk_index* ix, int32_t precision) {
   clear_error();
   GBK_REQUIRE(ix, "gbk_ivfpq_set_coarse_precision: NULL index");
   GBK_REQUIRE(precision == GBK_PREC_FP32 || precision == GBK_PREC_BF16 ||
-                  precision == GBK_PREC_FP8,
+                  precision == GBK_PREC_FP8 || precision == GBK_PREC_TF32X3,
               "gbk_ivfpq_set_coarse_precision: bad precision");
   ix->coarse_prec = precision;
   return GBK_OK;
@@ -694,7 +694,7 @@ gbk_status gbk_ivfpq_load(const char* path, gbk_index** out, void* stream) {
   } guard{ix};
   GBK_REQUIRE(h.ntotal >= 0 && h.ntotal <= (int64_t(1) << 32) - (int64_t(1) << 16),
               "gbk_ivfpq_load: bad vector count");
-  GBK_REQUIRE(h.coarse_prec >= GBK_PREC_FP32 && h.coarse_prec <= GBK_PREC_FP8 &&
+  GBK_REQUIRE(h.coarse_prec >= GBK_PREC_FP32 && h.coarse_prec <= GBK_PREC_TF32X3 &&
                   (h.codes_per_thread == 2 || h.codes_per_thread == 4 || h.codes_per_thread == 8) &&
                   h.blocks_per_sm >= 1 && h.blocks_per_sm <= 8 &&
                   (h.scan_threads == 256 || h.scan_threads == 384 || h.scan_threads == 512) &&

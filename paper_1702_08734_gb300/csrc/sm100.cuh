@@ -206,7 +206,7 @@ __host__ __device__ constexpr uint32_t idesc_f32acc(uint32_t fmt, int M, int N) 
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
-constexpr uint32_t FMT_TF32 = 2, FMT_BF16 = 1, FMT_E4M3 = 0;
+constexpr uint32_t FMT_TF32 = 2, FMT_BF16 = 1, FMT_E4M3 = 0, FMT_F16 = 0;  // F16: kind::f16
 
 }  // namespace sm100
 }  // namespace gbk

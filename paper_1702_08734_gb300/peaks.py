@@ -5,7 +5,8 @@ the kernel's own CUDA-event time from the library's profiler, not the operand
 preparation) at a shape where the tensor cores, not the output stores, bound it:
 nq = 8,192 queries against nb = 16,384 rows of d = 8,192 (2 d flops per 4 output bytes).  The
 float32-accurate precision issues three TF32 MMAs per product (hi x hi, hi x lo, lo x hi),
-so its executed TF32 rate is three times its algorithmic rate.  CUDA events on the
+so its executed TF32 rate is three times its algorithmic rate; the default float32-accurate
+precision issues three FP16 MMAs per product the same way (reported as "fp16").  CUDA events on the
 launching stream, one warm-up and `reps` timed calls.  The result is a rate this kernel
 reaches, i.e. a lower bound of the hardware's; the benchmark divides by the larger of it
 and the nominal ratio to the measured BF16 GEMM rate.
@@ -31,8 +32,10 @@ def measure(reps: int = 3, nq: int = 8192, nb: int = 16384, d: int = 8192):
     out = {"shape": {"nq": nq, "nb": nb, "d": d}, "reps": reps,
            "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
            "gpu": torch.cuda.get_device_name(0)}
-    kern = {"fp32": "dist_gemm_tf32x3", "bf16": "dist_gemm_bf16", "fp8": "dist_gemm_fp8"}
-    for prec, passes in (("fp32", 3), ("bf16", 1), ("fp8", 1)):
+    kern = {"fp32": "dist_gemm_fp16x3", "tf32x3": "dist_gemm_tf32x3", "bf16": "dist_gemm_bf16",
+            "fp8": "dist_gemm_fp8"}
+    names = {"fp32": "fp16", "tf32x3": "tf32", "bf16": "bf16", "fp8": "fp8"}
+    for prec, passes in (("tf32x3", 3), ("fp32", 3), ("bf16", 1), ("fp8", 1)):
         g.pairwise_distances(xq, xb, metric="ip", precision=prec)
         torch.cuda.synchronize()
         g.profile_enable(True)
@@ -42,12 +45,12 @@ def measure(reps: int = 3, nq: int = 8192, nb: int = 16384, d: int = 8192):
         g.profile_enable(False)
         times = [t for nm, t in g.profile_read() if nm == kern[prec]]
         ms = sum(times) / len(times)
-        name = {"fp32": "tf32", "bf16": "bf16", "fp8": "fp8"}[prec]
+        name = names[prec]
         out[name + "_tflops"] = passes * flops / (ms / 1e3) / 1e12
         out[name + "_ms"] = ms
     out["note"] = ("executed tensor-core rate of the library's pairwise GEMM kernel (its output "
-                   "stores included, operand preparation not); tf32 counts the 3 MMAs of the "
-                   "float32-accurate split")
+                   "stores included, operand preparation not); tf32 and fp16 count the 3 MMAs of "
+                   "the float32-accurate splits")
     return out
 
 

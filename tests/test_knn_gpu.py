@@ -41,13 +41,16 @@ def _check_knn(xq, xb, D, I, k, metric="l2", rtol=RTOL):
         assert np.all(ex >= kth - tol)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
 @pytest.mark.parametrize("d", [8, 32, 100, 128])
 @pytest.mark.parametrize("metric", ["l2", "ip"])
-def test_pairwise_fp32_matches_float64(gbk, d, metric):
+def test_pairwise_fp32_matches_float64(gbk, d, metric, prec):
+    # both float32-accurate kinds: FP16 hi/lo of power-of-two scaled rows (the default) and
+    # TF32 hi/lo
     xq = datagen.gaussian_matrix(500 + d, 300, d)
     xb = datagen.gaussian_matrix(600 + d, 1000, d)
     out = gbk.pairwise_distances(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(),
-                                 metric=metric).cpu().numpy().astype(np.float64)
+                                 metric=metric, precision=prec).cpu().numpy().astype(np.float64)
     x = xq.astype(np.float64)
     y = xb.astype(np.float64)
     ref = x @ y.T if metric == "ip" else ((x[:, None, :] - y[None]) ** 2).sum(-1)
@@ -73,11 +76,12 @@ def test_pairwise_low_precision_error_bounds(gbk, prec, tol):
                                        (300, 20000, 128, 100), (257, 5000, 32, 256),
                                        (77, 4099, 100, 33)])
 @pytest.mark.parametrize("metric", ["l2", "ip"])
-def test_knn_fp32_vs_oracle(gbk, nq, nb, d, k, metric):
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_knn_fp32_vs_oracle(gbk, nq, nb, d, k, metric, prec):
     xq = datagen.gaussian_matrix(800 + nq, nq, d)
     xb = datagen.gaussian_matrix(900 + nb, nb, d)
     D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), k,
-                         metric=metric)
+                         metric=metric, precision=prec)
     _check_knn(xq, xb, D, I, k, metric)
 
 
@@ -233,12 +237,34 @@ def test_clustered_near_duplicates_in_one_tile(gbk):
     assert np.array_equal(np.sort(I[2:], axis=1), np.sort(Io[2:], axis=1))
 
 
-def test_small_exact_configuration(gbk):
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_small_exact_configuration(gbk, prec):
     # the small exact configuration: database 65,536 x 128 and 1,024 queries, N(0,1), k = 10
     xb = datagen.gaussian_matrix(101, 65536, 128)
     xq = datagen.gaussian_matrix(102, 1024, 128)
-    D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), 10)
+    D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), 10,
+                         precision=prec)
     _check_knn(xq, xb, D, I, 10)
+
+
+def test_fp32_wide_dynamic_range(gbk):
+    # rows spanning many octaves (each row scaled by its own power of two, elements down to
+    # 2^-20 of the row's largest) and rows of very different norms: the FP16 pieces of the
+    # scaled rows still give float32-accurate distances
+    rng = np.random.default_rng(12)
+    xb = (rng.standard_normal((20000, 64)) * np.exp2(rng.integers(-20, 1, (20000, 64)))
+          * np.exp2(rng.integers(-30, 30, (20000, 1)))).astype(np.float32)
+    xq = xb[rng.integers(0, 20000, 150)] * np.float32(1.0001)
+    for metric in ("l2", "ip"):
+        D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), 10,
+                             metric=metric)
+        D32, I32 = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), 10,
+                                 metric=metric, precision="tf32x3")
+        Do, Io = oracle.knn(xq, xb, 10, metric=metric)
+        for Dg in (D, D32):
+            Dg = Dg.cpu().numpy().astype(np.float64)
+            scale = np.abs(Do).max(1, keepdims=True) + 1e-30
+            assert np.all(np.abs(Dg - Do) <= 1e-5 * scale)
 
 
 @pytest.mark.parametrize("d,offset", [(32, 1), (30, 0)])
@@ -262,12 +288,14 @@ def test_low_precision_rerank_unaligned_rows(gbk, d, offset):
 
 @pytest.mark.parametrize("d", [160, 784, 1000])
 @pytest.mark.parametrize("k", [1, 10, 100])
-def test_knn_long_rows_stream_query_tile(gbk, d, k):
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_knn_long_rows_stream_query_tile(gbk, d, k, prec):
     # rows too long to keep a 128-query tile resident beside the ring (float32-accurate
     # pieces beyond d = 128): the query k-blocks travel with the database's through the ring
     xq = datagen.gaussian_matrix(91, 200, d)
     xb = datagen.gaussian_matrix(92, 3000, d)
-    D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), k)
+    D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), k,
+                         precision=prec)
     _check_knn(xq, xb, D, I, k)
 
 
