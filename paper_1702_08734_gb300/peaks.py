@@ -4,12 +4,11 @@ Times the GEMM kernel of gbk_pairwise_distances (inner products, every output wr
 the kernel's own CUDA-event time from the library's profiler, not the operand
 preparation) at a shape where the tensor cores, not the output stores, bound it:
 nq = 8,192 queries against nb = 16,384 rows of d = 8,192 (2 d flops per 4 output bytes).  The
-float32-accurate precision issues three TF32 MMAs per product (hi x hi, hi x lo, lo x hi),
-so its executed TF32 rate is three times its algorithmic rate; the default float32-accurate
-precision issues three FP16 MMAs per product the same way (reported as "fp16").  CUDA events on the
-launching stream, one warm-up and `reps` timed calls.  The result is a rate this kernel
-reaches, i.e. a lower bound of the hardware's; the benchmark divides by the larger of it
-and the nominal ratio to the measured BF16 GEMM rate.
+default float32-accurate precision issues three FP16 MMAs per product (hi x hi, hi x lo,
+lo x hi; reported as "fp16"), the TF32 split three TF32 MMAs (reported as "tf32"): their
+executed rates are three times their algorithmic rates.  The kernel's own CUDA-event time
+on the launching stream, one warm-up and `reps` timed calls.  The result is a rate this
+kernel reaches, i.e. a lower bound of the hardware's.
 
     python -m paper_1702_08734_gb300.peaks [out.json]
 """
