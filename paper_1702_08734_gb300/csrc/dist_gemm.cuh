@@ -20,8 +20,10 @@
 //               candidate list (bitonic network over shuffles).
 // Work item = (query tile, database chunk); items are chunk-major so all CTAs sweep
 // the database in near lockstep and each B tile is fetched from HBM about once.  A
-// global per-query threshold (ordered key, atomicMin) carries the k-th distance of
-// finished chunks into later ones.
+// global per-query threshold (ordered key, atomicMin) is shared by all lists of a query:
+// every list merge publishes its k-th distance and every epilogue thread re-reads the key
+// once per tile, so chunks running at the same time and both column halves filter with
+// the best k-th distance found so far.
 //
 // Precision variants (KIND): TF32X3 keeps float32 accuracy by splitting each operand
 // x = hi + lo into TF32 pieces and accumulating hi*hi + hi*lo + lo*hi (Ootomo & Yokota,

@@ -75,12 +75,16 @@ __device__ __forceinline__ float batch_best32(const float (&v)[32]) {
 
 // Warp-cooperative merge of every lane's candidate queue holding more than `limit`
 // entries into that lane's sorted list (queue of lane l: sQ[l * GEMM_QSTRIDE ...] as
-// {value bits, column}; list of lane l at part + l * rowstride, KPR*32 composites).  The
-// merging lane's threshold becomes its list's k-th value.
+// {value bits, column}; list of lane l at part + l * rowstride, KPR*32 composites).  Once
+// the merging lane's list holds k values its k-th tightens the lane's threshold and is
+// published to the query's global threshold key `gthr` (every list of a query - other
+// chunks, the other column half - then filters with it: k values at or below it exist,
+// so nothing worse can be among the k nearest).
 template <int KPR, bool LARGEST>
 __device__ __forceinline__ void merge_queues(int limit, int& cnt, float& thr, const uint2* sQ,
                                              uint64_t* part, int64_t rowstride, int k,
-                                             int quarter, int lane, uint64_t pol) {
+                                             int quarter, int lane, uint64_t pol,
+                                             uint32_t* gthr) {
   if constexpr (KPR == 0) return;  // k = 1 keeps no lists
   constexpr int KR = KPR > 0 ? KPR : 1;
   unsigned m = __ballot_sync(FULL_MASK, cnt > limit);
@@ -112,7 +116,11 @@ __device__ __forceinline__ void merge_queues(int limit, int& cnt, float& thr, co
     tk = shfl64(tk, kk & 31);
     if (lane == l) {
       cnt = 0;
-      if (tk != ~0ull) thr = key_value((uint32_t)(tk >> 32), LARGEST);
+      if (tk != ~0ull) {
+        const float t = key_value((uint32_t)(tk >> 32), LARGEST);
+        thr = LARGEST ? fmaxf(thr, t) : fminf(thr, t);
+        if (gthr) atomicMin(gthr, (uint32_t)(tk >> 32));
+      }
     }
   }
   __syncwarp();
@@ -326,6 +334,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       int cnt = 0;
       float bestd = PASS_ALL;  // k = 1: running best; a strict improvement keeps the lowest column
       int besti = -1;
+      uint32_t* const gthr = (QUEUES && qvalid) ? args.thr_key + q : nullptr;
       if (MODE == MODE_SELECT) {
         if (!qvalid) {
           thr = -PASS_ALL;
@@ -356,7 +365,9 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       // ahead into registers so the global-load latency hides behind a tile of work, then
       // staged in shared memory (the values are the same for the warp's 32 rows).
       float4 pre_y = make_float4(0.f, 0.f, 0.f, 0.f), pre_s = pre_y;
+      uint32_t pre_g = NAN_KEY;  // the query's global threshold key, read a tile ahead
       auto prefetch = [&](int t) {
+        if (QUEUES && gthr) pre_g = __ldcg(gthr);
         if (lane < CW / 4) {
           if (!LARGEST)
             pre_y = __ldg(reinterpret_cast<const float4*>(args.ynorm + t * GEMM_BN + co) + lane);
@@ -374,6 +385,10 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           if (SCALED) reinterpret_cast<float4*>(sY + 128)[lane] = pre_s;
         }
         __syncwarp();
+        if (QUEUES && pre_g != NAN_KEY) {  // lists of other chunks / halves of this query
+          const float g = key_value(pre_g, LARGEST);
+          thr = LARGEST ? fmaxf(thr, g) : fminf(thr, g);
+        }
         if (t + 1 < t1) prefetch(t + 1);
         ok = sm100::mbar_wait(&acc_full[acc], (gtile / GEMM_NACC) & 1u, args.status, abort_flag);
         if (!ok) break;
@@ -462,7 +477,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
                   }
                 }
                 merge_queues<KPR, LARGEST>(GEMM_QCAP - 16, cnt, thr, sQh, pbase, rowstride,
-                                           args.k, quarter, lane, lpol);
+                                           args.k, quarter, lane, lpol, gthr);
               }
             }
           }
@@ -515,14 +530,9 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       if (!ok) break;
       if (MODE == MODE_SELECT) {
         if (QUEUES) {
+          // (every merge publishes its list's k-th value to the query's global threshold)
           merge_queues<KPR, LARGEST>(0, cnt, thr, sQh, pbase, rowstride, args.k, quarter, lane,
-                                     lpol);
-          // publish this chunk's k-th distance as an upper bound for later chunks
-          if (qvalid) {
-            const uint64_t* Lg = args.part + ((int64_t)q * lists + ch * EPI + half) * args.kp;
-            const uint64_t tk = ld_keep(Lg + args.k - 1, lpol);
-            if (tk != ~0ull) atomicMin(&args.thr_key[q], (uint32_t)(tk >> 32));
-          }
+                                     lpol, gthr);
         } else if (qvalid) {
           args.part[(int64_t)q * lists + ch * EPI + half] =
               besti >= 0 ? composite(ordered_key(bestd, LARGEST), (uint32_t)besti) : ~0ull;
