@@ -148,7 +148,8 @@ gbk_status gbk_row_norms(const float* x, int64_t n, int32_t d, float* out, void*
 
 /* Options of gbk_knn_brute (NULL = defaults). */
 typedef struct gbk_knn_opts {
-  int32_t precision; /* GBK_PREC_FP32 (default), GBK_PREC_BF16 or GBK_PREC_FP8          */
+  int32_t precision; /* GBK_PREC_FP32 (default), GBK_PREC_TF32X3, GBK_PREC_BF16 or      */
+                     /* GBK_PREC_FP8                                                    */
   int32_t kprime;    /* BF16/FP8: candidates re-ranked in float32 (0 = 4k for k <= 16,   */
                      /* k + k/4 above; >= k, <= 1024)                                  */
   int32_t chunks;    /* database chunks of the work decomposition (0 = planned)          */
@@ -161,6 +162,14 @@ typedef struct gbk_knn_opts {
                          cover on the float32 path and returns its result there, so every
                          row is the float32 top-k (the call then synchronises `stream`
                          once, to learn how many queries to re-run)                     */
+  int32_t prefilter;  /* threshold pre-pass of the fused selection: -1 off, 1 on for
+                         k > 1, 0 on for k >= 32 (64 with GBK_PREC_TF32X3; BF16/FP8
+                         count the over-fetched k'); either only where the database holds
+                         at least 4k blocks of 64 rows (128 with GBK_PREC_TF32X3).  The
+                         pre-pass takes the best distance of every (query, block) over
+                         the first sixteenth of the database; their k-th best bounds the
+                         k-th nearest distance, so the fused selection starts with that
+                         threshold.  Results are the same either way.                    */
 } gbk_knn_opts;
 
 /*
@@ -170,14 +179,16 @@ typedef struct gbk_knn_opts {
  *   xq [nq][d], xb [nb][d] float32;  1 <= k <= min(nb, GBK_MAX_K);  metric GBK_METRIC_*
  *   D  [nq][k] float32 out: squared L2 distances ascending (clamped at 0), or inner
  *      products descending;  I [nq][k] int64 out: database row numbers.
- * GBK_PREC_FP32 keeps float32 accuracy (TF32 hi/lo split).  BF16/FP8 select kprime
+ * GBK_PREC_FP32 keeps float32 accuracy (FP16 hi/lo split of power-of-two-scaled rows,
+ * three tensor-core passes; GBK_PREC_TF32X3 the TF32 split).  BF16/FP8 select kprime
  * candidates in low precision, then recompute their distances directly in float32 and
  * keep the best k.  A query is certified when the k'-th low-precision distance minus
  * the error bound exceeds the k-th re-ranked distance (plus, for inner product), which
  * proves no other database row belongs to the top k.
  * Limits: nb, nq < 2^31; BF16/FP8 d <= 8192 (the float32 re-rank).  A 128-query tile of
- * the GEMM stays in shared memory while d <= 128 (FP32), 512 (BF16) or 1024 (FP8) with
- * candidate lists (k > 1), 128 / 704 / 1408 without; longer rows stream the query
+ * the GEMM stays in shared memory while d <= 192 (FP32), 128 (TF32X3), 512 (BF16) or
+ * 1024 (FP8) with candidate lists (k > 1), 256 / 128 / 704 / 1408 without; longer rows
+ * stream the query
  * k-blocks through the shared-memory ring beside the database's (same results).  Errors:
  * GBK_EINVAL, GBK_EUNSUPPORTED, GBK_ENOMEM, GBK_ECUDA.  Inputs must be finite.
  */

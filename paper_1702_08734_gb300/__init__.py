@@ -202,7 +202,8 @@ PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "tf32x3": 3}
 class KnnOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("kprime", ctypes.c_int32),
                 ("chunks", ctypes.c_int32), ("certified", ctypes.c_void_p),
-                ("error_bound", ctypes.c_void_p), ("exact", ctypes.c_int32)]
+                ("error_bound", ctypes.c_void_p), ("exact", ctypes.c_int32),
+                ("prefilter", ctypes.c_int32)]
 
 
 def _metric(m):
@@ -211,13 +212,14 @@ def _metric(m):
 
 def knn_brute(xq: torch.Tensor, xb: torch.Tensor, k: int, metric="l2", precision="fp32",
               kprime: int = 0, chunks: int = 0, out=None, certify: bool = False,
-              exact: bool = False):
+              exact: bool = False, prefilter: int = 0):
     """Exact k-NN (squared L2 ascending, or inner product descending) with int64 ids.
 
     precision "bf16"/"fp8": over-fetch kprime candidates, exact float32 re-rank; with
     certify=True also returns (certified [nq] int32, error_bound [nq] float32); with
     exact=True the queries the certificate does not cover are re-run in float32
-    (certified = 2 for them)."""
+    (certified = 2 for them).  prefilter: threshold pre-pass of the fused selection (1 on,
+    -1 off, 0 automatic); the results are the same either way."""
     _dev(xq, torch.float32, "xq")
     _dev(xb, torch.float32, "xb")
     nq, d = xq.shape
@@ -235,7 +237,8 @@ def knn_brute(xq: torch.Tensor, xb: torch.Tensor, k: int, metric="l2", precision
         eb = torch.empty(nq, dtype=torch.float32, device=xq.device)
     opts = KnnOpts(PRECISIONS[precision], int(kprime), int(chunks),
                    cert.data_ptr() if cert is not None else None,
-                   eb.data_ptr() if eb is not None else None, int(bool(exact)))
+                   eb.data_ptr() if eb is not None else None, int(bool(exact)),
+                   int(prefilter))
     _call("gbk_knn_brute", _ptr(xq), nq, _ptr(xb), nb, int(d), int(k), _metric(metric), _ptr(D),
           _ptr(I), ctypes.byref(opts), _stream())
     return (D, I, cert, eb) if certify else (D, I)

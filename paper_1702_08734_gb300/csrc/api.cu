@@ -107,13 +107,17 @@ struct ProfRec {
 std::mutex g_prof_mu;
 bool g_prof_on = false;
 std::vector<ProfRec> g_prof;
+thread_local const char* t_prof_suffix = "";
 }  // namespace
+
+ProfSuffix::ProfSuffix(const char* suffix) : prev(t_prof_suffix) { t_prof_suffix = suffix; }
+ProfSuffix::~ProfSuffix() { t_prof_suffix = prev; }
 
 ProfScope::ProfScope(const char* name, cudaStream_t st) : stream(st) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on || g_prof.size() >= 4096) return;
   ProfRec r;
-  snprintf(r.name, sizeof(r.name), "%s", name);
+  snprintf(r.name, sizeof(r.name), "%s%s", name, t_prof_suffix);
   if (cudaEventCreate(&r.e0) != cudaSuccess) return;
   if (cudaEventCreate(&r.e1) != cudaSuccess) return;
   cudaEventRecord(r.e0, st);
@@ -247,6 +251,8 @@ gbk_status gbk_knn_brute(const float* xq, int64_t nq, const float* xb, int64_t n
     GBK_REQUIRE(opts->precision >= GBK_PREC_FP32 && opts->precision <= GBK_PREC_TF32X3,
                 "gbk_knn_brute: bad precision");
     GBK_REQUIRE(opts->chunks >= 0, "gbk_knn_brute: chunks < 0");
+    GBK_REQUIRE(opts->prefilter >= -1 && opts->prefilter <= 1,
+                "gbk_knn_brute: prefilter must be -1, 0 or 1");
     GBK_REQUIRE(opts->kprime == 0 || (opts->kprime >= k && opts->kprime <= GBK_MAX_K),
                 "gbk_knn_brute: kprime must be 0 or in [k, %d]", GBK_MAX_K);
     plan.prec = opts->precision;
@@ -255,6 +261,7 @@ gbk_status gbk_knn_brute(const float* xq, int64_t nq, const float* xb, int64_t n
     plan.certified = opts->certified;
     plan.error_bound = opts->error_bound;
     plan.exact = opts->exact != 0;
+    plan.prefilter = opts->prefilter;
   }
   return knn_run(xq, nq, xb, nb, d, k, metric, D, I, plan, as_stream(stream));
 }

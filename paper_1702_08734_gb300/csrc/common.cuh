@@ -48,6 +48,13 @@ struct ProfScope {
   ProfScope(const char* name, cudaStream_t st);
   ~ProfScope();
 };
+// While one is alive on a host thread, the names its ProfScopes record carry `suffix`
+// (e.g. the kernels of a helper pass told apart from the main pass's).
+struct ProfSuffix {
+  const char* prev;
+  explicit ProfSuffix(const char* suffix);
+  ~ProfSuffix();
+};
 
 // RAII scratch buffer (freed stream-ordered at scope exit).
 struct Scratch {

@@ -109,8 +109,10 @@ struct GemmArgs {
   const float* bscale;   // [ntiles*128] per-row database scale (FP8), else null
   uint64_t* part;        // SELECT: [nq][chunks * EPI][kp] sorted composite lists
   uint32_t* thr_key;     // SELECT: [nq] global threshold keys (init 0xffffffff)
-  float* out;            // STORE: [nq][ldo] partial distances
+  float* out;            // STORE: [nq][ldo] partial distances; tile_min: [nq][ldo] minima
   int64_t ldo;
+  int tile_min;          // SELECT, k = 1: out[q * ldo + tile * EPI + half] = the best value of
+                         // each (query, tile, column half) instead of one arg-best per list
   uint32_t* status;
 };
 

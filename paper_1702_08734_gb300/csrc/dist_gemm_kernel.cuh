@@ -6,11 +6,12 @@
 namespace gbk {
 
 struct GemmSmemLayout {
-  uint32_t a_off, b_off, q_off, y_off, bar_off, total;
+  uint32_t a_off, b_off, q_off, y_off, h_off, bar_off, total;
 };
 
 // Offsets relative to a 1024-byte aligned base (TMA 128B-swizzle tiles need it).  Per
-// epilogue warp a 1 KB slice stages the tile's database norms (and FP8 scales).
+// epilogue warp a 1 KB slice stages the tile's database norms (and row scales); with two
+// column halves keeping lists, one 8-byte half-list key per (half, query row) follows.
 __host__ __device__ inline GemmSmemLayout gemm_smem_layout(int pieces, int nkb, int stages,
                                                            bool queues, int epi) {
   GemmSmemLayout L;
@@ -19,7 +20,9 @@ __host__ __device__ inline GemmSmemLayout gemm_smem_layout(int pieces, int nkb, 
   L.q_off = L.b_off + (uint32_t)stages * pieces * GEMM_TILE_BYTES;
   const uint32_t qbytes = queues ? (uint32_t)(epi * GEMM_BM * GEMM_QSTRIDE * 8) : 0u;
   L.y_off = (L.q_off + qbytes + 15u) & ~15u;
-  L.bar_off = (L.y_off + (uint32_t)(epi * 4 * 1024) + 63u) & ~63u;
+  L.h_off = L.y_off + (uint32_t)(epi * 4 * 1024);
+  const uint32_t hbytes = (queues && epi == 2) ? 2u * GEMM_BM * 8u : 0u;
+  L.bar_off = (L.h_off + hbytes + 63u) & ~63u;
   L.total = L.bar_off + 8u * (2u + 2u * (uint32_t)stages + 2u * GEMM_NACC) + 16u;
   return L;
 }
@@ -73,18 +76,39 @@ __device__ __forceinline__ float batch_best32(const float (&v)[32]) {
   return LARGEST ? fmaxf(c, b[3]) : fminf(c, b[3]);
 }
 
+// Threshold sharing between the candidate lists of one query.  Any value t with k values
+// at or below it among the rows seen so far bounds the k-th nearest distance, so every
+// list of the query may filter with it: the k-th value of any one list, or - for the two
+// column halves of one tile, which see disjoint rows of the same chunk in lockstep - the
+// worse of the two halves' ceil(k/2)-th values.  Bounds are published as ordered keys
+// (smaller = better): to the query's global key (atomicMin; read by every list of the
+// query once per tile) and, per half, to a shared-memory word tagged with the work item,
+// so a half only pairs with the other half's list of the same query tile.
+struct ThrShare {
+  uint32_t* gthr;                  // the query's global key (null: row past nq)
+  volatile uint64_t* hmine;        // this warp's 32 rows' {item, key} words (null: one half)
+  const volatile uint64_t* hother; // the other half's words for the same rows
+  uint32_t tag;                    // work item
+  uint32_t own;                    // key of this lane's ceil(k/2)-th list value, or NAN_KEY
+};
+
+template <bool LARGEST>
+__device__ __forceinline__ void tighten(float& thr, uint32_t key) {
+  if (key == NAN_KEY) return;
+  const float t = key_value(key, LARGEST);
+  thr = LARGEST ? fmaxf(thr, t) : fminf(thr, t);
+}
+
 // Warp-cooperative merge of every lane's candidate queue holding more than `limit`
 // entries into that lane's sorted list (queue of lane l: sQ[l * GEMM_QSTRIDE ...] as
-// {value bits, column}; list of lane l at part + l * rowstride, KPR*32 composites).  Once
-// the merging lane's list holds k values its k-th tightens the lane's threshold and is
-// published to the query's global threshold key `gthr` (every list of a query - other
-// chunks, the other column half - then filters with it: k values at or below it exist,
-// so nothing worse can be among the k nearest).
+// {value bits, column}; list of lane l at part + l * rowstride, KPR*32 composites).  The
+// merging lane's threshold then tightens to its list's k-th value or the pair bound of
+// the two halves, whichever is better, and that bound is published (ThrShare).
 template <int KPR, bool LARGEST>
 __device__ __forceinline__ void merge_queues(int limit, int& cnt, float& thr, const uint2* sQ,
                                              uint64_t* part, int64_t rowstride, int k,
                                              int quarter, int lane, uint64_t pol,
-                                             uint32_t* gthr) {
+                                             ThrShare& ts) {
   if constexpr (KPR == 0) return;  // k = 1 keeps no lists
   constexpr int KR = KPR > 0 ? KPR : 1;
   unsigned m = __ballot_sync(FULL_MASK, cnt > limit);
@@ -114,13 +138,25 @@ __device__ __forceinline__ void merge_queues(int limit, int& cnt, float& thr, co
     for (int r = 0; r < KR; r++)  // masked OR, not an indexed read (keeps L in registers)
       tk |= L[r] & (0ull - (uint64_t)(r == (kk >> 5)));
     tk = shfl64(tk, kk & 31);
+    uint64_t th = ~0ull;  // element ceil(k/2)-1 (only with two halves)
+    if (ts.hmine) {
+      const int kh = (k + 1) / 2 - 1;
+      th = 0;
+#pragma unroll
+      for (int r = 0; r < KR; r++) th |= L[r] & (0ull - (uint64_t)(r == (kh >> 5)));
+      th = shfl64(th, kh & 31);
+    }
     if (lane == l) {
       cnt = 0;
-      if (tk != ~0ull) {
-        const float t = key_value((uint32_t)(tk >> 32), LARGEST);
-        thr = LARGEST ? fmaxf(thr, t) : fminf(thr, t);
-        if (gthr) atomicMin(gthr, (uint32_t)(tk >> 32));
+      uint32_t best = tk != ~0ull ? (uint32_t)(tk >> 32) : NAN_KEY;
+      if (th != ~0ull) {
+        ts.own = (uint32_t)(th >> 32);
+        ts.hmine[l] = ((uint64_t)ts.tag << 32) | ts.own;
+        const uint64_t o = ts.hother[l];
+        if ((uint32_t)(o >> 32) == ts.tag) best = min(best, max(ts.own, (uint32_t)o));
       }
+      tighten<LARGEST>(thr, best);
+      if (ts.gthr && best != NAN_KEY) atomicMin(ts.gthr, best);
     }
   }
   __syncwarp();
@@ -161,6 +197,8 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
   uint64_t* acc_empty = acc_full + GEMM_NACC;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + GEMM_NACC);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  constexpr bool PAIR = QUEUES && EPI == 2;  // the two column halves share a pair bound
+  volatile uint64_t* sH = reinterpret_cast<volatile uint64_t*>(smem + lay.h_off);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nitems = args.nqt * args.chunks;
@@ -179,6 +217,8 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
     *abort_flag = 0;
     sm100::fence_mbar_init();
   }
+  if (PAIR)  // no item has tag ~0: stale words never pair
+    for (int i = threadIdx.x; i < 2 * GEMM_BM; i += blockDim.x) sH[i] = ~0ull;
   if (warp == 1) {
     sm100::tmem_alloc(tmem_slot, GEMM_NACC * GEMM_BN);
     sm100::tmem_relinquish();
@@ -335,6 +375,12 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       float bestd = PASS_ALL;  // k = 1: running best; a strict improvement keeps the lowest column
       int besti = -1;
       uint32_t* const gthr = (QUEUES && qvalid) ? args.thr_key + q : nullptr;
+      ThrShare ts;
+      ts.gthr = gthr;
+      ts.hmine = PAIR ? sH + half * GEMM_BM + quarter * 32 : nullptr;
+      ts.hother = PAIR ? sH + (1 - half) * GEMM_BM + quarter * 32 : nullptr;
+      ts.tag = (uint32_t)item;
+      ts.own = NAN_KEY;
       if (MODE == MODE_SELECT) {
         if (!qvalid) {
           thr = -PASS_ALL;
@@ -385,9 +431,12 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           if (SCALED) reinterpret_cast<float4*>(sY + 128)[lane] = pre_s;
         }
         __syncwarp();
-        if (QUEUES && pre_g != NAN_KEY) {  // lists of other chunks / halves of this query
-          const float g = key_value(pre_g, LARGEST);
-          thr = LARGEST ? fmaxf(thr, g) : fminf(thr, g);
+        if (QUEUES) {
+          tighten<LARGEST>(thr, pre_g);  // lists of other chunks / halves of this query
+          if (PAIR && ts.own != NAN_KEY) {  // this tile's other half
+            const uint64_t o = ts.hother[lane];
+            if ((uint32_t)(o >> 32) == ts.tag) tighten<LARGEST>(thr, max(ts.own, (uint32_t)o));
+          }
         }
         if (t + 1 < t1) prefetch(t + 1);
         ok = sm100::mbar_wait(&acc_full[acc], (gtile / GEMM_NACC) & 1u, args.status, abort_flag);
@@ -477,7 +526,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
                   }
                 }
                 merge_queues<KPR, LARGEST>(GEMM_QCAP - 16, cnt, thr, sQh, pbase, rowstride,
-                                           args.k, quarter, lane, lpol, gthr);
+                                           args.k, quarter, lane, lpol, ts);
               }
             }
           }
@@ -525,6 +574,10 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           batch(d0, b * 64);
           batch(d1, b * 64 + 32);
         }
+        if (MODE == MODE_SELECT && args.tile_min) {
+          if (qvalid) args.out[(int64_t)q * args.ldo + t * EPI + half] = bestd;
+          bestd = PASS_ALL;
+        }
         }
       }
       if (!ok) break;
@@ -532,8 +585,8 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
         if (QUEUES) {
           // (every merge publishes its list's k-th value to the query's global threshold)
           merge_queues<KPR, LARGEST>(0, cnt, thr, sQh, pbase, rowstride, args.k, quarter, lane,
-                                     lpol, gthr);
-        } else if (qvalid) {
+                                     lpol, ts);
+        } else if (qvalid && !args.tile_min) {
           args.part[(int64_t)q * lists + ch * EPI + half] =
               besti >= 0 ? composite(ordered_key(bestd, LARGEST), (uint32_t)besti) : ~0ull;
         }

@@ -25,6 +25,8 @@ struct KnnPlan {
   int32_t* certified = nullptr;  // low precision: [nq] 1 if provably the float32 top-k
   float* error_bound = nullptr;  // low precision: [nq] bound on |low - exact| distance
   bool exact = false;            // low precision: re-run uncertified queries in float32
+  int prefilter = 0;             // threshold pre-pass of the fused selection: 1 on, -1 off,
+                                 // 0 automatic
 };
 
 gbk_status prepare_operand(const float* x, int64_t n, int d, int prec, int64_t nrows_pad,

@@ -183,9 +183,10 @@ def sift_like():
 
 
 @pytest.mark.parametrize("k", [10, 100])
-def test_benchmark_workload_sampled(gbk, sift_like, k):
+@pytest.mark.parametrize("prefilter", [-1, 1])
+def test_benchmark_workload_sampled(gbk, sift_like, k, prefilter):
     xq, xb = sift_like
-    D, I = gbk.knn_brute(xq, xb, k)
+    D, I = gbk.knn_brute(xq, xb, k, prefilter=prefilter)
     torch.cuda.synchronize()
     sample = np.unique(datagen.randint(213, 0, 12, xq.shape[0]))
     xs = xq[torch.from_numpy(sample).cuda()].cpu().numpy()
@@ -212,6 +213,36 @@ def test_fused_large_k(gbk, prec, metric):
         D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), k,
                              metric=metric, precision=prec, exact=True)
         _check_knn(xq, xb, D, I, k, metric)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16"])
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+@pytest.mark.parametrize("k", [2, 33, 100, 256])
+def test_prefilter_does_not_change_results(gbk, prec, metric, k):
+    # the threshold pre-pass only removes rows that cannot be among the k best: the
+    # output is bit-identical with and without it (the TF32 split at k = 256 has too few
+    # 128-row blocks for it and runs without, as the documented rule says)
+    xq = torch.from_numpy(datagen.gaussian_matrix(75, 300, 64)).cuda()
+    xb = torch.from_numpy(datagen.gaussian_matrix(76, 100000, 64)).cuda()
+    D0, I0 = gbk.knn_brute(xq, xb, k, metric=metric, precision=prec, prefilter=-1)
+    D1, I1 = gbk.knn_brute(xq, xb, k, metric=metric, precision=prec, prefilter=1)
+    assert torch.equal(I0, I1) and torch.equal(D0, D1)
+
+
+def test_prefilter_integer_lattice_ties(gbk):
+    # exact distances with many ties (duplicated rows, equidistant lattice points): the
+    # pre-pass bound equals some rows' distances, which must still be kept, so the lower-id
+    # tie order of the oracle holds bit for bit
+    rng = np.random.default_rng(6)
+    xb = rng.integers(-2, 3, size=(80000, 12)).astype(np.float32)  # > 65,536: fused path
+    xb[70000:71000] = xb[:1000]
+    xq = rng.integers(-2, 3, size=(150, 12)).astype(np.float32)
+    for k in (7, 64, 100):
+        D, I = gbk.knn_brute(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda(), k,
+                             prefilter=1)
+        Do, Io = oracle.knn(xq, xb, k)
+        np.testing.assert_array_equal(I.cpu().numpy(), Io)
+        np.testing.assert_array_equal(D.cpu().numpy(), Do.astype(np.float32))
 
 
 def test_clustered_near_duplicates_in_one_tile(gbk):
