@@ -493,6 +493,7 @@ gbk_status gemm_launch(int mode, int kpr, bool largest, const PreparedOperand& Q
   }
   a.stages = stages;
   a.nkb = Q.nkb;
+  a.dual = stages >= 2 * Q.nkb ? 1 : 0;
   // at least half the SM's shared memory, so one CTA per SM owns the TMEM it allocates
   const GemmSmemLayout lf = a.stream_a ? gemm_smem_layout(2 * pieces, 0, stages, queues, epi)
                                        : gemm_smem_layout(pieces, Q.nkb, stages, queues, epi);

@@ -4,14 +4,15 @@
 // selection and writes D' once, section 5.1; on sm_103a the accumulator tile can be
 // filtered straight out of tensor memory).
 //
-// CTA = 64 + 128 * EPI threads, one per SM (persistent):
+// CTA = 96 + 128 * EPI threads, one per SM (persistent):
 //   warp 0      TMA producer: the 128-query A tile (all of d, resident for a work item)
 //               and a ring of 128-row database B k-blocks (128 bytes of K per row,
 //               SWIZZLE_128B boxes);
-//   warp 1      TMEM allocator + single-thread MMA issuer: 128x128 tiles, K = 32 bytes
-//               per instruction, GEMM_NACC accumulator buffers of 128 TMEM columns, so
-//               the MMAs run several tiles ahead of the epilogue;
-//   warps 2..   epilogue, EPI warpgroups each owning 128 / EPI columns of every tile:
+//   warps 1, 2  MMA issuers (one thread each, alternate tiles; warp 1 also allocates
+//               TMEM): 128x128 tiles, K = 32 bytes per instruction, GEMM_NACC
+//               accumulator buffers of 128 TMEM columns, so the MMAs run several tiles
+//               ahead of the epilogue;
+//   warps 3..   epilogue, EPI warpgroups each owning 128 / EPI columns of every tile:
 //               thread t of quarter q owns query row 32q+t (its TMEM lane), reads 32
 //               accumulator columns at a time, forms ||y||^2 - 2<x,y> (or <x,y> for
 //               inner product), and tests the batch's best value against its query's
@@ -81,7 +82,7 @@ struct KindTraits<KIND_FP16X3> {
   static constexpr int ELEM = 2, PIECES = 2, EPI = 2;
   static constexpr uint32_t FMT = sm100::FMT_F16;
 };
-__host__ __device__ constexpr int gemm_threads(int epi) { return 64 + 128 * epi; }
+__host__ __device__ constexpr int gemm_threads(int epi) { return 96 + 128 * epi; }
 // Kernel kind of a public precision: float32 accuracy comes from the FP16 split (the
 // faster of the two float32-accurate kinds), GBK_PREC_TF32X3 asks for the TF32 split.
 __host__ __device__ constexpr int gemm_kind(int prec) {
@@ -98,6 +99,7 @@ struct GemmArgs {
   int nq, nb;            // queries, database rows
   int nkb;               // 128-byte k-blocks per row (padded d)
   int stages;            // ring depth
+  int dual;              // two MMA issuers on alternate tiles (requires stages >= 2 nkb)
   int stream_a;          // 1: the query tile's k-blocks travel with B's through the ring
                          // (rows too long to keep the query tile resident)
   int nqt, ntiles;       // query tiles, database tiles

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
 
   if (threadIdx.x == 0) {
     sm100::mbar_init(a_full, 1);
-    sm100::mbar_init(a_empty, 1);
+    sm100::mbar_init(a_empty, args.dual ? 2 : 1);  // one commit from each MMA issuer
     for (int i = 0; i < args.stages; i++) {
       sm100::mbar_init(&b_full[i], 1);
       sm100::mbar_init(&b_empty[i], 1);
@@ -237,7 +237,9 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
         sm100::tma_prefetch_desc(&tmA1);
         sm100::tma_prefetch_desc(&tmB1);
       }
-      uint32_t gstage = 0;
+      // ring position kept incrementally (no division by the runtime stage count)
+      int st = 0;
+      uint32_t ph = 0;
       int local = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, local++) {
@@ -257,9 +259,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           }
         }
         for (int t = t0; t < t1 && ok; t++) {
-          for (int kb = 0; kb < args.nkb; kb++, gstage++) {
-            const int st = (int)(gstage % args.stages);
-            const uint32_t ph = (gstage / args.stages) & 1u;
+          for (int kb = 0; kb < args.nkb; kb++) {
             ok = sm100::mbar_wait(&b_empty[st], ph ^ 1u, args.status, abort_flag);
             if (!ok) break;
             sm100::mbar_arrive_expect_tx(&b_full[st], (uint32_t)SP * GEMM_TILE_BYTES);
@@ -274,69 +274,92 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
             sm100::tma_load_2d(dst, &tmB0, &b_full[st], x, t * GEMM_BN);
             if (PIECES > 1)
               sm100::tma_load_2d(dst + GEMM_TILE_BYTES, &tmB1, &b_full[st], x, t * GEMM_BN);
+            if (++st == args.stages) {
+              st = 0;
+              ph ^= 1u;
+            }
           }
         }
       }
     }
-  } else if (warp == 1) {
-    // ---------------------------------------------------------------- MMA issuer
-    if (lane == 0) {
-      uint32_t gstage = 0, gtile = 0;
+  } else if (warp == 1 || warp == 2) {
+    // ---------------------------------------------------------------- MMA issuers
+    // With `dual`, two issuing threads in different warps take alternate tiles: the tensor
+    // core keeps only a few MMAs queued, so while one thread waits for its next
+    // accumulator buffer and operands (and does its bookkeeping) the other's MMAs keep the
+    // pipe busy.  Each thread's commits track its own MMAs.  `dual` requires a ring of at
+    // least two tiles (stages >= 2 nkb): a slot's previous fill then belongs to the same
+    // thread's previous tile, which that thread has already waited for, so a parity wait
+    // can never mistake an older phase for the one it needs (same for the accumulator
+    // buffers: tile g and g - 4 have the same issuer).
+    const uint32_t par = (uint32_t)(warp - 1);
+    if (lane == 0 && (par == 0 || args.dual)) {
+      // Ring position and phase are kept incrementally (the other thread's tiles skipped),
+      // descriptors are formed once per k-block and stepped by 32 bytes of K (start address
+      // field, >> 4), and TMA-filled operands need no tcgen05 fence after their mbarrier
+      // waits (the fence orders an accumulator buffer after the epilogue's TMEM loads).
+      uint32_t gtile = 0;
+      int st = 0;
+      uint32_t ph = 0;
+      auto advance = [&](int n) {
+        st += n;
+        while (st >= args.stages) {
+          st -= args.stages;
+          ph ^= 1u;
+        }
+      };
       int local = 0;
       bool ok = true;
+      const uint32_t a_base = sm100::smem_u32(sA), ring_base = sm100::smem_u32(sB);
+      constexpr uint32_t TILE16 = GEMM_TILE_BYTES >> 4;  // one 128 x 128-byte box in desc units
       for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, local++) {
         const int ch = item / args.nqt;
         const int t0 = ch * args.tpc, t1 = min(args.ntiles, t0 + args.tpc);
         if (!args.stream_a) {
           ok = sm100::mbar_wait(a_full, (uint32_t)(local & 1), args.status, abort_flag);
           if (!ok) break;
-          sm100::tc_fence_after();
         }
-        const uint32_t a_base = sm100::smem_u32(sA);
         for (int t = t0; t < t1 && ok; t++, gtile++) {
+          if (args.dual && (gtile & 1u) != par) {  // the other issuer's tile
+            advance(args.nkb);
+            continue;
+          }
           const int acc = (int)(gtile % GEMM_NACC);
           ok = sm100::mbar_wait(&acc_empty[acc], ((gtile / GEMM_NACC) & 1u) ^ 1u, args.status,
                                 abort_flag);
           if (!ok) break;
           sm100::tc_fence_after();
           const uint32_t d_tmem = tmem_base + (uint32_t)(acc * GEMM_BN);
-          for (int kb = 0; kb < args.nkb; kb++, gstage++) {
-            const int st = (int)(gstage % args.stages);
-            ok = sm100::mbar_wait(&b_full[st], (gstage / args.stages) & 1u, args.status,
-                                  abort_flag);
+          for (int kb = 0; kb < args.nkb; kb++) {
+            ok = sm100::mbar_wait(&b_full[st], ph, args.status, abort_flag);
             if (!ok) break;
-            sm100::tc_fence_after();
-            const uint32_t s_base = sm100::smem_u32(sB) + (uint32_t)st * SP * GEMM_TILE_BYTES;
-            // A piece 0 / piece 1 and B of this k-block
-            const uint32_t a_kb0 = args.stream_a ? s_base : a_base + kb * GEMM_TILE_BYTES;
-            const uint32_t a_kb1 = args.stream_a ? s_base + GEMM_TILE_BYTES
-                                                 : a_base + (args.nkb + kb) * GEMM_TILE_BYTES;
-            const uint32_t b_base = args.stream_a ? s_base + PIECES * GEMM_TILE_BYTES : s_base;
+            const uint32_t s_base = ring_base + (uint32_t)st * SP * GEMM_TILE_BYTES;
+            // A piece 0 / piece 1 and B piece 0 / piece 1 of this k-block
+            const uint64_t a0 = sm100::sdesc_k_sw128(args.stream_a ? s_base
+                                                                   : a_base + kb * GEMM_TILE_BYTES);
+            const uint64_t a1 = args.stream_a ? a0 + TILE16 : a0 + (uint64_t)args.nkb * TILE16;
+            const uint64_t b0 = args.stream_a ? a0 + PIECES * TILE16 : sm100::sdesc_k_sw128(s_base);
+            const uint64_t b1 = b0 + TILE16;
 #pragma unroll
             for (int ks = 0; ks < 4; ks++) {  // 32 bytes of K per MMA
-              const uint32_t koff = (uint32_t)ks * 32u;
-              const uint64_t a0 = sm100::sdesc_k_sw128(a_kb0 + koff);
-              const uint64_t b0 = sm100::sdesc_k_sw128(b_base + koff);
+              const uint64_t ko = (uint64_t)(ks * 2);
               const uint32_t accum = (kb | ks) != 0 ? 1u : 0u;
               if (KIND == KIND_TF32X3) {
-                const uint64_t a1 = sm100::sdesc_k_sw128(a_kb1 + koff);
-                const uint64_t b1 = sm100::sdesc_k_sw128(b_base + GEMM_TILE_BYTES + koff);
-                sm100::mma_tf32(d_tmem, a0, b0, IDESC, accum);
-                sm100::mma_tf32(d_tmem, a0, b1, IDESC, 1u);
-                sm100::mma_tf32(d_tmem, a1, b0, IDESC, 1u);
+                sm100::mma_tf32(d_tmem, a0 + ko, b0 + ko, IDESC, accum);
+                sm100::mma_tf32(d_tmem, a0 + ko, b1 + ko, IDESC, 1u);
+                sm100::mma_tf32(d_tmem, a1 + ko, b0 + ko, IDESC, 1u);
               } else if (KIND == KIND_FP16X3) {
-                const uint64_t a1 = sm100::sdesc_k_sw128(a_kb1 + koff);
-                const uint64_t b1 = sm100::sdesc_k_sw128(b_base + GEMM_TILE_BYTES + koff);
-                sm100::mma_f16(d_tmem, a0, b0, IDESC, accum);
-                sm100::mma_f16(d_tmem, a0, b1, IDESC, 1u);
-                sm100::mma_f16(d_tmem, a1, b0, IDESC, 1u);
+                sm100::mma_f16(d_tmem, a0 + ko, b0 + ko, IDESC, accum);
+                sm100::mma_f16(d_tmem, a0 + ko, b1 + ko, IDESC, 1u);
+                sm100::mma_f16(d_tmem, a1 + ko, b0 + ko, IDESC, 1u);
               } else if (KIND == KIND_BF16) {
-                sm100::mma_f16(d_tmem, a0, b0, IDESC, accum);
+                sm100::mma_f16(d_tmem, a0 + ko, b0 + ko, IDESC, accum);
               } else {
-                sm100::mma_f8(d_tmem, a0, b0, IDESC, accum);
+                sm100::mma_f8(d_tmem, a0 + ko, b0 + ko, IDESC, accum);
               }
             }
             sm100::mma_commit(&b_empty[st]);  // frees the ring stage once read
+            advance(1);
           }
           if (ok) sm100::mma_commit(&acc_full[acc]);
         }
@@ -346,13 +369,13 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
   } else {
     // ---------------------------------------------------------------- epilogue
     const int quarter = warp & 3;          // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;      // column part of the tile (EPI parts)
+    const int half = (warp - 3) >> 2;      // column part of the tile (EPI parts)
     constexpr int CW = GEMM_BN / EPI;      // columns per warp per tile
     const int co = half * CW;
     const int qrow = quarter * 32 + lane;  // TMEM lane == query row in the tile
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     uint64_t* myQ = sQ + (half * GEMM_BM + qrow) * GEMM_QSTRIDE;
-    float* sY = reinterpret_cast<float*>(smem + lay.y_off) + (warp - 2) * 256;  // norms, scales
+    float* sY = reinterpret_cast<float*>(smem + lay.y_off) + (warp - 3) * 256;  // norms, scales
     const int lists = args.chunks * EPI;   // candidate lists per query
     const uint64_t lpol = l2_keep_policy();
     const bool vec_out = MODE == MODE_STORE && (args.ldo & 3) == 0 &&
