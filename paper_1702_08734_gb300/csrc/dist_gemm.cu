@@ -482,6 +482,24 @@ gbk_status gemm_launch(int mode, int kpr, bool largest, const PreparedOperand& Q
   const int64_t stage_bytes = (int64_t)pieces * GEMM_TILE_BYTES + 16;
   int stages = (int)std::min<int64_t>(8, avail / stage_bytes);
   a.stream_a = 0;
+  a.tmem_a = 0;
+  a.nacc = GEMM_NACC;
+  // A resident in shared memory leaves a ring shorter than two tiles: keep A in tensor
+  // memory instead (its pieces x k-blocks x 32 columns beside two accumulator buffers)
+  // when that makes room for a two-tile ring, so both MMA issuers can run.  Not with
+  // candidate lists longer than 32: their merges make the epilogue the bound and it then
+  // needs the slack of four accumulator buffers (10^4 x 10^6 x 128, FP16 split: k = 10
+  // 7.5 -> 6.4 ms, k = 100 8.5 -> 9.1 ms with this mode)
+  if (stages < 2 * Q.nkb && kpr <= 1 && pieces * Q.nkb * 32 <= 512 - 2 * GEMM_BN) {
+    const GemmSmemLayout lt = gemm_smem_layout(pieces, 1, 0, queues, epi);
+    const int st_t = (int)std::min<int64_t>(8, ((int64_t)di.smem_optin - 1024 - lt.total) /
+                                                   stage_bytes);
+    if (st_t >= 2 * Q.nkb) {
+      stages = st_t;
+      a.tmem_a = 1;
+      a.nacc = 2;
+    }
+  }
   if (stages < 2) {
     // the query tile does not fit beside a 2-stage ring: stream its k-blocks with B's
     const GemmSmemLayout l1 = gemm_smem_layout(2 * pieces, 0, 0, queues, epi);
@@ -495,8 +513,9 @@ gbk_status gemm_launch(int mode, int kpr, bool largest, const PreparedOperand& Q
   a.nkb = Q.nkb;
   a.dual = stages >= 2 * Q.nkb ? 1 : 0;
   // at least half the SM's shared memory, so one CTA per SM owns the TMEM it allocates
-  const GemmSmemLayout lf = a.stream_a ? gemm_smem_layout(2 * pieces, 0, stages, queues, epi)
-                                       : gemm_smem_layout(pieces, Q.nkb, stages, queues, epi);
+  const GemmSmemLayout lf =
+      a.stream_a ? gemm_smem_layout(2 * pieces, 0, stages, queues, epi)
+                 : gemm_smem_layout(pieces, a.tmem_a ? 1 : Q.nkb, stages, queues, epi);
   const size_t smem = std::max<size_t>(lf.total + 1024, di.smem_optin / 2 + 1024);
   const int nitems = a.nqt * a.chunks;
   const int grid = std::min(nitems, di.sm_count);

@@ -23,7 +23,7 @@ __host__ __device__ inline GemmSmemLayout gemm_smem_layout(int pieces, int nkb, 
   L.h_off = L.y_off + (uint32_t)(epi * 4 * 1024);
   const uint32_t hbytes = (queues && epi == 2) ? 2u * GEMM_BM * 8u : 0u;
   L.bar_off = (L.h_off + hbytes + 63u) & ~63u;
-  L.total = L.bar_off + 8u * (2u + 2u * (uint32_t)stages + 2u * GEMM_NACC) + 16u;
+  L.total = L.bar_off + 8u * (4u + 2u * (uint32_t)stages + 2u * GEMM_NACC) + 16u;
   return L;
 }
 
@@ -182,9 +182,13 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
   // stage = B's pieces, or A's and B's pieces of one k-block when A is streamed
   const int SP = args.stream_a ? 2 * PIECES : PIECES;
-  const GemmSmemLayout lay = args.stream_a
-                                 ? gemm_smem_layout(2 * PIECES, 0, args.stages, QUEUES, EPI)
-                                 : gemm_smem_layout(PIECES, args.nkb, args.stages, QUEUES, EPI);
+  // A in shared memory: all of its k-blocks (resident), none (streamed), or one staging
+  // k-block on its way into tensor memory (tmem_a)
+  const GemmSmemLayout lay =
+      args.stream_a ? gemm_smem_layout(2 * PIECES, 0, args.stages, QUEUES, EPI)
+                    : gemm_smem_layout(PIECES, args.tmem_a ? 1 : args.nkb, args.stages, QUEUES, EPI);
+  const int nacc = args.nacc;  // accumulator buffers: 4, or 2 when A takes tensor memory
+  const uint32_t nacc_log = nacc == 4 ? 2u : 1u;
   unsigned char* sA = smem + lay.a_off;
   unsigned char* sB = smem + lay.b_off;
   uint64_t* sQ = reinterpret_cast<uint64_t*>(smem + lay.q_off);
@@ -195,7 +199,9 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
   uint64_t* b_empty = b_full + args.stages;
   uint64_t* acc_full = b_empty + args.stages;
   uint64_t* acc_empty = acc_full + GEMM_NACC;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + GEMM_NACC);
+  uint64_t* as_full = acc_empty + GEMM_NACC;  // A staging k-block (tmem_a)
+  uint64_t* as_empty = as_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(as_empty + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   constexpr bool PAIR = QUEUES && EPI == 2;  // the two column halves share a pair bound
   volatile uint64_t* sH = reinterpret_cast<volatile uint64_t*>(smem + lay.h_off);
@@ -214,6 +220,8 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       sm100::mbar_init(&acc_full[i], 1);
       sm100::mbar_init(&acc_empty[i], 4 * EPI);
     }
+    sm100::mbar_init(as_full, 1);
+    sm100::mbar_init(as_empty, 1);
     *abort_flag = 0;
     sm100::fence_mbar_init();
   }
@@ -240,12 +248,25 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       // ring position kept incrementally (no division by the runtime stage count)
       int st = 0;
       uint32_t ph = 0;
+      uint32_t as_use = 0;  // A staging slot uses (tmem_a)
       int local = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, local++) {
         const int qt = item % args.nqt, ch = item / args.nqt;
         const int t0 = ch * args.tpc, t1 = min(args.ntiles, t0 + args.tpc);
-        if (!args.stream_a) {
+        if (args.tmem_a) {
+          // A's k-blocks one at a time through the staging slot; the MMA thread copies
+          // each into tensor memory
+          for (int kb = 0; kb < args.nkb && ok; kb++, as_use++) {
+            ok = sm100::mbar_wait(as_empty, (as_use & 1u) ^ 1u, args.status, abort_flag);
+            if (!ok) break;
+            sm100::mbar_arrive_expect_tx(as_full, (uint32_t)PIECES * GEMM_TILE_BYTES);
+            const int x = kb * (128 / T::ELEM);
+            sm100::tma_load_2d(sA, &tmA0, as_full, x, qt * GEMM_BM);
+            if (PIECES > 1) sm100::tma_load_2d(sA + GEMM_TILE_BYTES, &tmA1, as_full, x, qt * GEMM_BM);
+          }
+          if (!ok) break;
+        } else if (!args.stream_a) {
           ok = sm100::mbar_wait(a_empty, (uint32_t)((local & 1) ^ 1), args.status, abort_flag);
           if (!ok) break;
           sm100::mbar_arrive_expect_tx(a_full, (uint32_t)(PIECES * args.nkb) * GEMM_TILE_BYTES);
@@ -291,7 +312,10 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
     // least two tiles (stages >= 2 nkb): a slot's previous fill then belongs to the same
     // thread's previous tile, which that thread has already waited for, so a parity wait
     // can never mistake an older phase for the one it needs (same for the accumulator
-    // buffers: tile g and g - 4 have the same issuer).
+    // buffers: tile g and g - nacc have the same issuer, nacc being even).
+    // With `tmem_a`, issuer 0 copies each work item's A tile from its staging k-block into
+    // tensor memory (columns after the accumulators) once the previous item's MMAs of both
+    // issuers are done, and both issuers read A from there.
     const uint32_t par = (uint32_t)(warp - 1);
     if (lane == 0 && (par == 0 || args.dual)) {
       // Ring position and phase are kept incrementally (the other thread's tiles skipped),
@@ -312,10 +336,33 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       bool ok = true;
       const uint32_t a_base = sm100::smem_u32(sA), ring_base = sm100::smem_u32(sB);
       constexpr uint32_t TILE16 = GEMM_TILE_BYTES >> 4;  // one 128 x 128-byte box in desc units
+      const uint32_t a_tm = tmem_base + (uint32_t)(nacc * GEMM_BN);  // A in tensor memory
+      uint32_t as_use = 0;
       for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, local++) {
         const int ch = item / args.nqt;
         const int t0 = ch * args.tpc, t1 = min(args.ntiles, t0 + args.tpc);
-        if (!args.stream_a) {
+        if (args.tmem_a) {
+          if (par == 0) {
+            ok = sm100::mbar_wait(a_empty, (uint32_t)((local & 1) ^ 1), args.status, abort_flag);
+            if (ok) sm100::tc_fence_after();
+            for (int kb = 0; kb < args.nkb && ok; kb++, as_use++) {
+              ok = sm100::mbar_wait(as_full, as_use & 1u, args.status, abort_flag);
+              if (!ok) break;
+              const uint64_t s0 = sm100::sdesc_k_sw128(a_base);
+#pragma unroll
+              for (int pc = 0; pc < PIECES; pc++)
+#pragma unroll
+                for (int ks = 0; ks < 4; ks++)
+                  sm100::tmem_cp_128x256b(a_tm + (uint32_t)((pc * args.nkb + kb) * 32 + ks * 8),
+                                          s0 + (uint64_t)(pc * TILE16 + ks * 2));
+              sm100::mma_commit(as_empty);  // the staging k-block is free once copied
+            }
+            if (ok) sm100::mma_commit(a_full);
+          }
+          if (ok) ok = sm100::mbar_wait(a_full, (uint32_t)(local & 1), args.status, abort_flag);
+          if (!ok) break;
+          sm100::tc_fence_after();
+        } else if (!args.stream_a) {
           ok = sm100::mbar_wait(a_full, (uint32_t)(local & 1), args.status, abort_flag);
           if (!ok) break;
         }
@@ -324,8 +371,8 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
             advance(args.nkb);
             continue;
           }
-          const int acc = (int)(gtile % GEMM_NACC);
-          ok = sm100::mbar_wait(&acc_empty[acc], ((gtile / GEMM_NACC) & 1u) ^ 1u, args.status,
+          const int acc = (int)(gtile & (uint32_t)(nacc - 1));
+          ok = sm100::mbar_wait(&acc_empty[acc], ((gtile >> nacc_log) & 1u) ^ 1u, args.status,
                                 abort_flag);
           if (!ok) break;
           sm100::tc_fence_after();
@@ -340,6 +387,29 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
             const uint64_t a1 = args.stream_a ? a0 + TILE16 : a0 + (uint64_t)args.nkb * TILE16;
             const uint64_t b0 = args.stream_a ? a0 + PIECES * TILE16 : sm100::sdesc_k_sw128(s_base);
             const uint64_t b1 = b0 + TILE16;
+            const uint32_t at0 = a_tm + (uint32_t)(kb * 32);  // tmem_a: A pieces of this k-block
+            const uint32_t at1 = at0 + (uint32_t)(args.nkb * 32);
+            if (args.tmem_a) {
+#pragma unroll
+              for (int ks = 0; ks < 4; ks++) {
+                const uint64_t ko = (uint64_t)(ks * 2);
+                const uint32_t ka = (uint32_t)(ks * 8);
+                const uint32_t accum = (kb | ks) != 0 ? 1u : 0u;
+                if (KIND == KIND_TF32X3) {
+                  sm100::mma_tf32_ts(d_tmem, at0 + ka, b0 + ko, IDESC, accum);
+                  sm100::mma_tf32_ts(d_tmem, at0 + ka, b1 + ko, IDESC, 1u);
+                  sm100::mma_tf32_ts(d_tmem, at1 + ka, b0 + ko, IDESC, 1u);
+                } else if (KIND == KIND_FP16X3) {
+                  sm100::mma_f16_ts(d_tmem, at0 + ka, b0 + ko, IDESC, accum);
+                  sm100::mma_f16_ts(d_tmem, at0 + ka, b1 + ko, IDESC, 1u);
+                  sm100::mma_f16_ts(d_tmem, at1 + ka, b0 + ko, IDESC, 1u);
+                } else if (KIND == KIND_BF16) {
+                  sm100::mma_f16_ts(d_tmem, at0 + ka, b0 + ko, IDESC, accum);
+                } else {
+                  sm100::mma_f8_ts(d_tmem, at0 + ka, b0 + ko, IDESC, accum);
+                }
+              }
+            } else
 #pragma unroll
             for (int ks = 0; ks < 4; ks++) {  // 32 bytes of K per MMA
               const uint64_t ko = (uint64_t)(ks * 2);
@@ -446,7 +516,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       };
       if (t0 < t1) prefetch(t0);
       for (int t = t0; t < t1; t++, gtile++) {
-        const int acc = (int)(gtile % GEMM_NACC);
+        const int acc = (int)(gtile & (uint32_t)(nacc - 1));
         const int col0 = t * GEMM_BN + co;  // first column of this warp's part
         __syncwarp();
         if (lane < CW / 4) {
@@ -462,7 +532,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           }
         }
         if (t + 1 < t1) prefetch(t + 1);
-        ok = sm100::mbar_wait(&acc_full[acc], (gtile / GEMM_NACC) & 1u, args.status, abort_flag);
+        ok = sm100::mbar_wait(&acc_full[acc], (gtile >> nacc_log) & 1u, args.status, abort_flag);
         if (!ok) break;
         sm100::tc_fence_after();
         const int lim = args.nb - col0;  // valid columns in this part (warp-uniform)
