@@ -486,18 +486,21 @@ gbk_status gemm_launch(int mode, int kpr, bool largest, const PreparedOperand& Q
   a.nacc = GEMM_NACC;
   // A resident in shared memory leaves a ring shorter than two tiles: keep A in tensor
   // memory instead (its pieces x k-blocks x 32 columns beside two accumulator buffers)
-  // when that makes room for a two-tile ring, so both MMA issuers can run.  Not with
-  // candidate lists longer than 32: their merges make the epilogue the bound and it then
-  // needs the slack of four accumulator buffers (10^4 x 10^6 x 128, FP16 split: k = 10
-  // 7.5 -> 6.4 ms, k = 100 8.5 -> 9.1 ms with this mode)
-  if (stages < 2 * Q.nkb && kpr <= 1 && pieces * Q.nkb * 32 <= 512 - 2 * GEMM_BN) {
+  // when that makes room for a two-tile ring, so both MMA issuers can run; the remaining
+  // columns hold 3 (d <= 128 for the FP16 split) or 2 accumulator buffers.  With only 2,
+  // not for candidate lists longer than 32: their merges make the epilogue the bound and
+  // it needs more slack (10^4 x 10^6 x 128, FP16 split, 2 buffers: k = 10 7.5 -> 6.4 ms,
+  // k = 100 8.5 -> 9.1 ms)
+  const int acols = pieces * Q.nkb * 32;  // tensor-memory columns of A
+  const int nacc_t = std::min(GEMM_NACC, (512 - acols) / GEMM_BN);
+  if (stages < 2 * Q.nkb && nacc_t >= 2 && (kpr <= 1 || nacc_t >= 3)) {
     const GemmSmemLayout lt = gemm_smem_layout(pieces, 1, 0, queues, epi);
     const int st_t = (int)std::min<int64_t>(8, ((int64_t)di.smem_optin - 1024 - lt.total) /
                                                    stage_bytes);
     if (st_t >= 2 * Q.nkb) {
       stages = st_t;
       a.tmem_a = 1;
-      a.nacc = 2;
+      a.nacc = nacc_t;
     }
   }
   if (stages < 2) {

@@ -102,7 +102,7 @@ struct GemmArgs {
   int dual;              // two MMA issuers on alternate tiles (requires stages >= 2 nkb)
   int tmem_a;            // A tile in tensor memory (copied from one staging k-block) instead
                          // of shared memory, freeing shared memory for the ring
-  int nacc;              // accumulator buffers: 4, or 2 with tmem_a
+  int nacc;              // accumulator buffers: 4, or 2-3 with tmem_a
   int stream_a;          // 1: the query tile's k-blocks travel with B's through the ring
                          // (rows too long to keep the query tile resident)
   int nqt, ntiles;       // query tiles, database tiles

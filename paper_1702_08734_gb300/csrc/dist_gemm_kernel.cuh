@@ -123,11 +123,12 @@ __device__ __forceinline__ void merge_queues(int limit, int& cnt, float& thr, co
       const uint2 e = sQ[l * GEMM_QSTRIDE + lane];
       v = composite(ordered_key(__uint_as_float(e.x), LARGEST), e.y);
     }
-    v = warp_sort32(v);
+    // the list's L2 round trip overlaps the queue's sort
     uint64_t* Lg = part + (int64_t)l * rowstride;
     uint64_t L[KR];
 #pragma unroll
     for (int r = 0; r < KR; r++) L[r] = ld_keep(Lg + r * 32 + lane, pol);
+    v = warp_sort32(v);
     warp_merge_list<KR>(L, v);
 #pragma unroll
     for (int r = 0; r < KR; r++) st_keep(Lg + r * 32 + lane, L[r], pol);
@@ -187,8 +188,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
   const GemmSmemLayout lay =
       args.stream_a ? gemm_smem_layout(2 * PIECES, 0, args.stages, QUEUES, EPI)
                     : gemm_smem_layout(PIECES, args.tmem_a ? 1 : args.nkb, args.stages, QUEUES, EPI);
-  const int nacc = args.nacc;  // accumulator buffers: 4, or 2 when A takes tensor memory
-  const uint32_t nacc_log = nacc == 4 ? 2u : 1u;
+  const int nacc = args.nacc;  // accumulator buffers: 4, or fewer when A takes tensor memory
   unsigned char* sA = smem + lay.a_off;
   unsigned char* sB = smem + lay.b_off;
   uint64_t* sQ = reinterpret_cast<uint64_t*>(smem + lay.q_off);
@@ -311,8 +311,11 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
     // pipe busy.  Each thread's commits track its own MMAs.  `dual` requires a ring of at
     // least two tiles (stages >= 2 nkb): a slot's previous fill then belongs to the same
     // thread's previous tile, which that thread has already waited for, so a parity wait
-    // can never mistake an older phase for the one it needs (same for the accumulator
-    // buffers: tile g and g - nacc have the same issuer, nacc being even).
+    // can never mistake an older phase for the one it needs.  The accumulator buffers need
+    // no such condition for nacc >= 2: the issuer of tile g waited, for its previous tile
+    // g - 2, until the epilogue had released tile g - 2 - nacc, so tile g - 2 nacc (the
+    // older phase of tile g's buffer) is released too; buffer index and phase are counted
+    // per tile, skipped tiles included.
     // With `tmem_a`, issuer 0 copies each work item's A tile from its staging k-block into
     // tensor memory (columns after the accumulators) once the previous item's MMAs of both
     // issuers are done, and both issuers read A from there.
@@ -330,6 +333,14 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
         while (st >= args.stages) {
           st -= args.stages;
           ph ^= 1u;
+        }
+      };
+      int acc_i = 0;  // accumulator buffer of tile gtile and its use parity
+      uint32_t acc_ph = 0;
+      auto next_acc = [&]() {
+        if (++acc_i == nacc) {
+          acc_i = 0;
+          acc_ph ^= 1u;
         }
       };
       int local = 0;
@@ -366,14 +377,13 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           ok = sm100::mbar_wait(a_full, (uint32_t)(local & 1), args.status, abort_flag);
           if (!ok) break;
         }
-        for (int t = t0; t < t1 && ok; t++, gtile++) {
+        for (int t = t0; t < t1 && ok; t++, gtile++, next_acc()) {
           if (args.dual && (gtile & 1u) != par) {  // the other issuer's tile
             advance(args.nkb);
             continue;
           }
-          const int acc = (int)(gtile & (uint32_t)(nacc - 1));
-          ok = sm100::mbar_wait(&acc_empty[acc], ((gtile >> nacc_log) & 1u) ^ 1u, args.status,
-                                abort_flag);
+          const int acc = acc_i;
+          ok = sm100::mbar_wait(&acc_empty[acc], acc_ph ^ 1u, args.status, abort_flag);
           if (!ok) break;
           sm100::tc_fence_after();
           const uint32_t d_tmem = tmem_base + (uint32_t)(acc * GEMM_BN);
@@ -451,6 +461,8 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
     const bool vec_out = MODE == MODE_STORE && (args.ldo & 3) == 0 &&
                          (reinterpret_cast<uintptr_t>(args.out) & 15) == 0;
     uint32_t gtile = 0;
+    int acc_i = 0;  // accumulator buffer of tile gtile and its use parity
+    uint32_t acc_ph = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
       const int qt = item % args.nqt, ch = item / args.nqt;
@@ -516,7 +528,12 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       };
       if (t0 < t1) prefetch(t0);
       for (int t = t0; t < t1; t++, gtile++) {
-        const int acc = (int)(gtile & (uint32_t)(nacc - 1));
+        const int acc = acc_i;
+        const uint32_t accph = acc_ph;
+        if (++acc_i == nacc) {
+          acc_i = 0;
+          acc_ph ^= 1u;
+        }
         const int col0 = t * GEMM_BN + co;  // first column of this warp's part
         __syncwarp();
         if (lane < CW / 4) {
@@ -532,7 +549,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           }
         }
         if (t + 1 < t1) prefetch(t + 1);
-        ok = sm100::mbar_wait(&acc_full[acc], (gtile >> nacc_log) & 1u, args.status, abort_flag);
+        ok = sm100::mbar_wait(&acc_full[acc], accph, args.status, abort_flag);
         if (!ok) break;
         sm100::tc_fence_after();
         const int lim = args.nb - col0;  // valid columns in this part (warp-uniform)
