@@ -167,7 +167,7 @@ typedef struct gbk_knn_opts {
                          count the over-fetched k'); either only where the database holds
                          at least 4k blocks of 64 rows (128 with GBK_PREC_TF32X3).  The
                          pre-pass takes the best distance of every (query, block) over
-                         the first sixteenth of the database; their k-th best bounds the
+                         the first sixth of the database; their k-th best bounds the
                          k-th nearest distance, so the fused selection starts with that
                          threshold.  Results are the same either way.                    */
 } gbk_knn_opts;

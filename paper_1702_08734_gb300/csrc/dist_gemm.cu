@@ -575,14 +575,14 @@ __global__ void kth_key_kernel(const float* __restrict__ Dk, int64_t nq, int k, 
 // the k-th nearest distance from the start and the fused selection queues far fewer
 // candidates (a streamed threshold admits about k (1 + ln(n / k)) of n values, a threshold
 // from a prefix of n / f rows about k (1 + ln f)).  prefilter: -1 off, 1 on for k > 1, 0 on
-// for k >= 32 (k >= 64 with the TF32 split, whose slower GEMM makes the pre-pass dearer;
-// measured on 10^4 x 10^6 x 128: at k = 100 the FP16 split goes from 10.1 to 9.2 ms and
-// BF16 from 9.2 to 7.9, at k = 10 the FP16 split loses 0.3 ms); the prefix is a sixteenth
-// of the database, at least k values long and at most a quarter of the database.
+// for k >= 32 (k >= 64 with the TF32 split, whose slower GEMM makes the pre-pass dearer).
+// The prefix is a sixth of the database (at least k values, at most a quarter of it):
+// on 10^4 x 10^6 x 128, FP16 split, k = 100 takes 9.8 / 9.5 / 9.2 / 8.9 ms with a prefix of
+// 1/32, 1/16, 1/8, 1/6 (10.6 ms without the pre-pass), k = 32 and k = 256 likewise.
 static int prefilter_tiles(int prefilter, int k, int ntiles, int epi) {
   const int kmin = epi == 1 ? 64 : 32;
   if (prefilter < 0 || k <= 1 || (prefilter == 0 && k < kmin)) return 0;
-  const int ts = std::max((ntiles + 15) / 16, (k + epi - 1) / epi);
+  const int ts = std::max((ntiles + 5) / 6, (k + epi - 1) / epi);
   return 4 * ts <= ntiles ? ts : 0;
 }
 
