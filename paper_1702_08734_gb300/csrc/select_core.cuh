@@ -299,6 +299,11 @@ struct BlockSelect {
     const int n = s.n_top;
     for (int i = n + threadIdx.x; i < KP; i += THREADS) s.top[i] = ~0ull;
     __syncthreads();
+    constexpr int E = KP / THREADS;  // elements per thread in the register sort
+    if constexpr ((THREADS & (THREADS - 1)) == 0 && E >= 2 && E <= 16) {
+      sort_registers(s);
+      return;
+    }
     for (int size = 2; size <= KP; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
         for (int t = threadIdx.x; t < KP / 2; t += THREADS) {
@@ -314,6 +319,71 @@ struct BlockSelect {
         __syncthreads();
       }
     }
+  }
+
+  // The same bitonic network with thread t holding elements t*E .. t*E+E-1 in registers:
+  // strides below E compare within a thread, strides below 32 E between the lanes of a
+  // warp (shuffles), only the longer ones go through shared memory with block barriers
+  // (3 of the 55 stages at KP = 1024 with 128 threads).
+  __device__ static void sort_registers(Smem& s) {
+    constexpr int E = KP / THREADS;
+    const int t = threadIdx.x;
+    uint64_t v[E];
+#pragma unroll
+    for (int r = 0; r < E; r++) v[r] = s.top[t * E + r];
+    for (int size = 2; size <= KP; size <<= 1) {
+      int stride = size >> 1;
+      if (stride >= 32 * E) {  // partners in other warps
+#pragma unroll
+        for (int r = 0; r < E; r++) s.top[t * E + r] = v[r];
+        __syncthreads();
+        for (; stride >= 32 * E; stride >>= 1) {
+          for (int p = t; p < KP / 2; p += THREADS) {
+            const int lo = 2 * p - (p & (stride - 1));
+            const int hi = lo + stride;
+            const bool asc = (lo & size) == 0;
+            const uint64_t a = s.top[lo], b = s.top[hi];
+            if ((a > b) == asc) {
+              s.top[lo] = b;
+              s.top[hi] = a;
+            }
+          }
+          __syncthreads();
+        }
+#pragma unroll
+        for (int r = 0; r < E; r++) v[r] = s.top[t * E + r];
+        __syncthreads();  // every thread has read before the next write-back
+      }
+      for (; stride >= E; stride >>= 1) {  // partner lane t ^ (stride / E), same slot
+        const int tm = stride / E;
+        const bool lower = (t & tm) == 0;
+#pragma unroll
+        for (int r = 0; r < E; r++) {
+          const uint64_t o = __shfl_xor_sync(FULL_MASK, v[r], tm);
+          const bool asc = ((t * E + r) & size) == 0;
+          v[r] = (lower == asc) ? min(v[r], o) : max(v[r], o);
+        }
+      }
+#pragma unroll
+      for (int st = E / 2; st >= 1; st >>= 1) {  // within the thread
+        if (st < size) {
+#pragma unroll
+          for (int r = 0; r < E; r++) {
+            if ((r & st) == 0) {
+              const bool asc = ((t * E + r) & size) == 0;
+              const uint64_t a = v[r], b = v[r + st];
+              if ((a > b) == asc) {
+                v[r] = b;
+                v[r + st] = a;
+              }
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < E; r++) s.top[t * E + r] = v[r];
+    __syncthreads();
   }
 };
 
