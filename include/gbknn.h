@@ -11,8 +11,9 @@
  *    stream).  Calls are asynchronous: outputs are complete when `stream` is synchronised.
  *  - Matrices are dense row-major float32; indices and ids are int64.
  *  - Scratch memory comes from the allocator installed with gbk_set_allocator (default:
- *    cudaMallocAsync / cudaFreeAsync on `stream`).  It is freed stream-ordered before
- *    the call returns.
+ *    stream-ordered allocation on `stream` from the library's own memory pool per device,
+ *    which keeps up to 8 GiB of freed scratch mapped between calls).  It is freed
+ *    stream-ordered before the call returns.
  *  - Selection order: for "smallest" (squared L2) a candidate is better when its value is
  *    smaller; for "largest" (inner product) when larger.  NaN ranks after every number in
  *    both orders, -0 equals +0, and equal values are ordered by the lower index.  (The
@@ -195,6 +196,23 @@ typedef struct gbk_knn_opts {
 gbk_status gbk_knn_brute(const float* xq, int64_t nq, const float* xb, int64_t nb, int32_t d,
                          int32_t k, int32_t metric, float* D, int64_t* I,
                          const gbk_knn_opts* opts, void* stream);
+
+/*
+ * gbk_knn_brute with HOST arrays: xq [nq][d], xb [nb][d] float32 and the outputs D [nq][k],
+ * I [nq][k] in host memory (page-locked for the copies to overlap the search; pageable
+ * memory works but serialises them).  The call enqueues the host->device copies, the
+ * search and the device->host copies of D and I on `stream` and returns; D and I are
+ * valid once the stream has been synchronised, and the host arrays must stay alive until
+ * then.  With a float32-accurate precision and the fused selection (k <= 512, nb > 65,536)
+ * the database is copied in pieces of 2^18 rows on a second stream while the search runs
+ * over the pieces already copied (the result is that of gbk_knn_brute).  Device scratch:
+ * the inputs, outputs and the search's own.  Options as gbk_knn_brute, except that the
+ * certified / error_bound outputs are not available (GBK_EINVAL).  Errors: as
+ * gbk_knn_brute.
+ */
+gbk_status gbk_knn_brute_host(const float* xq, int64_t nq, const float* xb, int64_t nb,
+                              int32_t d, int32_t k, int32_t metric, float* D, int64_t* I,
+                              const gbk_knn_opts* opts, void* stream);
 
 /*
  * All pairwise distances out[i*ldo + j] between xq[i] and xb[j] (section 2, "Exact

@@ -44,6 +44,7 @@ _SIGNATURES = {
     "gbk_device_status": [_vp],
     "gbk_selftest_wait_timeout": [_i64, _vp],
     "gbk_knn_brute": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
+    "gbk_knn_brute_host": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
     "gbk_pairwise_distances": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _vp, _i64, _vp],
 }
 
@@ -242,6 +243,35 @@ def knn_brute(xq: torch.Tensor, xb: torch.Tensor, k: int, metric="l2", precision
     _call("gbk_knn_brute", _ptr(xq), nq, _ptr(xb), nb, int(d), int(k), _metric(metric), _ptr(D),
           _ptr(I), ctypes.byref(opts), _stream())
     return (D, I, cert, eb) if certify else (D, I)
+
+
+def knn_brute_host(xq: torch.Tensor, xb: torch.Tensor, k: int, metric="l2", precision="fp32",
+                   kprime: int = 0, chunks: int = 0, out=None, exact: bool = False,
+                   prefilter: int = 0, sync: bool = True):
+    """knn_brute on host (CPU) float32 tensors, pinned for the copies to overlap the search:
+    the library copies the inputs in, searches and copies D, I (CPU tensors) back, all on the
+    current stream; with sync=False the caller synchronises the stream before reading them."""
+    for t, nm in ((xq, "xq"), (xb, "xb")):
+        if t.device.type != "cpu" or t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous float32 CPU tensor" % nm)
+    nq, d = xq.shape
+    nb = xb.shape[0]
+    if xb.shape[1] != d:
+        raise ValueError("dimension mismatch")
+    if out is None:
+        D = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+        I = torch.empty((nq, k), dtype=torch.int64).pin_memory()
+    else:
+        D, I = out
+    opts = KnnOpts(PRECISIONS[precision], int(kprime), int(chunks), None, None,
+                   int(bool(exact)), int(prefilter))
+    _call("gbk_knn_brute_host", ctypes.c_void_p(xq.data_ptr()), nq,
+          ctypes.c_void_p(xb.data_ptr()), nb, int(d), int(k), _metric(metric),
+          ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(I.data_ptr()), ctypes.byref(opts),
+          _stream())
+    if sync:
+        torch.cuda.current_stream().synchronize()
+    return D, I
 
 
 def pairwise_distances(xq: torch.Tensor, xb: torch.Tensor, metric="l2", precision="fp32"):

@@ -34,6 +34,36 @@ gbk_status clear_error() {
   return GBK_OK;
 }
 
+// The library's own stream-ordered pool per device (the default pool is left as it is):
+// it keeps up to 8 GiB of freed scratch mapped between calls instead of releasing it at
+// every synchronisation, so a call that follows a synchronising one (host-buffer search,
+// an end-to-end loop) does not map its scratch afresh.  0 on failure (then the default
+// pool is used).
+static cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  static bool failed[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[dev] && !failed[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      failed[dev] = true;
+      return nullptr;
+    }
+    uint64_t keep = (uint64_t)8 << 30;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
 void* scratch_alloc(size_t bytes, cudaStream_t stream, gbk_status* st) {
   gbk_allocator a;
   {
@@ -46,7 +76,9 @@ void* scratch_alloc(size_t bytes, cudaStream_t stream, gbk_status* st) {
     if (!p) *st = set_error(GBK_ENOMEM, "installed allocator failed for %zu bytes", bytes);
     return p;
   }
-  cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+  cudaMemPool_t pool = library_pool();
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, stream)
+                       : cudaMallocAsync(&p, bytes, stream);
   if (e != cudaSuccess) {
     *st = set_error(GBK_ENOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
     cudaGetLastError();
@@ -234,36 +266,59 @@ gbk_status gbk_device_status(void* stream) {
   return set_error(GBK_EDEVICE, "kernel status word 0x%x", v);
 }
 
+// Argument checks and options of gbk_knn_brute and gbk_knn_brute_host (`fn`: the
+// entry point's name for the error messages).
+static gbk_status knn_args(const char* fn, int64_t nq, int64_t nb, int32_t d, int32_t k,
+                           int32_t metric, const void* xq, const void* xb, const void* D,
+                           const void* I, const gbk_knn_opts* opts, KnnPlan* plan) {
+  GBK_REQUIRE(nq >= 0 && nq < (int64_t(1) << 31), "%s: nq out of range", fn);
+  GBK_REQUIRE(nb >= 1 && nb < (int64_t(1) << 31), "%s: nb out of range", fn);
+  GBK_REQUIRE(d >= 1, "%s: d < 1", fn);
+  GBK_REQUIRE(k >= 1 && k <= GBK_MAX_K && k <= nb, "%s: k=%d out of [1, min(nb, %d)]", fn, k,
+              GBK_MAX_K);
+  GBK_REQUIRE(metric == GBK_METRIC_L2 || metric == GBK_METRIC_IP, "%s: bad metric", fn);
+  GBK_REQUIRE(nq == 0 || (xq && xb && D && I), "%s: NULL pointer", fn);
+  if (opts) {
+    GBK_REQUIRE(opts->precision >= GBK_PREC_FP32 && opts->precision <= GBK_PREC_TF32X3,
+                "%s: bad precision", fn);
+    GBK_REQUIRE(opts->chunks >= 0, "%s: chunks < 0", fn);
+    GBK_REQUIRE(opts->prefilter >= -1 && opts->prefilter <= 1,
+                "%s: prefilter must be -1, 0 or 1", fn);
+    GBK_REQUIRE(opts->kprime == 0 || (opts->kprime >= k && opts->kprime <= GBK_MAX_K),
+                "%s: kprime must be 0 or in [k, %d]", fn, GBK_MAX_K);
+    plan->prec = opts->precision;
+    plan->chunks = opts->chunks;
+    plan->kprime = opts->kprime;
+    plan->certified = opts->certified;
+    plan->error_bound = opts->error_bound;
+    plan->exact = opts->exact != 0;
+    plan->prefilter = opts->prefilter;
+  }
+  return GBK_OK;
+}
+
 gbk_status gbk_knn_brute(const float* xq, int64_t nq, const float* xb, int64_t nb, int32_t d,
                          int32_t k, int32_t metric, float* D, int64_t* I,
                          const gbk_knn_opts* opts, void* stream) {
   clear_error();
-  GBK_REQUIRE(nq >= 0 && nq < (int64_t(1) << 31), "gbk_knn_brute: nq out of range");
-  GBK_REQUIRE(nb >= 1 && nb < (int64_t(1) << 31), "gbk_knn_brute: nb out of range");
-  GBK_REQUIRE(d >= 1, "gbk_knn_brute: d < 1");
-  GBK_REQUIRE(k >= 1 && k <= GBK_MAX_K && k <= nb, "gbk_knn_brute: k=%d out of [1, min(nb, %d)]",
-              k, GBK_MAX_K);
-  GBK_REQUIRE(metric == GBK_METRIC_L2 || metric == GBK_METRIC_IP, "gbk_knn_brute: bad metric");
-  if (nq == 0) return GBK_OK;
-  GBK_REQUIRE(xq && xb && D && I, "gbk_knn_brute: NULL pointer");
   KnnPlan plan;
-  if (opts) {
-    GBK_REQUIRE(opts->precision >= GBK_PREC_FP32 && opts->precision <= GBK_PREC_TF32X3,
-                "gbk_knn_brute: bad precision");
-    GBK_REQUIRE(opts->chunks >= 0, "gbk_knn_brute: chunks < 0");
-    GBK_REQUIRE(opts->prefilter >= -1 && opts->prefilter <= 1,
-                "gbk_knn_brute: prefilter must be -1, 0 or 1");
-    GBK_REQUIRE(opts->kprime == 0 || (opts->kprime >= k && opts->kprime <= GBK_MAX_K),
-                "gbk_knn_brute: kprime must be 0 or in [k, %d]", GBK_MAX_K);
-    plan.prec = opts->precision;
-    plan.chunks = opts->chunks;
-    plan.kprime = opts->kprime;
-    plan.certified = opts->certified;
-    plan.error_bound = opts->error_bound;
-    plan.exact = opts->exact != 0;
-    plan.prefilter = opts->prefilter;
-  }
+  gbk_status r = knn_args("gbk_knn_brute", nq, nb, d, k, metric, xq, xb, D, I, opts, &plan);
+  if (r != GBK_OK || nq == 0) return r;
   return knn_run(xq, nq, xb, nb, d, k, metric, D, I, plan, as_stream(stream));
+}
+
+gbk_status gbk_knn_brute_host(const float* xq, int64_t nq, const float* xb, int64_t nb,
+                              int32_t d, int32_t k, int32_t metric, float* D, int64_t* I,
+                              const gbk_knn_opts* opts, void* stream) {
+  clear_error();
+  KnnPlan plan;
+  gbk_status r =
+      knn_args("gbk_knn_brute_host", nq, nb, d, k, metric, xq, xb, D, I, opts, &plan);
+  if (r != GBK_OK || nq == 0) return r;
+  GBK_REQUIRE(!plan.certified && !plan.error_bound,
+              "gbk_knn_brute_host: certified / error_bound outputs are device arrays; use "
+              "gbk_knn_brute");
+  return knn_host_run(xq, nq, xb, nb, d, k, metric, D, I, plan, as_stream(stream));
 }
 
 gbk_status gbk_merge_topk(const float* D_parts, const int64_t* I_parts, int32_t nparts,

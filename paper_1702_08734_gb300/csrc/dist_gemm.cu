@@ -586,6 +586,48 @@ static int prefilter_tiles(int prefilter, int k, int ntiles, int epi) {
   return 4 * ts <= ntiles ? ts : 0;
 }
 
+// The threshold pre-pass (see prefilter_tiles) over the first tiles of B: per-(query, tile,
+// half) best values, then their k-th best per query as its initial threshold key thr[q]
+// (profiled as "*_bound").  Does nothing when prefilter_tiles gives none.
+static gbk_status prefilter_run(const PreparedOperand& Q, const PreparedOperand& B, int64_t nq,
+                                int64_t nb, int ntiles, int k, bool ip, int prefilter,
+                                uint32_t* thr, cudaStream_t st) {
+  const int epi = gemm_epi(Q.prec);
+  const int ts = prefilter_tiles(prefilter, k, ntiles, epi);
+  if (!ts) return GBK_OK;
+  ProfSuffix tag("_bound");
+  gbk_status r;
+  const int nv = ts * epi;
+  Scratch mins, Dk, Ik;
+  if ((r = mins.alloc(sizeof(float) * (size_t)nq * nv, st)) != GBK_OK) return r;
+  if ((r = Dk.alloc(sizeof(float) * (size_t)nq * k, st)) != GBK_OK) return r;
+  if ((r = Ik.alloc(sizeof(int64_t) * (size_t)nq * k, st)) != GBK_OK) return r;
+  GemmArgs p = {};
+  p.nq = (int)nq;
+  p.nb = (int)std::min<int64_t>(nb, (int64_t)ts * GEMM_BN);
+  p.nqt = (int)((nq + GEMM_BM - 1) / GEMM_BM);
+  p.ntiles = ts;
+  p.chunks = plan_chunks(p.nqt, ts, device_info().sm_count, 1);
+  p.tpc = (ts + p.chunks - 1) / p.chunks;
+  p.chunks = (ts + p.tpc - 1) / p.tpc;
+  p.k = 1;
+  p.kp = 1;
+  p.ynorm = B.norms.as<float>();
+  p.qscale = Q.scale.as<float>();
+  p.bscale = B.scale.as<float>();
+  p.out = mins.as<float>();
+  p.ldo = nv;
+  p.tile_min = 1;
+  if ((r = gemm_launch(MODE_SELECT, 0, ip, Q, B, p, st)) != GBK_OK) return r;
+  if ((r = kselect_run(mins.as<float>(), nq, nv, k, ip, Dk.as<float>(), Ik.as<int64_t>(), st,
+                       nullptr)) != GBK_OK)
+    return r;
+  ProfScope prof("kth_key", st);
+  kth_key_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(Dk.as<float>(), nq, k, ip, thr);
+  GBK_LAUNCH_CHECK();
+  return GBK_OK;
+}
+
 // Top-k (ascending distance / descending inner product) of prepared operands in their
 // own precision, written as full distances D and database rows I.
 static gbk_status select_run(const float* xq, const PreparedOperand& Q, const PreparedOperand& B,
@@ -638,41 +680,9 @@ static gbk_status select_run(const float* xq, const PreparedOperand& Q, const Pr
   if ((r = part.alloc(sizeof(uint64_t) * (size_t)nq * lists * a.kp, st)) != GBK_OK) return r;
   if ((r = thr.alloc(sizeof(uint32_t) * (size_t)nq, st)) != GBK_OK) return r;
   GBK_CUDA_CHECK(cudaMemsetAsync(thr.p, 0xff, sizeof(uint32_t) * (size_t)nq, st));
-  const int epi = gemm_epi(Q.prec);
-  if (const int ts = prefilter_tiles(prefilter, k, ntiles, epi)) {
-    // the threshold pre-pass: per-(query, tile, half) best values over the first ts tiles,
-    // then their k-th best per query as the initial threshold key (profiled as "*_bound")
-    ProfSuffix tag("_bound");
-    const int nv = ts * epi;
-    Scratch mins, Dk, Ik;
-    if ((r = mins.alloc(sizeof(float) * (size_t)nq * nv, st)) != GBK_OK) return r;
-    if ((r = Dk.alloc(sizeof(float) * (size_t)nq * k, st)) != GBK_OK) return r;
-    if ((r = Ik.alloc(sizeof(int64_t) * (size_t)nq * k, st)) != GBK_OK) return r;
-    GemmArgs p = {};
-    p.nq = (int)nq;
-    p.nb = (int)std::min<int64_t>(nb, (int64_t)ts * GEMM_BN);
-    p.nqt = a.nqt;
-    p.ntiles = ts;
-    p.chunks = plan_chunks(p.nqt, ts, device_info().sm_count, 1);
-    p.tpc = (ts + p.chunks - 1) / p.chunks;
-    p.chunks = (ts + p.tpc - 1) / p.tpc;
-    p.k = 1;
-    p.kp = 1;
-    p.ynorm = a.ynorm;
-    p.qscale = a.qscale;
-    p.bscale = a.bscale;
-    p.out = mins.as<float>();
-    p.ldo = nv;
-    p.tile_min = 1;
-    if ((r = gemm_launch(MODE_SELECT, 0, ip, Q, B, p, st)) != GBK_OK) return r;
-    if ((r = kselect_run(mins.as<float>(), nq, nv, k, ip, Dk.as<float>(), Ik.as<int64_t>(), st,
-                         nullptr)) != GBK_OK)
-      return r;
-    ProfScope prof("kth_key", st);
-    kth_key_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(Dk.as<float>(), nq, k, ip,
-                                                                 thr.as<uint32_t>());
-    GBK_LAUNCH_CHECK();
-  }
+  if ((r = prefilter_run(Q, B, nq, nb, ntiles, k, ip, prefilter, thr.as<uint32_t>(), st)) !=
+      GBK_OK)
+    return r;
   a.part = part.as<uint64_t>();
   a.thr_key = thr.as<uint32_t>();
   const int kpr = k == 1 ? 0 : a.kp / 32;
@@ -764,6 +774,136 @@ gbk_status knn_run(const float* xq, int64_t nq, const float* xb, int64_t nb, int
   scatter_rows_kernel<<<(unsigned)nu, 128, 0, st>>>(Du.as<float>(), Iu.as<int64_t>(),
                                                     idx.as<int64_t>(), k, D, I, cp);
   GBK_LAUNCH_CHECK();
+  return GBK_OK;
+}
+
+}  // namespace gbk
+
+namespace gbk {
+
+// Exact k-NN of host-resident queries and database, results to host memory.  With a
+// float32-accurate precision and the fused selection (k <= 512, nb > 65,536) the database
+// crosses to the GPU in pieces of 2^18 rows on a second stream while the fused GEMM runs
+// over the pieces already there: each piece's launch keeps its own candidate lists (one
+// slice of a shared buffer, its rows offset to database numbering) and all pieces filter
+// with the same per-query threshold keys, so one final merge gives the same result as a
+// single launch over the whole database.  Other cases copy everything, then search.
+gbk_status knn_host_run(const float* xq_h, int64_t nq, const float* xb_h, int64_t nb, int d,
+                        int k, int metric, float* D_h, int64_t* I_h, const KnnPlan& plan,
+                        cudaStream_t st) {
+  if (nq == 0) return GBK_OK;
+  gbk_status r;
+  const bool ip = metric == GBK_METRIC_IP;
+  Scratch xq, xb, Dd, Id;
+  if ((r = xq.alloc(sizeof(float) * (size_t)nq * d, st)) != GBK_OK) return r;
+  if ((r = xb.alloc(sizeof(float) * (size_t)nb * d, st)) != GBK_OK) return r;
+  if ((r = Dd.alloc(sizeof(float) * (size_t)nq * k, st)) != GBK_OK) return r;
+  if ((r = Id.alloc(sizeof(int64_t) * (size_t)nq * k, st)) != GBK_OK) return r;
+  GBK_CUDA_CHECK(cudaMemcpyAsync(xq.p, xq_h, sizeof(float) * (size_t)nq * d,
+                                 cudaMemcpyHostToDevice, st));
+  const bool accurate = plan.prec == GBK_PREC_FP32 || plan.prec == GBK_PREC_TF32X3;
+  constexpr int64_t PIECE_ROWS = (int64_t)1 << 18;
+  const int npieces = (accurate && k <= 512 && nb > 65536)
+                          ? (int)std::min<int64_t>(16, (nb + PIECE_ROWS - 1) / PIECE_ROWS)
+                          : 1;
+  if (npieces <= 1) {
+    GBK_CUDA_CHECK(cudaMemcpyAsync(xb.p, xb_h, sizeof(float) * (size_t)nb * d,
+                                   cudaMemcpyHostToDevice, st));
+    if ((r = knn_run(xq.as<float>(), nq, xb.as<float>(), nb, d, k, metric, Dd.as<float>(),
+                     Id.as<int64_t>(), plan, st)) != GBK_OK)
+      return r;
+  } else {
+    // piece p: rows [p * prows, min(nb, (p + 1) * prows)), prows a multiple of the tile
+    const int64_t prows = ((nb + npieces - 1) / npieces + GEMM_BN - 1) / GEMM_BN * GEMM_BN;
+    const int np = (int)((nb + prows - 1) / prows);
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[17] = {};
+    GBK_CUDA_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    // On every exit `st` first waits for all copies (so no buffer is freed under one in
+    // flight, even after an error); the stream and events are released once their queued
+    // work completes.
+    struct Cleanup {
+      cudaStream_t s, main;
+      cudaEvent_t* e;
+      ~Cleanup() {
+        for (int i = 0; i < 17; i++)
+          if (e[i]) cudaStreamWaitEvent(main, e[i], 0);
+        for (int i = 0; i < 17; i++)
+          if (e[i]) cudaEventDestroy(e[i]);
+        if (s) cudaStreamDestroy(s);
+      }
+    } cleanup{cs, st, ev};
+    for (int i = 0; i <= np; i++)
+      GBK_CUDA_CHECK(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+    // the copy stream starts after the buffers exist on `st`
+    GBK_CUDA_CHECK(cudaEventRecord(ev[np], st));
+    GBK_CUDA_CHECK(cudaStreamWaitEvent(cs, ev[np], 0));
+    for (int p = 0; p < np; p++) {
+      const int64_t r0 = p * prows, n = std::min(prows, nb - r0);
+      GBK_CUDA_CHECK(cudaMemcpyAsync(xb.as<float>() + r0 * d, xb_h + r0 * d,
+                                     sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, cs));
+      GBK_CUDA_CHECK(cudaEventRecord(ev[p], cs));
+    }
+    PreparedOperand Q;
+    if ((r = prepare_operand(xq.as<float>(), nq, d, plan.prec, nq, 0.f, &Q, st)) != GBK_OK)
+      return r;
+    const int epi = gemm_epi(Q.prec);
+    const int nqt = (int)((nq + GEMM_BM - 1) / GEMM_BM);
+    const int kp = k == 1 ? 1 : std::max(32, 1 << (32 - __builtin_clz((unsigned)(k - 1))));
+    int chunks[16], tpc[16], list0[16], lists = 0;
+    for (int p = 0; p < np; p++) {
+      const int64_t n = std::min(prows, nb - p * prows);
+      const int nt = (int)((n + GEMM_BN - 1) / GEMM_BN);
+      int c = plan.chunks > 0 ? std::min(plan.chunks, nt)
+                              : plan_chunks(nqt, nt, device_info().sm_count, k);
+      tpc[p] = (nt + c - 1) / c;
+      chunks[p] = (nt + tpc[p] - 1) / tpc[p];
+      list0[p] = lists;
+      lists += chunks[p] * epi;
+    }
+    Scratch part, thr;
+    if ((r = part.alloc(sizeof(uint64_t) * (size_t)nq * lists * kp, st)) != GBK_OK) return r;
+    if ((r = thr.alloc(sizeof(uint32_t) * (size_t)nq, st)) != GBK_OK) return r;
+    GBK_CUDA_CHECK(cudaMemsetAsync(thr.p, 0xff, sizeof(uint32_t) * (size_t)nq, st));
+    for (int p = 0; p < np; p++) {
+      const int64_t r0 = p * prows, n = std::min(prows, nb - r0);
+      const int nt = (int)((n + GEMM_BN - 1) / GEMM_BN);
+      GBK_CUDA_CHECK(cudaStreamWaitEvent(st, ev[p], 0));
+      PreparedOperand B;
+      if ((r = prepare_operand(xb.as<float>() + r0 * d, n, d, plan.prec, (int64_t)nt * GEMM_BN,
+                               0.f, &B, st)) != GBK_OK)
+        return r;
+      if (p == 0 && (r = prefilter_run(Q, B, nq, n, nt, k, ip, plan.prefilter,
+                                       thr.as<uint32_t>(), st)) != GBK_OK)
+        return r;
+      GemmArgs a = {};
+      a.nq = (int)nq;
+      a.nb = (int)n;
+      a.nqt = nqt;
+      a.ntiles = nt;
+      a.chunks = chunks[p];
+      a.tpc = tpc[p];
+      a.k = k;
+      a.kp = kp;
+      a.ynorm = B.norms.as<float>();
+      a.qscale = Q.scale.as<float>();
+      a.bscale = B.scale.as<float>();
+      a.part = part.as<uint64_t>();
+      a.part_lists = lists;
+      a.list0 = list0[p];
+      a.row0 = r0;
+      a.thr_key = thr.as<uint32_t>();
+      if ((r = gemm_launch(MODE_SELECT, k == 1 ? 0 : kp / 32, ip, Q, B, a, st)) != GBK_OK)
+        return r;
+    }
+    if ((r = knn_merge(part.as<uint64_t>(), nq, lists, kp, k, ip ? nullptr : Q.norms.as<float>(),
+                       ip, Dd.as<float>(), Id.as<int64_t>(), st)) != GBK_OK)
+      return r;
+  }
+  GBK_CUDA_CHECK(cudaMemcpyAsync(D_h, Dd.p, sizeof(float) * (size_t)nq * k,
+                                 cudaMemcpyDeviceToHost, st));
+  GBK_CUDA_CHECK(cudaMemcpyAsync(I_h, Id.p, sizeof(int64_t) * (size_t)nq * k,
+                                 cudaMemcpyDeviceToHost, st));
   return GBK_OK;
 }
 

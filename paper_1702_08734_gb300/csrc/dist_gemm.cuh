@@ -112,7 +112,10 @@ struct GemmArgs {
   const float* xnorm;    // STORE: [nq] ||x||^2 added (and the sum clamped at 0), or null
   const float* qscale;   // [nq] per-query dequantisation scale (FP8), else null
   const float* bscale;   // [ntiles*128] per-row database scale (FP8), else null
-  uint64_t* part;        // SELECT: [nq][chunks * EPI][kp] sorted composite lists
+  uint64_t* part;        // SELECT: [nq][part_lists][kp] sorted composite lists; this launch
+                         // uses lists [list0, list0 + chunks * EPI)
+  int part_lists, list0; // part_lists 0: chunks * EPI
+  int64_t row0;          // added to the database row numbers stored in the lists
   uint32_t* thr_key;     // SELECT: [nq] global threshold keys (init 0xffffffff)
   float* out;            // STORE: [nq][ldo] partial distances; tile_min: [nq][ldo] minima
   int64_t ldo;

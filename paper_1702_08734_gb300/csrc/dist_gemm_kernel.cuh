@@ -456,7 +456,10 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     uint64_t* myQ = sQ + (half * GEMM_BM + qrow) * GEMM_QSTRIDE;
     float* sY = reinterpret_cast<float*>(smem + lay.y_off) + (warp - 3) * 256;  // norms, scales
-    const int lists = args.chunks * EPI;   // candidate lists per query
+    // candidate lists per query (this launch's start at list0 when several launches, one
+    // per database piece, share the buffer)
+    const int lists = args.part_lists ? args.part_lists : args.chunks * EPI;
+    const int list0 = args.list0;
     const uint64_t lpol = l2_keep_policy();
     const bool vec_out = MODE == MODE_STORE && (args.ldo & 3) == 0 &&
                          (reinterpret_cast<uintptr_t>(args.out) & 15) == 0;
@@ -498,7 +501,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           for (int j = 0; j < 32; j++) {
             const int qq = qt * GEMM_BM + quarter * 32 + j;
             if (qq < args.nq) {
-              uint64_t* Lg = args.part + ((int64_t)qq * lists + ch * EPI + half) * args.kp;
+              uint64_t* Lg = args.part + ((int64_t)qq * lists + list0 + ch * EPI + half) * args.kp;
               for (int r = lane; r < args.kp; r += 32) st_keep(Lg + r, ~0ull, lpol);
             }
           }
@@ -508,7 +511,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       // lists of this warp's 32 queries (lane l: pbase + l * rowstride) and their queues
       const int64_t rowstride = (int64_t)lists * args.kp;
       uint64_t* pbase =
-          QUEUES ? args.part + ((int64_t)(qt * GEMM_BM + quarter * 32) * lists + ch * EPI + half) *
+          QUEUES ? args.part + ((int64_t)(qt * GEMM_BM + quarter * 32) * lists + list0 + ch * EPI + half) *
                                    args.kp
                  : nullptr;
       const uint2* sQh = reinterpret_cast<const uint2*>(sQ + (half * GEMM_BM + quarter * 32) * GEMM_QSTRIDE);
@@ -619,7 +622,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
               for (int j = 31; j >= 0; j--)
                 if (dist[j] == bm) jj = j;  // lowest column holding the best value
               bestd = bm;
-              besti = cbase + jj;
+              besti = (int)args.row0 + cbase + jj;
             }
           } else {
             const bool any = LARGEST ? bm >= thr : bm <= thr;
@@ -632,7 +635,8 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
                   for (int jj = 0; jj < 16; jj++) {
                     const float dv = dist[hf * 16 + jj];
                     if (LARGEST ? dv >= thr : dv <= thr)
-                      q2[cnt++] = make_uint2(__float_as_uint(dv), (uint32_t)(cbase + hf * 16 + jj));
+                      q2[cnt++] = make_uint2(__float_as_uint(dv),
+                                             (uint32_t)(args.row0 + cbase + hf * 16 + jj));
                   }
                 }
                 merge_queues<KPR, LARGEST>(GEMM_QCAP - 16, cnt, thr, sQh, pbase, rowstride,
@@ -697,7 +701,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           merge_queues<KPR, LARGEST>(0, cnt, thr, sQh, pbase, rowstride, args.k, quarter, lane,
                                      lpol, ts);
         } else if (qvalid && !args.tile_min) {
-          args.part[(int64_t)q * lists + ch * EPI + half] =
+          args.part[(int64_t)q * lists + list0 + ch * EPI + half] =
               besti >= 0 ? composite(ordered_key(bestd, LARGEST), (uint32_t)besti) : ~0ull;
         }
       }

@@ -302,8 +302,7 @@ struct BlockSelect {
     constexpr int E = KP / THREADS;  // elements per thread in the register sort
     if constexpr ((THREADS & (THREADS - 1)) == 0 && E >= 2 && E <= 16) {
       sort_registers(s);
-      return;
-    }
+    } else {
     for (int size = 2; size <= KP; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
         for (int t = threadIdx.x; t < KP / 2; t += THREADS) {
@@ -318,6 +317,7 @@ struct BlockSelect {
         }
         __syncthreads();
       }
+    }
     }
   }
 

@@ -383,3 +383,43 @@ def test_pairwise_long_rows(gbk):
     P = gbk.pairwise_distances(torch.from_numpy(xq).cuda(), torch.from_numpy(xb).cuda())
     ex = ((xq.astype(np.float64)[:, None, :] - xb.astype(np.float64)[None]) ** 2).sum(-1)
     np.testing.assert_allclose(P.cpu().numpy(), ex, rtol=2e-5, atol=1e-3)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+@pytest.mark.parametrize("k", [1, 10, 100])
+def test_host_buffers_match_device_search(gbk, prec, metric, k):
+    # host inputs and outputs: the database crosses in pieces of 2^18 rows while the
+    # search runs over the pieces already copied; the result is the device search's, bit
+    # for bit (same per-pair arithmetic, one shared threshold, one final merge)
+    xq = torch.from_numpy(datagen.gaussian_matrix(91, 700, 64)).pin_memory()
+    xb = torch.from_numpy(datagen.gaussian_matrix(92, 600000, 64)).pin_memory()
+    Dd, Id = gbk.knn_brute(xq.cuda(), xb.cuda(), k, metric=metric, precision=prec)
+    Dh, Ih = gbk.knn_brute_host(xq, xb, k, metric=metric, precision=prec)
+    assert Dh.device.type == "cpu"
+    assert torch.equal(Id.cpu(), Ih) and torch.equal(Dd.cpu(), Dh)
+
+
+def test_host_buffers_ties_and_other_paths(gbk):
+    # integer lattice (exact distances, many ties) across pieces; the paths that copy
+    # everything first (low precision, k > 512, short databases) give the device result too
+    rng = np.random.default_rng(9)
+    xb = torch.from_numpy(rng.integers(-2, 3, size=(300000, 12)).astype(np.float32))
+    xb[290000:291000] = xb[:1000]
+    xq = torch.from_numpy(rng.integers(-2, 3, size=(100, 12)).astype(np.float32))
+    Dh, Ih = gbk.knn_brute_host(xq.pin_memory(), xb.pin_memory(), 50)
+    Do, Io = oracle.knn(xq.numpy(), xb.numpy(), 50)
+    np.testing.assert_array_equal(Ih.numpy(), Io)
+    np.testing.assert_array_equal(Dh.numpy(), Do.astype(np.float32))
+    xq2 = torch.from_numpy(datagen.gaussian_matrix(93, 200, 32))
+    xb2 = torch.from_numpy(datagen.gaussian_matrix(94, 70000, 32))
+    for kw in ({"k": 600}, {"k": 10, "precision": "bf16", "exact": True}):
+        Dd, Id = gbk.knn_brute(xq2.cuda(), xb2.cuda(), **kw)
+        Dh, Ih = gbk.knn_brute_host(xq2, xb2, **kw)  # pageable host memory
+        assert torch.equal(Id.cpu(), Ih) and torch.equal(Dd.cpu(), Dh)
+    xb3 = torch.from_numpy(datagen.gaussian_matrix(95, 5000, 32))
+    Dd, Id = gbk.knn_brute(xq2.cuda(), xb3.cuda(), 20)
+    Dh, Ih = gbk.knn_brute_host(xq2, xb3, 20)
+    assert torch.equal(Id.cpu(), Ih) and torch.equal(Dd.cpu(), Dh)
+    with pytest.raises(gbk.GbkError):
+        gbk.knn_brute_host(xq2, xb3, 6000)
