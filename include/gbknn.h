@@ -204,8 +204,9 @@ gbk_status gbk_knn_brute(const float* xq, int64_t nq, const float* xb, int64_t n
  * search and the device->host copies of D and I on `stream` and returns; D and I are
  * valid once the stream has been synchronised, and the host arrays must stay alive until
  * then.  With a float32-accurate precision and the fused selection (k <= 512, nb > 65,536)
- * the database is copied in pieces of 2^18 rows on a second stream while the search runs
- * over the pieces already copied (the result is that of gbk_knn_brute).  Device scratch:
+ * the database is copied in growing pieces (2^16, 2^17, ... rows) on a second stream while
+ * the search runs over the pieces already copied (the result is that of gbk_knn_brute).
+ * Device scratch:
  * the inputs, outputs and the search's own.  Options as gbk_knn_brute, except that the
  * certified / error_bound outputs are not available (GBK_EINVAL).  Errors: as
  * gbk_knn_brute.

@@ -783,7 +783,7 @@ namespace gbk {
 
 // Exact k-NN of host-resident queries and database, results to host memory.  With a
 // float32-accurate precision and the fused selection (k <= 512, nb > 65,536) the database
-// crosses to the GPU in pieces of 2^18 rows on a second stream while the fused GEMM runs
+// crosses to the GPU in growing pieces on a second stream while the fused GEMM runs
 // over the pieces already there: each piece's launch keeps its own candidate lists (one
 // slice of a shared buffer, its rows offset to database numbering) and all pieces filter
 // with the same per-query threshold keys, so one final merge gives the same result as a
@@ -802,20 +802,31 @@ gbk_status knn_host_run(const float* xq_h, int64_t nq, const float* xb_h, int64_
   GBK_CUDA_CHECK(cudaMemcpyAsync(xq.p, xq_h, sizeof(float) * (size_t)nq * d,
                                  cudaMemcpyHostToDevice, st));
   const bool accurate = plan.prec == GBK_PREC_FP32 || plan.prec == GBK_PREC_TF32X3;
-  constexpr int64_t PIECE_ROWS = (int64_t)1 << 18;
-  const int npieces = (accurate && k <= 512 && nb > 65536)
-                          ? (int)std::min<int64_t>(16, (nb + PIECE_ROWS - 1) / PIECE_ROWS)
-                          : 1;
-  if (npieces <= 1) {
+  // pieces of 2^16, 2^17, 2^18 ... rows: the search runs about twice as long per row as
+  // the copy, so each piece arrives while the previous one is searched and only the first,
+  // small one is exposed; a remainder shorter than half the next size joins the last piece
+  int64_t pstart[17];
+  int np = 0;
+  if (accurate && k <= 512 && nb > 65536) {
+    int64_t r0 = 0, size = (int64_t)1 << 16;
+    while (r0 < nb && np < 16) {
+      int64_t n = std::min(size, nb - r0);
+      if (nb - (r0 + n) < size || np == 15) n = nb - r0;  // the remainder joins this piece
+      pstart[np++] = r0;
+      r0 += n;
+      size *= 2;
+    }
+    pstart[np] = nb;
+  }
+  if (np <= 1) {
     GBK_CUDA_CHECK(cudaMemcpyAsync(xb.p, xb_h, sizeof(float) * (size_t)nb * d,
                                    cudaMemcpyHostToDevice, st));
     if ((r = knn_run(xq.as<float>(), nq, xb.as<float>(), nb, d, k, metric, Dd.as<float>(),
                      Id.as<int64_t>(), plan, st)) != GBK_OK)
       return r;
   } else {
-    // piece p: rows [p * prows, min(nb, (p + 1) * prows)), prows a multiple of the tile
-    const int64_t prows = ((nb + npieces - 1) / npieces + GEMM_BN - 1) / GEMM_BN * GEMM_BN;
-    const int np = (int)((nb + prows - 1) / prows);
+    // piece p: rows [pstart[p], pstart[p + 1]); all but the last start at multiples of the
+    // tile (powers of two >= 2^16)
     cudaStream_t cs = nullptr;
     cudaEvent_t ev[17] = {};
     GBK_CUDA_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -839,7 +850,7 @@ gbk_status knn_host_run(const float* xq_h, int64_t nq, const float* xb_h, int64_
     GBK_CUDA_CHECK(cudaEventRecord(ev[np], st));
     GBK_CUDA_CHECK(cudaStreamWaitEvent(cs, ev[np], 0));
     for (int p = 0; p < np; p++) {
-      const int64_t r0 = p * prows, n = std::min(prows, nb - r0);
+      const int64_t r0 = pstart[p], n = pstart[p + 1] - r0;
       GBK_CUDA_CHECK(cudaMemcpyAsync(xb.as<float>() + r0 * d, xb_h + r0 * d,
                                      sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, cs));
       GBK_CUDA_CHECK(cudaEventRecord(ev[p], cs));
@@ -852,7 +863,7 @@ gbk_status knn_host_run(const float* xq_h, int64_t nq, const float* xb_h, int64_
     const int kp = k == 1 ? 1 : std::max(32, 1 << (32 - __builtin_clz((unsigned)(k - 1))));
     int chunks[16], tpc[16], list0[16], lists = 0;
     for (int p = 0; p < np; p++) {
-      const int64_t n = std::min(prows, nb - p * prows);
+      const int64_t n = pstart[p + 1] - pstart[p];
       const int nt = (int)((n + GEMM_BN - 1) / GEMM_BN);
       int c = plan.chunks > 0 ? std::min(plan.chunks, nt)
                               : plan_chunks(nqt, nt, device_info().sm_count, k);
@@ -866,7 +877,7 @@ gbk_status knn_host_run(const float* xq_h, int64_t nq, const float* xb_h, int64_
     if ((r = thr.alloc(sizeof(uint32_t) * (size_t)nq, st)) != GBK_OK) return r;
     GBK_CUDA_CHECK(cudaMemsetAsync(thr.p, 0xff, sizeof(uint32_t) * (size_t)nq, st));
     for (int p = 0; p < np; p++) {
-      const int64_t r0 = p * prows, n = std::min(prows, nb - r0);
+      const int64_t r0 = pstart[p], n = pstart[p + 1] - r0;
       const int nt = (int)((n + GEMM_BN - 1) / GEMM_BN);
       GBK_CUDA_CHECK(cudaStreamWaitEvent(st, ev[p], 0));
       PreparedOperand B;

@@ -389,7 +389,7 @@ def test_pairwise_long_rows(gbk):
 @pytest.mark.parametrize("metric", ["l2", "ip"])
 @pytest.mark.parametrize("k", [1, 10, 100])
 def test_host_buffers_match_device_search(gbk, prec, metric, k):
-    # host inputs and outputs: the database crosses in pieces of 2^18 rows while the
+    # host inputs and outputs: the database crosses in growing pieces while the
     # search runs over the pieces already copied; the result is the device search's, bit
     # for bit (same per-pair arithmetic, one shared threshold, one final merge)
     xq = torch.from_numpy(datagen.gaussian_matrix(91, 700, 64)).pin_memory()
