@@ -431,15 +431,23 @@ gbk_status prepare_operand(const float* x, int64_t n, int d, int prec, int64_t n
   return GBK_OK;
 }
 
+// Chunks whose candidate lists ([nq][chunks * epi][kp] composites) fit in 4 GiB.
+static int list_chunk_cap(int64_t nq, int epi, int kp) {
+  const int64_t per_chunk = std::max<int64_t>(1, nq * epi * kp * 8);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(512, ((int64_t)4 << 30) / per_chunk));
+}
+
 // Chunks S minimising waves x (tiles per chunk + per-item overhead); ties to fewer chunks.
 // The overhead is a chunk's candidate lists learning their threshold again: measured at
 // about 0.9 k tiles per (query tile, chunk) item for k = 16..128 (1e4 - 5e4 queries), none
-// for k = 1.
-int plan_chunks(int nqt, int ntiles, int grid_cap, int k) {
+// for k = 1.  At most max_chunks (the candidate lists' memory, nq x chunks x lists, grows
+// with S: with 10^8 queries a rounding gain of a few tiles would otherwise buy 100+
+// chunks and 200 GB of lists).
+int plan_chunks(int nqt, int ntiles, int grid_cap, int k, int max_chunks) {
   int best = 1;
   int64_t best_cost = INT64_MAX;
   const int64_t ovh = k <= 1 ? 0 : (9 * (int64_t)k + 9) / 10;
-  for (int S = 1; S <= std::min(ntiles, 512); S++) {
+  for (int S = 1; S <= std::min(std::min(ntiles, 512), std::max(1, max_chunks)); S++) {
     const int64_t waves = ((int64_t)nqt * S + grid_cap - 1) / grid_cap;
     const int64_t tpc = (ntiles + S - 1) / S;
     const int64_t cost = waves * (tpc + ovh) * 64 + S;  // + small penalty per chunk (merge)
@@ -666,12 +674,13 @@ static gbk_status select_run(const float* xq, const PreparedOperand& Q, const Pr
   a.nb = (int)nb;
   a.nqt = (int)((nq + GEMM_BM - 1) / GEMM_BM);
   a.ntiles = ntiles;
+  a.kp = k == 1 ? 1 : std::max(32, 1 << (32 - __builtin_clz((unsigned)(k - 1))));
   a.chunks = chunks_opt > 0 ? std::min(chunks_opt, ntiles)
-                            : plan_chunks(a.nqt, ntiles, device_info().sm_count, k);
+                            : plan_chunks(a.nqt, ntiles, device_info().sm_count, k,
+                                          list_chunk_cap(nq, gemm_epi(Q.prec), a.kp));
   a.tpc = (ntiles + a.chunks - 1) / a.chunks;
   a.chunks = (ntiles + a.tpc - 1) / a.tpc;
   a.k = k;
-  a.kp = k == 1 ? 1 : std::max(32, 1 << (32 - __builtin_clz((unsigned)(k - 1))));
   a.ynorm = B.norms.as<float>();
   a.qscale = Q.scale.as<float>();
   a.bscale = B.scale.as<float>();
@@ -866,7 +875,8 @@ gbk_status knn_host_run(const float* xq_h, int64_t nq, const float* xb_h, int64_
       const int64_t n = pstart[p + 1] - pstart[p];
       const int nt = (int)((n + GEMM_BN - 1) / GEMM_BN);
       int c = plan.chunks > 0 ? std::min(plan.chunks, nt)
-                              : plan_chunks(nqt, nt, device_info().sm_count, k);
+                              : plan_chunks(nqt, nt, device_info().sm_count, k,
+                                            list_chunk_cap(nq, epi, kp) / np);
       tpc[p] = (nt + c - 1) / c;
       chunks[p] = (nt + tpc[p] - 1) / tpc[p];
       list0[p] = lists;

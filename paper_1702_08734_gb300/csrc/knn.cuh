@@ -47,7 +47,7 @@ gbk_status knn_host_run(const float* xq_h, int64_t nq, const float* xb_h, int64_
                         int k, int metric, float* D_h, int64_t* I_h, const KnnPlan& plan,
                         cudaStream_t st);
 
-int plan_chunks(int nqt, int ntiles, int grid_cap, int k);
+int plan_chunks(int nqt, int ntiles, int grid_cap, int k, int max_chunks = 512);
 
 // Top k of nparts sorted partial lists per query: Dp/Ip [nparts][nq][kin] (ids < 2^32;
 // negative ids skipped) -> D/I [nq][k], order (value, id); padding (+-inf, -1).
