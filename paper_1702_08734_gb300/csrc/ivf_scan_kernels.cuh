@@ -257,7 +257,11 @@ __global__ void __launch_bounds__(THREADS, 2)
       }
       Sel::template push<U>(s, mask, cc);
       __syncthreads();
-      if (s.n_buf > CAP - STEP) {
+      // compact when the buffer fills, and once early, as soon as a step's worth of
+      // candidates is there while fewer than k are kept: the k-th of them becomes the
+      // threshold, so later steps push a fraction of their codes instead of all of them
+      // (uniform: both counts are read after the barrier)
+      if (s.n_buf > CAP - STEP || (s.n_top < kq && s.n_buf >= STEP)) {
         Sel::compact(s, kq);
         const uint32_t tk = (uint32_t)(s.thr >> 32);
         thr = tk == NAN_KEY ? __int_as_float(0x7f800000) : key_value(tk, false);
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(256)
         }
         Sel::template push<U>(s, mask, cc);
         __syncthreads();
-        if (s.n_buf > CAP - STEP) {
+        if (s.n_buf > CAP - STEP || (s.n_top < kq && s.n_buf >= STEP)) {  // as above
           Sel::compact(s, kq);
           f.set((uint32_t)(s.thr >> 32), false);
         }
