@@ -198,6 +198,26 @@ gbk_status gbk_knn_brute(const float* xq, int64_t nq, const float* xb, int64_t n
                          const gbk_knn_opts* opts, void* stream);
 
 /*
+ * A database prepared once for repeated exact k-NN searches (section 5.1's exact search
+ * against a fixed database): the operand pieces of `precision` (the FP16 / TF32 hi-lo
+ * split, BF16 or FP8 with row scales) and the squared norms are formed at creation and
+ * kept in device memory owned by the handle, so each gbk_knn_db_search skips that pass
+ * over the database.  xb [nb][d] float32 (device) is NOT copied: it must stay valid and
+ * unchanged while the handle is used (the BF16/FP8 re-rank and the float32 repair read
+ * it).  gbk_knn_db_search takes the arguments and options of gbk_knn_brute (opts may be
+ * NULL; a precision other than the handle's is GBK_EINVAL) and returns the same results.
+ * gbk_knn_db_destroy frees the handle's device memory stream-ordered on `stream`.
+ * Errors: GBK_EINVAL, GBK_ENOMEM, GBK_ECUDA, and those of gbk_knn_brute.
+ */
+typedef struct gbk_knn_db gbk_knn_db;
+gbk_status gbk_knn_db_create(const float* xb, int64_t nb, int32_t d, int32_t precision,
+                             gbk_knn_db** out, void* stream);
+gbk_status gbk_knn_db_search(const gbk_knn_db* db, const float* xq, int64_t nq, int32_t k,
+                             int32_t metric, float* D, int64_t* I, const gbk_knn_opts* opts,
+                             void* stream);
+void gbk_knn_db_destroy(gbk_knn_db* db, void* stream);
+
+/*
  * gbk_knn_brute with HOST arrays: xq [nq][d], xb [nb][d] float32 and the outputs D [nq][k],
  * I [nq][k] in host memory (page-locked for the copies to overlap the search; pageable
  * memory works but serialises them).  The call enqueues the host->device copies, the

@@ -45,6 +45,8 @@ _SIGNATURES = {
     "gbk_selftest_wait_timeout": [_i64, _vp],
     "gbk_knn_brute": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
     "gbk_knn_brute_host": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
+    "gbk_knn_db_create": [_vp, _i64, _i32, _i32, _vp, _vp],
+    "gbk_knn_db_search": [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp, _vp],
     "gbk_pairwise_distances": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _vp, _i64, _vp],
 }
 
@@ -243,6 +245,52 @@ def knn_brute(xq: torch.Tensor, xb: torch.Tensor, k: int, metric="l2", precision
     _call("gbk_knn_brute", _ptr(xq), nq, _ptr(xb), nb, int(d), int(k), _metric(metric), _ptr(D),
           _ptr(I), ctypes.byref(opts), _stream())
     return (D, I, cert, eb) if certify else (D, I)
+
+
+class KnnDatabase:
+    """A database prepared once for repeated exact k-NN searches (gbk_knn_db_*): the operand
+    pieces of `precision` and the norms stay on the device; `xb` (CUDA float32) is kept
+    referenced, unchanged, for the re-rank and repair.  search() takes knn_brute's arguments
+    and returns the same results."""
+
+    def __init__(self, xb: torch.Tensor, precision="fp32"):
+        _dev(xb, torch.float32, "xb")
+        lib = load()
+        lib.gbk_knn_db_destroy.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        lib.gbk_knn_db_destroy.restype = None
+        self._xb = xb.contiguous()
+        self.precision = precision
+        self._h = ctypes.c_void_p()
+        _call("gbk_knn_db_create", _ptr(self._xb), self._xb.shape[0], int(self._xb.shape[1]),
+              PRECISIONS[precision], ctypes.byref(self._h), _stream())
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().gbk_knn_db_destroy(self._h, _stream())
+            self._h = ctypes.c_void_p()
+
+    def search(self, xq: torch.Tensor, k: int, metric="l2", kprime: int = 0, chunks: int = 0,
+               out=None, certify: bool = False, exact: bool = False, prefilter: int = 0):
+        _dev(xq, torch.float32, "xq")
+        nq, d = xq.shape
+        if d != self._xb.shape[1]:
+            raise ValueError("dimension mismatch")
+        if out is None:
+            D = torch.empty((nq, k), dtype=torch.float32, device=xq.device)
+            I = torch.empty((nq, k), dtype=torch.int64, device=xq.device)
+        else:
+            D, I = out
+        cert = eb = None
+        if certify:
+            cert = torch.empty(nq, dtype=torch.int32, device=xq.device)
+            eb = torch.empty(nq, dtype=torch.float32, device=xq.device)
+        opts = KnnOpts(PRECISIONS[self.precision], int(kprime), int(chunks),
+                       cert.data_ptr() if cert is not None else None,
+                       eb.data_ptr() if eb is not None else None, int(bool(exact)),
+                       int(prefilter))
+        _call("gbk_knn_db_search", self._h, _ptr(xq), nq, int(k), _metric(metric), _ptr(D),
+              _ptr(I), ctypes.byref(opts), _stream())
+        return (D, I, cert, eb) if certify else (D, I)
 
 
 def knn_brute_host(xq: torch.Tensor, xb: torch.Tensor, k: int, metric="l2", precision="fp32",

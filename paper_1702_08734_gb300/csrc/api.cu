@@ -307,6 +307,66 @@ gbk_status gbk_knn_brute(const float* xq, int64_t nq, const float* xb, int64_t n
   return knn_run(xq, nq, xb, nb, d, k, metric, D, I, plan, as_stream(stream));
 }
 
+}  // extern "C"
+
+struct gbk_knn_db {
+  gbk::PreparedOperand B;  // the database operand in its precision
+  const float* xb = nullptr;
+  int64_t nb = 0;
+  int d = 0, prec = 0;
+};
+
+extern "C" {
+
+gbk_status gbk_knn_db_create(const float* xb, int64_t nb, int32_t d, int32_t precision,
+                             gbk_knn_db** out, void* stream) {
+  clear_error();
+  GBK_REQUIRE(out, "gbk_knn_db_create: out is NULL");
+  GBK_REQUIRE(xb, "gbk_knn_db_create: xb is NULL");
+  GBK_REQUIRE(nb >= 1 && nb < (int64_t(1) << 31), "gbk_knn_db_create: nb out of range");
+  GBK_REQUIRE(d >= 1, "gbk_knn_db_create: d < 1");
+  GBK_REQUIRE(precision >= GBK_PREC_FP32 && precision <= GBK_PREC_TF32X3,
+              "gbk_knn_db_create: bad precision");
+  gbk_knn_db* db = new gbk_knn_db();
+  db->xb = xb;
+  db->nb = nb;
+  db->d = d;
+  db->prec = precision;
+  const gbk_status r = prepare_database(xb, nb, d, precision, &db->B, as_stream(stream));
+  if (r != GBK_OK) {
+    delete db;
+    return r;
+  }
+  *out = db;
+  return GBK_OK;
+}
+
+gbk_status gbk_knn_db_search(const gbk_knn_db* db, const float* xq, int64_t nq, int32_t k,
+                             int32_t metric, float* D, int64_t* I, const gbk_knn_opts* opts,
+                             void* stream) {
+  clear_error();
+  GBK_REQUIRE(db, "gbk_knn_db_search: db is NULL");
+  KnnPlan plan;
+  plan.prec = db->prec;
+  gbk_status r = knn_args("gbk_knn_db_search", nq, db->nb, db->d, k, metric, xq, db->xb, D, I,
+                          opts, &plan);
+  if (r != GBK_OK || nq == 0) return r;
+  GBK_REQUIRE(!opts || opts->precision == db->prec,
+              "gbk_knn_db_search: options ask for precision %d, the database is prepared in %d",
+              opts ? opts->precision : 0, db->prec);
+  return knn_run_prepared(xq, nq, db->xb, db->B, db->nb, db->d, k, metric, D, I, plan,
+                          as_stream(stream));
+}
+
+void gbk_knn_db_destroy(gbk_knn_db* db, void* stream) {
+  if (!db) return;
+  cudaStream_t st = as_stream(stream);
+  db->B.data.stream = st;  // freed stream-ordered on the caller's stream
+  db->B.norms.stream = st;
+  db->B.scale.stream = st;
+  delete db;
+}
+
 gbk_status gbk_knn_brute_host(const float* xq, int64_t nq, const float* xb, int64_t nb,
                               int32_t d, int32_t k, int32_t metric, float* D, int64_t* I,
                               const gbk_knn_opts* opts, void* stream) {

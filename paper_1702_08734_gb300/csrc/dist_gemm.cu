@@ -718,17 +718,29 @@ __global__ void scatter_rows_kernel(const float* __restrict__ Du, const int64_t*
   if (threadIdx.x == 0) certified[q] = 2;
 }
 
+gbk_status prepare_database(const float* xb, int64_t nb, int d, int prec, PreparedOperand* B,
+                            cudaStream_t st) {
+  const int ntiles = (int)((nb + GEMM_BN - 1) / GEMM_BN);
+  return prepare_operand(xb, nb, d, prec, (int64_t)ntiles * GEMM_BN, 0.f, B, st);
+}
+
 gbk_status knn_run(const float* xq, int64_t nq, const float* xb, int64_t nb, int d, int k,
                    int metric, float* D, int64_t* I, const KnnPlan& plan, cudaStream_t st) {
   if (nq == 0) return GBK_OK;
+  PreparedOperand B;
+  gbk_status r;
+  if ((r = prepare_database(xb, nb, d, plan.prec, &B, st)) != GBK_OK) return r;
+  return knn_run_prepared(xq, nq, xb, B, nb, d, k, metric, D, I, plan, st);
+}
+
+gbk_status knn_run_prepared(const float* xq, int64_t nq, const float* xb,
+                            const PreparedOperand& B, int64_t nb, int d, int k, int metric,
+                            float* D, int64_t* I, const KnnPlan& plan, cudaStream_t st) {
+  if (nq == 0) return GBK_OK;
   const bool ip = metric == GBK_METRIC_IP;
-  const int ntiles = (int)((nb + GEMM_BN - 1) / GEMM_BN);
-  PreparedOperand Q, B;
+  PreparedOperand Q;
   gbk_status r;
   if ((r = prepare_operand(xq, nq, d, plan.prec, nq, 0.f, &Q, st)) != GBK_OK) return r;
-  if ((r = prepare_operand(xb, nb, d, plan.prec, (int64_t)ntiles * GEMM_BN, 0.f, &B, st)) !=
-      GBK_OK)
-    return r;
   if (plan.prec == GBK_PREC_FP32 || plan.prec == GBK_PREC_TF32X3)  // float32-accurate kinds
     return select_run(xq, Q, B, nq, nb, d, k, ip, plan.chunks, plan.prefilter, D, I, st);
   // low precision: over-fetch k' candidates, then the exact float32 re-rank + certificate.

@@ -42,6 +42,15 @@ gbk_status pairwise_run(const PreparedOperand& Q, const PreparedOperand& B, bool
 // Exact k-NN (arguments validated by the caller).
 gbk_status knn_run(const float* xq, int64_t nq, const float* xb, int64_t nb, int d, int k,
                    int metric, float* D, int64_t* I, const KnnPlan& plan, cudaStream_t st);
+// The database operand of knn_run in the plan's precision (rows padded to whole tiles),
+// and knn_run on such a prepared database (xb: its float32 rows, used by the low-precision
+// re-rank and the float32 repair).
+gbk_status prepare_database(const float* xb, int64_t nb, int d, int prec, PreparedOperand* B,
+                            cudaStream_t st);
+gbk_status knn_run_prepared(const float* xq, int64_t nq, const float* xb,
+                            const PreparedOperand& B, int64_t nb, int d, int k, int metric,
+                            float* D, int64_t* I, const KnnPlan& plan, cudaStream_t st);
+
 // The same with host-resident inputs and outputs (D_h, I_h written by copies on `st`).
 gbk_status knn_host_run(const float* xq_h, int64_t nq, const float* xb_h, int64_t nb, int d,
                         int k, int metric, float* D_h, int64_t* I_h, const KnnPlan& plan,

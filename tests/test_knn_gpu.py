@@ -423,3 +423,24 @@ def test_host_buffers_ties_and_other_paths(gbk):
     assert torch.equal(Id.cpu(), Ih) and torch.equal(Dd.cpu(), Dh)
     with pytest.raises(gbk.GbkError):
         gbk.knn_brute_host(xq2, xb3, 6000)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16", "fp8"])
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+def test_prepared_database_matches_brute(gbk, prec, metric):
+    # a database prepared once and searched repeatedly gives knn_brute's results bit for bit
+    xb = torch.from_numpy(datagen.gaussian_matrix(96, 90000, 64)).cuda()
+    db = gbk.KnnDatabase(xb, precision=prec)
+    for seed, k in ((97, 10), (98, 100), (99, 1)):
+        xq = torch.from_numpy(datagen.gaussian_matrix(seed, 300, 64)).cuda()
+        D0, I0 = gbk.knn_brute(xq, xb, k, metric=metric, precision=prec, exact=prec in ("bf16", "fp8"))
+        D1, I1 = db.search(xq, k, metric=metric, exact=prec in ("bf16", "fp8"))
+        assert torch.equal(I0, I1) and torch.equal(D0, D1)
+    with pytest.raises(gbk.GbkError):  # another precision than the prepared one
+        gbk.load()
+        opts = gbk.KnnOpts(gbk.PRECISIONS["fp32" if prec != "fp32" else "bf16"], 0, 0, None, None, 0, 0)
+        D = torch.empty((300, 10), device="cuda")
+        I = torch.empty((300, 10), dtype=torch.int64, device="cuda")
+        gbk._call("gbk_knn_db_search", db._h, gbk._ptr(xq), 300, 10, 0, gbk._ptr(D), gbk._ptr(I),
+                  gbk.ctypes.byref(opts), gbk._stream())
+    del db
