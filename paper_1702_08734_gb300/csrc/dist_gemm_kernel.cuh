@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
       if (MODE == MODE_SELECT) {
         if (!qvalid) {
           thr = -PASS_ALL;
-        } else {
+        } else if (QUEUES) {  // (the k = 1 and tile-minimum launches carry no keys)
           const uint32_t tk = args.thr_key[q];
           thr = tk == NAN_KEY ? PASS_ALL : key_value(tk, LARGEST);
         }

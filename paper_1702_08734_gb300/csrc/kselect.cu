@@ -92,7 +92,9 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
   const int64_t sample = (n4 < (int64_t)C::CHUNK / 4 ? n4 : (int64_t)C::CHUNK / 4) * 4;
   constexpr int GROUPS = 4;  // minima per thread (groups of PT / 4 values)
   const int64_t r64 = n > 0 ? (5 * (int64_t)k * sample) / (4 * n) + 8 : 0;
-  const bool use_guess = k > 32 && r64 < (int64_t)(GROUPS * THREADS / 2) &&
+  // (the rank-th minimum is found by a compaction to `rank`, so rank may not exceed the
+  // kept set's capacity KP: on short rows 1.25 k sample/n + 8 can, e.g. k = 125, n = 2606)
+  const bool use_guess = k > 32 && r64 < (int64_t)(GROUPS * THREADS / 2) && r64 <= KP &&
                          sample >= 4 * (int64_t)THREADS;
   const int rank = (int)r64;
   float ht_v = 0.f;  // this thread's head / tail element, offered after the guess
