@@ -166,11 +166,13 @@ typedef struct gbk_knn_opts {
   int32_t prefilter;  /* threshold pre-pass of the fused selection: -1 off, 1 on for
                          k > 1, 0 on for k >= 32 (64 with GBK_PREC_TF32X3; BF16/FP8
                          count the over-fetched k'); either only where the database holds
-                         at least 4k blocks of 64 rows (128 with GBK_PREC_TF32X3).  The
+                         at least 2k blocks of 64 rows (128 with GBK_PREC_TF32X3).  The
                          pre-pass takes the best distance of every (query, block) over
-                         the first sixth of the database; their k-th best bounds the
-                         k-th nearest distance, so the fused selection starts with that
-                         threshold.  Results are the same either way.                    */
+                         the first quarter of the database (the float32-accurate kinds
+                         in one pass over their high pieces, the k-th best then widened
+                         by a bound on the terms that pass leaves out); their k-th best
+                         bounds the k-th nearest distance, so the fused selection starts
+                         with that threshold.  Results are the same either way.          */
 } gbk_knn_opts;
 
 /*

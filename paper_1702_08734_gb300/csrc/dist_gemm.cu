@@ -570,11 +570,77 @@ gbk_status pairwise_run(const PreparedOperand& Q, const PreparedOperand& B, bool
   return gemm_launch(MODE_STORE, 0, ip, Q, B, a, st, q0, qn);
 }
 
-// thr[q] = ordered key of the k-th best value of row q of Dk [nq][k] (sorted best first)
+// Row norms of the two pieces of a split operand, in the operand's units: hn = s ||hi||,
+// ln = s ||lo|| (s the row scale, 1 without one), accumulated in float32 and rounded up by
+// 2^-20 relative so they bound the exact norms.  One warp per row.  With `maxes` the
+// rows' maxima go there (atomicMax on the bits of non-negative floats) instead of hn, ln.
+template <typename E>
+__global__ void split_norms_kernel(const E* __restrict__ p0, const E* __restrict__ p1,
+                                   const float* __restrict__ scale, int64_t n, int dpad,
+                                   float* __restrict__ hn, float* __restrict__ ln,
+                                   float* __restrict__ maxes) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float mh = 0.f, ml = 0.f;
+  for (int64_t r = w0; r < n; r += nw) {
+    float sh = 0.f, sl = 0.f;
+    for (int t = lane; t < dpad; t += 32) {
+      const float h = (float)p0[r * dpad + t], l = (float)p1[r * dpad + t];
+      sh = fmaf(h, h, sh);
+      sl = fmaf(l, l, sl);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sh += __shfl_xor_sync(FULL_MASK, sh, o);
+      sl += __shfl_xor_sync(FULL_MASK, sl, o);
+    }
+    const float sc = scale ? scale[r] : 1.f;
+    const float h = sqrtf(sh) * sc * (1.f + 0x1p-20f), l = sqrtf(sl) * sc * (1.f + 0x1p-20f);
+    if (maxes) {
+      mh = fmaxf(mh, h);
+      ml = fmaxf(ml, l);
+    } else if (lane == 0) {
+      hn[r] = h;
+      ln[r] = l;
+    }
+  }
+  if (maxes && lane == 0) {
+    atomicMax(reinterpret_cast<unsigned int*>(&maxes[0]), __float_as_uint(mh));
+    atomicMax(reinterpret_cast<unsigned int*>(&maxes[1]), __float_as_uint(ml));
+  }
+}
+
+// thr[q] = ordered key of the k-th best value of row q of Dk [nq][k] (sorted best first).
+// With xh (one-pass pre-pass over the high pieces, hi_only) the value is first widened by
+// a bound on how far the one-pass value a of any row of the prefix can lie from the value
+// v the full pass ranks (so the k rows behind the k-th best a have v within the key):
+//   v - a = -2 (<xh, yl> + <xl, yh>) (L2; without the -2 for inner product) plus both
+//   accumulations' rounding and the epilogue's;  |<xh, yl>| <= ||xh|| ||yl|| (Cauchy-
+//   Schwarz) with the database side's maxima over the prefix (stats: max ||yh||, ||yl||),
+//   the float32 accumulations (at most 4 dpad additions in all) within 4 dpad 2^-21
+//   ||x|| ||y||, the epilogue's rounding within 2^-23 (||y||^2 + 2 ||x|| ||y||).
 __global__ void kth_key_kernel(const float* __restrict__ Dk, int64_t nq, int k, bool largest,
+                               const float* __restrict__ xh, const float* __restrict__ xl,
+                               const float* __restrict__ stats, int dpad,
                                uint32_t* __restrict__ thr) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < nq) thr[q] = ordered_key(Dk[q * k + k - 1], largest);
+  if (q >= nq) return;
+  const float d = Dk[q * k + k - 1];
+  if (!xh || !(fabsf(d) <= 3.0e38f)) {
+    thr[q] = ordered_key(d, largest);
+    return;
+  }
+  const double Xh = xh[q], Xl = xl[q], Yh = stats[0], Yl = stats[1];
+  const double X = Xh + Xl, Y = Yh + Yl;
+  const double cross = Xh * Yl + Xl * Yh;
+  const double acc = 4.0 * dpad * 0x1p-21 * X * Y;
+  const double eps = (largest ? cross + acc + 0x1p-23 * X * Y
+                              : 2.0 * (cross + acc) + 0x1p-23 * (Y * Y + 2.0 * X * Y)) *
+                         (1.0 + 0x1p-10) +
+                     1e-30;
+  const float t = largest ? __double2float_rd((double)d - eps) : __double2float_ru((double)d + eps);
+  thr[q] = ordered_key(t, largest);
 }
 
 // Database tiles of the threshold pre-pass for a fused top-k over `ntiles` tiles (0: none).
@@ -584,14 +650,18 @@ __global__ void kth_key_kernel(const float* __restrict__ Dk, int64_t nq, int k, 
 // candidates (a streamed threshold admits about k (1 + ln(n / k)) of n values, a threshold
 // from a prefix of n / f rows about k (1 + ln f)).  prefilter: -1 off, 1 on for k > 1, 0 on
 // for k >= 32 (k >= 64 with the TF32 split, whose slower GEMM makes the pre-pass dearer).
-// The prefix is a sixth of the database (at least k values, at most a quarter of it):
-// on 10^4 x 10^6 x 128, FP16 split, k = 100 takes 9.8 / 9.5 / 9.2 / 8.9 ms with a prefix of
-// 1/32, 1/16, 1/8, 1/6 (10.6 ms without the pre-pass), k = 32 and k = 256 likewise.
+// The split kinds take the prefix in one MMA pass over their high pieces (the bound then
+// widened, kth_key_kernel); the pass is bound by its epilogue at about the full pass's
+// per-tile time, so the prefix is sized on measurements: a quarter of the database (at
+// least k values, at most half of it).  On 10^4 x 10^6 x 128, FP16 split, k = 100 takes
+// 8.91 / 8.44 / 8.35 ms with a prefix of 1/6, 1/4, 1/3 (11.05 ms without the pre-pass),
+// k = 32 6.55 ms at 1/4 (7.0 without); at k = 10 it costs more than it saves (5.76 ms
+// without, 5.93 at 1/6).
 static int prefilter_tiles(int prefilter, int k, int ntiles, int epi) {
   const int kmin = epi == 1 ? 64 : 32;
   if (prefilter < 0 || k <= 1 || (prefilter == 0 && k < kmin)) return 0;
-  const int ts = std::max((ntiles + 5) / 6, (k + epi - 1) / epi);
-  return 4 * ts <= ntiles ? ts : 0;
+  const int ts = std::max((ntiles + 3) / 4, (k + epi - 1) / epi);
+  return 2 * ts <= ntiles ? ts : 0;
 }
 
 // The threshold pre-pass (see prefilter_tiles) over the first tiles of B: per-(query, tile,
@@ -626,12 +696,47 @@ static gbk_status prefilter_run(const PreparedOperand& Q, const PreparedOperand&
   p.out = mins.as<float>();
   p.ldo = nv;
   p.tile_min = 1;
+  // the split kinds bound with one pass over their high pieces, widened afterwards by the
+  // bound on the two cross terms it leaves out (kth_key_kernel)
+  const bool split = pieces_of(Q.prec) > 1;
+  p.hi_only = split ? 1 : 0;
   if ((r = gemm_launch(MODE_SELECT, 0, ip, Q, B, p, st)) != GBK_OK) return r;
+  Scratch xn, stats;
+  if (split) {
+    ProfScope prof("split_norms", st);
+    if ((r = xn.alloc(sizeof(float) * 2 * (size_t)nq, st)) != GBK_OK) return r;
+    if ((r = stats.alloc(2 * sizeof(float), st)) != GBK_OK) return r;
+    GBK_CUDA_CHECK(cudaMemsetAsync(stats.p, 0, 2 * sizeof(float), st));
+    const int64_t rows = p.nb;
+    const unsigned gb = (unsigned)std::min<int64_t>((rows + 7) / 8, 8ll * device_info().sm_count);
+    const unsigned gq = (unsigned)((nq + 7) / 8);
+    const float* bsc = scaled_of(B.prec) ? B.scale.as<float>() : nullptr;
+    const float* qsc = scaled_of(Q.prec) ? Q.scale.as<float>() : nullptr;
+    float* xh = xn.as<float>();
+    if (gemm_kind(Q.prec) == KIND_FP16X3) {
+      split_norms_kernel<__half><<<gb, 256, 0, st>>>(
+          (const __half*)B.piece[0], (const __half*)B.piece[1], bsc, rows, B.dpad, nullptr,
+          nullptr, stats.as<float>());
+      split_norms_kernel<__half><<<gq, 256, 0, st>>>(
+          (const __half*)Q.piece[0], (const __half*)Q.piece[1], qsc, nq, Q.dpad, xh, xh + nq,
+          nullptr);
+    } else {
+      split_norms_kernel<float><<<gb, 256, 0, st>>>(
+          (const float*)B.piece[0], (const float*)B.piece[1], bsc, rows, B.dpad, nullptr,
+          nullptr, stats.as<float>());
+      split_norms_kernel<float><<<gq, 256, 0, st>>>(
+          (const float*)Q.piece[0], (const float*)Q.piece[1], qsc, nq, Q.dpad, xh, xh + nq,
+          nullptr);
+    }
+    GBK_LAUNCH_CHECK();
+  }
   if ((r = kselect_run(mins.as<float>(), nq, nv, k, ip, Dk.as<float>(), Ik.as<int64_t>(), st,
                        nullptr)) != GBK_OK)
     return r;
   ProfScope prof("kth_key", st);
-  kth_key_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(Dk.as<float>(), nq, k, ip, thr);
+  kth_key_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(
+      Dk.as<float>(), nq, k, ip, split ? xn.as<float>() : nullptr,
+      split ? xn.as<float>() + nq : nullptr, split ? stats.as<float>() : nullptr, Q.dpad, thr);
   GBK_LAUNCH_CHECK();
   return GBK_OK;
 }

@@ -121,6 +121,8 @@ struct GemmArgs {
   int64_t ldo;
   int tile_min;          // SELECT, k = 1: out[q * ldo + tile * EPI + half] = the best value of
                          // each (query, tile, column half) instead of one arg-best per list
+  int hi_only;           // split kinds: one MMA pass over the high pieces (hi x hi) instead of
+                         // three, and only B's high piece loaded (the threshold pre-pass)
   uint32_t* status;
 };
 

@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(as_empty + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   constexpr bool PAIR = QUEUES && EPI == 2;  // the two column halves share a pair bound
+  const bool hi_only = PIECES > 1 && args.hi_only != 0;  // one pass: high pieces only
   volatile uint64_t* sH = reinterpret_cast<volatile uint64_t*>(smem + lay.h_off);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -283,17 +284,18 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           for (int kb = 0; kb < args.nkb; kb++) {
             ok = sm100::mbar_wait(&b_empty[st], ph ^ 1u, args.status, abort_flag);
             if (!ok) break;
-            sm100::mbar_arrive_expect_tx(&b_full[st], (uint32_t)SP * GEMM_TILE_BYTES);
+            sm100::mbar_arrive_expect_tx(&b_full[st], (uint32_t)(hi_only ? SP / PIECES : SP) *
+                                                          GEMM_TILE_BYTES);
             const int x = kb * (128 / T::ELEM);
             unsigned char* dst = sB + (uint32_t)st * SP * GEMM_TILE_BYTES;
             if (args.stream_a) {
               sm100::tma_load_2d(dst, &tmA0, &b_full[st], x, qt * GEMM_BM);
-              if (PIECES > 1)
+              if (PIECES > 1 && !hi_only)
                 sm100::tma_load_2d(dst + GEMM_TILE_BYTES, &tmA1, &b_full[st], x, qt * GEMM_BM);
               dst += PIECES * GEMM_TILE_BYTES;
             }
             sm100::tma_load_2d(dst, &tmB0, &b_full[st], x, t * GEMM_BN);
-            if (PIECES > 1)
+            if (PIECES > 1 && !hi_only)
               sm100::tma_load_2d(dst + GEMM_TILE_BYTES, &tmB1, &b_full[st], x, t * GEMM_BN);
             if (++st == args.stages) {
               st = 0;
@@ -407,12 +409,16 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
                 const uint32_t accum = (kb | ks) != 0 ? 1u : 0u;
                 if (KIND == KIND_TF32X3) {
                   sm100::mma_tf32_ts(d_tmem, at0 + ka, b0 + ko, IDESC, accum);
-                  sm100::mma_tf32_ts(d_tmem, at0 + ka, b1 + ko, IDESC, 1u);
-                  sm100::mma_tf32_ts(d_tmem, at1 + ka, b0 + ko, IDESC, 1u);
+                  if (!hi_only) {
+                    sm100::mma_tf32_ts(d_tmem, at0 + ka, b1 + ko, IDESC, 1u);
+                    sm100::mma_tf32_ts(d_tmem, at1 + ka, b0 + ko, IDESC, 1u);
+                  }
                 } else if (KIND == KIND_FP16X3) {
                   sm100::mma_f16_ts(d_tmem, at0 + ka, b0 + ko, IDESC, accum);
-                  sm100::mma_f16_ts(d_tmem, at0 + ka, b1 + ko, IDESC, 1u);
-                  sm100::mma_f16_ts(d_tmem, at1 + ka, b0 + ko, IDESC, 1u);
+                  if (!hi_only) {
+                    sm100::mma_f16_ts(d_tmem, at0 + ka, b1 + ko, IDESC, 1u);
+                    sm100::mma_f16_ts(d_tmem, at1 + ka, b0 + ko, IDESC, 1u);
+                  }
                 } else if (KIND == KIND_BF16) {
                   sm100::mma_f16_ts(d_tmem, at0 + ka, b0 + ko, IDESC, accum);
                 } else {
@@ -426,12 +432,16 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
               const uint32_t accum = (kb | ks) != 0 ? 1u : 0u;
               if (KIND == KIND_TF32X3) {
                 sm100::mma_tf32(d_tmem, a0 + ko, b0 + ko, IDESC, accum);
-                sm100::mma_tf32(d_tmem, a0 + ko, b1 + ko, IDESC, 1u);
-                sm100::mma_tf32(d_tmem, a1 + ko, b0 + ko, IDESC, 1u);
+                if (!hi_only) {
+                  sm100::mma_tf32(d_tmem, a0 + ko, b1 + ko, IDESC, 1u);
+                  sm100::mma_tf32(d_tmem, a1 + ko, b0 + ko, IDESC, 1u);
+                }
               } else if (KIND == KIND_FP16X3) {
                 sm100::mma_f16(d_tmem, a0 + ko, b0 + ko, IDESC, accum);
-                sm100::mma_f16(d_tmem, a0 + ko, b1 + ko, IDESC, 1u);
-                sm100::mma_f16(d_tmem, a1 + ko, b0 + ko, IDESC, 1u);
+                if (!hi_only) {
+                  sm100::mma_f16(d_tmem, a0 + ko, b1 + ko, IDESC, 1u);
+                  sm100::mma_f16(d_tmem, a1 + ko, b0 + ko, IDESC, 1u);
+                }
               } else if (KIND == KIND_BF16) {
                 sm100::mma_f16(d_tmem, a0 + ko, b0 + ko, IDESC, accum);
               } else {

@@ -229,6 +229,28 @@ def test_prefilter_does_not_change_results(gbk, prec, metric, k):
     assert torch.equal(I0, I1) and torch.equal(D0, D1)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+def test_prefilter_one_pass_bound(gbk, prec, metric):
+    # The split kinds' pre-pass runs one MMA pass over the high pieces and widens its k-th
+    # value by a bound on the two cross terms it leaves out.  Rows here are 40 far-apart
+    # base rows (entries ~50, row scales 2^7..2^8) plus perturbations well below the high
+    # pieces' resolution, so the left-out terms decide the order among thousands of
+    # near-equal rows: a bound that is too tight (a dropped term, a missing row scale)
+    # prunes rows the plain search keeps and the outputs differ.
+    rng = np.random.default_rng(11)
+    d = 64
+    base = 50.0 * rng.standard_normal((40, d))
+    xb = (base[rng.integers(0, 40, 100000)] + 0.05 * rng.standard_normal((100000, d)))
+    xq = base[rng.integers(0, 40, 200)] + 0.05 * rng.standard_normal((200, d))
+    xq = torch.from_numpy(xq.astype(np.float32)).cuda()
+    xb = torch.from_numpy(xb.astype(np.float32)).cuda()
+    for k in (64, 100):
+        D0, I0 = gbk.knn_brute(xq, xb, k, metric=metric, precision=prec, prefilter=-1)
+        D1, I1 = gbk.knn_brute(xq, xb, k, metric=metric, precision=prec, prefilter=1)
+        assert torch.equal(I0, I1) and torch.equal(D0, D1)
+
+
 def test_prefilter_integer_lattice_ties(gbk):
     # exact distances with many ties (duplicated rows, equidistant lattice points): the
     # pre-pass bound equals some rows' distances, which must still be kept, so the lower-id
