@@ -168,11 +168,12 @@ typedef struct gbk_knn_opts {
                          count the over-fetched k'); either only where the database holds
                          at least 2k blocks of 64 rows (128 with GBK_PREC_TF32X3).  The
                          pre-pass takes the best distance of every (query, block) over
-                         the first quarter of the database (the float32-accurate kinds
-                         in one pass over their high pieces, the k-th best then widened
-                         by a bound on the terms that pass leaves out); their k-th best
-                         bounds the k-th nearest distance, so the fused selection starts
-                         with that threshold.  Results are the same either way.          */
+                         the first third (k > 64) or quarter of the database (the
+                         float32-accurate kinds in one pass over their high pieces, the
+                         k-th best then widened by a bound on the terms that pass leaves
+                         out); their k-th best bounds the k-th nearest distance, so the
+                         fused selection starts with that threshold.  Results are the
+                         same either way.                                                */
 } gbk_knn_opts;
 
 /*

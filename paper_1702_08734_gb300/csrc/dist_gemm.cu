@@ -651,16 +651,17 @@ __global__ void kth_key_kernel(const float* __restrict__ Dk, int64_t nq, int k, 
 // from a prefix of n / f rows about k (1 + ln f)).  prefilter: -1 off, 1 on for k > 1, 0 on
 // for k >= 32 (k >= 64 with the TF32 split, whose slower GEMM makes the pre-pass dearer).
 // The split kinds take the prefix in one MMA pass over their high pieces (the bound then
-// widened, kth_key_kernel); the pass is bound by its epilogue at about the full pass's
-// per-tile time, so the prefix is sized on measurements: a quarter of the database (at
-// least k values, at most half of it).  On 10^4 x 10^6 x 128, FP16 split, k = 100 takes
-// 8.91 / 8.44 / 8.35 ms with a prefix of 1/6, 1/4, 1/3 (11.05 ms without the pre-pass),
-// k = 32 6.55 ms at 1/4 (7.0 without); at k = 10 it costs more than it saves (5.76 ms
-// without, 5.93 at 1/6).
+// widened, kth_key_kernel); the pass is bound by its epilogue, so the prefix is sized on
+// measurements: a third of the database for k > 64, a quarter below (at least k values,
+// at most half of it).  On 10^4 x 10^6 x 128, FP16 split, whole calls with a third / a
+// quarter: k = 64 7.12 / 7.01 ms, k = 100 7.96 / 8.01, k = 256 12.9 / 14.7 (half: 22.1);
+// k = 32 main pass 5.17 / 4.91 / 4.86 ms after 1/6, 1/4, 1/3; at k = 10 the pre-pass costs
+// about what it saves and stays off.
 static int prefilter_tiles(int prefilter, int k, int ntiles, int epi) {
   const int kmin = epi == 1 ? 64 : 32;
   if (prefilter < 0 || k <= 1 || (prefilter == 0 && k < kmin)) return 0;
-  const int ts = std::max((ntiles + 3) / 4, (k + epi - 1) / epi);
+  const int f = k > 64 ? 3 : 4;  // 1 / prefix fraction
+  const int ts = std::max((ntiles + f - 1) / f, (k + epi - 1) / epi);
   return 2 * ts <= ntiles ? ts : 0;
 }
 

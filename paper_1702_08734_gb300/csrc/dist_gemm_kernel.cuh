@@ -570,30 +570,45 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
         // One batch = 32 accumulator columns of this lane's row, already in registers.
         auto batch = [&](float (&dist)[32], const int cb) {
           const int cbase = col0 + cb;  // database row of dist[0]
+          // (paired float32 operations: each element rounded as by its scalar form)
           if (SCALED) {
             const float4* bs4 = reinterpret_cast<const float4*>(sY + 128 + cb);
 #pragma unroll
             for (int j4 = 0; j4 < 8; j4++) {
               const float4 y = bs4[j4];
-              dist[j4 * 4 + 0] *= y.x;
-              dist[j4 * 4 + 1] *= y.y;
-              dist[j4 * 4 + 2] *= y.z;
-              dist[j4 * 4 + 3] *= y.w;
+              const float2 lo = __fmul2_rn(make_float2(dist[j4 * 4 + 0], dist[j4 * 4 + 1]),
+                                           make_float2(y.x, y.y));
+              const float2 hi = __fmul2_rn(make_float2(dist[j4 * 4 + 2], dist[j4 * 4 + 3]),
+                                           make_float2(y.z, y.w));
+              dist[j4 * 4 + 0] = lo.x;
+              dist[j4 * 4 + 1] = lo.y;
+              dist[j4 * 4 + 2] = hi.x;
+              dist[j4 * 4 + 3] = hi.y;
             }
           }
           if (!LARGEST) {
             const float4* yn4 = reinterpret_cast<const float4*>(sY + cb);
+            const float2 mm = make_float2(m2, m2);
 #pragma unroll
             for (int j4 = 0; j4 < 8; j4++) {
               const float4 y = yn4[j4];
-              dist[j4 * 4 + 0] = fmaf(m2, dist[j4 * 4 + 0], y.x);
-              dist[j4 * 4 + 1] = fmaf(m2, dist[j4 * 4 + 1], y.y);
-              dist[j4 * 4 + 2] = fmaf(m2, dist[j4 * 4 + 2], y.z);
-              dist[j4 * 4 + 3] = fmaf(m2, dist[j4 * 4 + 3], y.w);
+              const float2 lo = __ffma2_rn(mm, make_float2(dist[j4 * 4 + 0], dist[j4 * 4 + 1]),
+                                           make_float2(y.x, y.y));
+              const float2 hi = __ffma2_rn(mm, make_float2(dist[j4 * 4 + 2], dist[j4 * 4 + 3]),
+                                           make_float2(y.z, y.w));
+              dist[j4 * 4 + 0] = lo.x;
+              dist[j4 * 4 + 1] = lo.y;
+              dist[j4 * 4 + 2] = hi.x;
+              dist[j4 * 4 + 3] = hi.y;
             }
           } else if (SCALED) {
+            const float2 qq = make_float2(qs, qs);
 #pragma unroll
-            for (int j = 0; j < 32; j++) dist[j] *= qs;
+            for (int j = 0; j < 32; j += 2) {
+              const float2 r = __fmul2_rn(make_float2(dist[j], dist[j + 1]), qq);
+              dist[j] = r.x;
+              dist[j + 1] = r.y;
+            }
           }
           const bool ragged = lim < cb + 32;  // columns past nb in this batch (last tile only)
           if (MODE == MODE_STORE) {
@@ -624,7 +639,11 @@ __global__ void __launch_bounds__(gemm_threads(KindTraits<KIND>::EPI), 1)
           // Fast path: the batch's best value (NaN ignored) decides whether any of its 32
           // values can enter; most batches end here once the threshold has settled.
           const float bm = batch_best32<LARGEST>(dist);
-          if (!QUEUES) {
+          if (!QUEUES && MODE == MODE_SELECT && args.tile_min) {
+            // tile minima keep the value only (NaN ignored); the row search below would run
+            // on every tile here, since the running best restarts with each tile
+            bestd = LARGEST ? fmaxf(bestd, bm) : fminf(bestd, bm);
+          } else if (!QUEUES) {
             const bool imp = LARGEST ? bm > bestd : bm < bestd;  // strict: earlier column wins ties
             if (__any_sync(FULL_MASK, imp) && imp) {
               int jj = 31;
