@@ -440,7 +440,8 @@ static int list_chunk_cap(int64_t nq, int epi, int kp) {
 // Chunks S minimising waves x (tiles per chunk + per-item overhead); ties to fewer chunks.
 // The overhead is a chunk's candidate lists learning their threshold again: measured at
 // about 0.9 k tiles per (query tile, chunk) item for k = 16..128 (1e4 - 5e4 queries), none
-// for k = 1.  At most max_chunks (the candidate lists' memory, nq x chunks x lists, grows
+// for k = 1 (callers pass a smaller k where a threshold pre-pass gives every list a
+// near-final key from the start).  At most max_chunks (the candidate lists' memory, nq x chunks x lists, grows
 // with S: with 10^8 queries a rounding gain of a few tiles would otherwise buy 100+
 // chunks and 200 GB of lists).
 int plan_chunks(int nqt, int ntiles, int grid_cap, int k, int max_chunks) {
@@ -781,8 +782,14 @@ static gbk_status select_run(const float* xq, const PreparedOperand& Q, const Pr
   a.nqt = (int)((nq + GEMM_BM - 1) / GEMM_BM);
   a.ntiles = ntiles;
   a.kp = k == 1 ? 1 : std::max(32, 1 << (32 - __builtin_clz((unsigned)(k - 1))));
+  // With the threshold pre-pass every list starts from a near-final key, so a chunk's
+  // lists relearn little: for k >= 64 the plan charges a tenth of the usual per-item
+  // overhead (10^4 x 10^6 x 128: k = 64 / 100 / 256 6.98 -> 6.91, 8.00 -> 7.78,
+  // 12.95 -> 11.91 ms; at k = 32 the usual charge stays, 6.19 against 6.24 ms)
+  const int kplan =
+      (k >= 64 && prefilter_tiles(prefilter, k, ntiles, gemm_epi(Q.prec))) ? (k + 8) / 9 : k;
   a.chunks = chunks_opt > 0 ? std::min(chunks_opt, ntiles)
-                            : plan_chunks(a.nqt, ntiles, device_info().sm_count, k,
+                            : plan_chunks(a.nqt, ntiles, device_info().sm_count, kplan,
                                           list_chunk_cap(nq, gemm_epi(Q.prec), a.kp));
   a.tpc = (ntiles + a.chunks - 1) / a.chunks;
   a.chunks = (ntiles + a.tpc - 1) / a.tpc;
