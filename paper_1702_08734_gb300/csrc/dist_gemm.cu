@@ -160,24 +160,56 @@ __global__ void __launch_bounds__(256)
   typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(smem_raw);
   const int64_t q = blockIdx.x;
   const uint64_t* src = part + q * (int64_t)chunks * kp;
-  const int64_t nper = (int64_t)chunks * k;
   Sel::init(s);
-  __syncthreads();
   uint64_t thr = ~0ull;
-  for (int64_t base = 0; base < nper; base += THREADS) {
-    const int64_t i = base + threadIdx.x;
-    uint64_t c[1];
-    uint32_t mask = 0;
-    if (i < nper) {
-      const int64_t ch = i / k, j = i % k;
-      c[0] = src[ch * kp + j];
-      mask = (c[0] != ~0ull && c[0] <= thr) ? 1u : 0u;
-    }
-    Sel::template push<1>(s, mask, c);
+  if (KP <= 32) {
     __syncthreads();
-    if (s.n_buf > CAP - THREADS) {
-      Sel::compact(s, k);
-      thr = s.thr;
+    const int64_t nper = (int64_t)chunks * k;
+    for (int64_t base = 0; base < nper; base += THREADS) {
+      const int64_t i = base + threadIdx.x;
+      uint64_t c[1];
+      uint32_t mask = 0;
+      if (i < nper) {
+        const int64_t ch = i / k, j = i % k;
+        c[0] = src[ch * kp + j];
+        mask = (c[0] != ~0ull && c[0] <= thr) ? 1u : 0u;
+      }
+      Sel::template push<1>(s, mask, c);
+      __syncthreads();
+      if (s.n_buf > CAP - THREADS) {
+        Sel::compact(s, k);
+        thr = s.thr;
+      }
+    }
+  } else {
+    // Longer lists: rounds of 32 entries of every list still alive, one list per warp
+    // per step (coalesced 256-byte reads).  The first k candidates in give the threshold
+    // (an early compaction), and since each list is sorted, a list whose last entry of a
+    // round misses the threshold has no later entry that passes: it is not read again.
+    constexpr int NW = THREADS / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t* alive = smem_raw + sizeof(typename Sel::Smem);
+    for (int l = threadIdx.x; l < chunks; l += THREADS) alive[l] = 1;
+    __syncthreads();
+    for (int r = 0; r * 32 < k; r++) {
+      for (int l0 = 0; l0 < chunks; l0 += NW) {
+        const int l = l0 + warp;
+        uint64_t c[1] = {~0ull};
+        uint32_t mask = 0;
+        if (l < chunks && alive[l]) {  // warp-uniform
+          const int j = r * 32 + lane;
+          if (j < k) c[0] = src[(int64_t)l * kp + j];
+          mask = (c[0] != ~0ull && c[0] <= thr) ? 1u : 0u;
+          const uint64_t last = __shfl_sync(FULL_MASK, c[0], 31);
+          if (lane == 0 && (last == ~0ull || last > thr)) alive[l] = 0;
+        }
+        Sel::template push<1>(s, mask, c);
+        __syncthreads();
+        if (s.n_buf > CAP - THREADS || (s.n_top < k && s.n_top + s.n_buf >= k)) {
+          Sel::compact(s, k);
+          thr = s.thr;
+        }
+      }
     }
   }
   Sel::finish(s, k);
@@ -205,9 +237,9 @@ gbk_status launch_knn_merge(const uint64_t* part, int64_t nq, int chunks, int kp
                             cudaStream_t st) {
   using Sel = BlockSelect<256, KP, 4096>;
   auto kern = knn_merge_kernel<KP>;
-  GBK_TRY(set_smem_limit(kern, sizeof(typename Sel::Smem)));
-  kern<<<(unsigned)nq, 256, sizeof(typename Sel::Smem), st>>>(part, chunks, kp, k, xnorm,
-                                                              largest, D, I);
+  const size_t smem = sizeof(typename Sel::Smem) + (KP > 32 ? (size_t)chunks : 0);  // + alive
+  GBK_TRY(set_smem_limit(kern, smem));
+  kern<<<(unsigned)nq, 256, smem, st>>>(part, chunks, kp, k, xnorm, largest, D, I);
   GBK_LAUNCH_CHECK();
   return GBK_OK;
 }
