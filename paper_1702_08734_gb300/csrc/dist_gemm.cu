@@ -62,43 +62,91 @@ __global__ void prep_bf16_kernel(const float* __restrict__ x, int64_t n, int d, 
   if (lane == 0) norms[row] = s;
 }
 
+// Rows per warp of prep_fp16x3_kernel: both rows' loads are issued before either is used,
+// doubling the bytes in flight per SM (one row per warp reached 63% of HBM at d = 128).
+constexpr int PREP16_ROWS = 2;
+
 __global__ void prep_fp16x3_kernel(const float* __restrict__ x, int64_t n, int d, int dpad,
                                    __half* __restrict__ hi, __half* __restrict__ lo,
                                    float* __restrict__ scale, float* __restrict__ norms,
                                    int64_t nrows_pad, float pad_norm) {
   const int lane = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-  if (row >= nrows_pad) return;
-  if (row >= n) {
-    if (lane == 0) {
-      norms[row] = pad_norm;
-      scale[row] = 0.f;
+  const int64_t row0 =
+      ((int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * PREP16_ROWS;
+  constexpr int MAXE = 8;  // elements per lane kept in registers (dpad <= 256)
+  const bool in_regs = dpad <= 32 * MAXE;
+  float v[PREP16_ROWS][MAXE];
+  if (in_regs) {
+#pragma unroll
+    for (int r = 0; r < PREP16_ROWS; r++) {
+      const int64_t row = row0 + r;
+#pragma unroll
+      for (int i = 0; i < MAXE; i++) {
+        const int t = lane + 32 * i;
+        v[r][i] = (row < n && t < d) ? x[row * d + t] : 0.f;
+      }
     }
-    return;
-  }
-  float s = 0.f, amax = 0.f;
-  for (int t = lane; t < dpad; t += 32) {
-    const float v = t < d ? x[row * d + t] : 0.f;
-    s = fmaf(v, v, s);
-    amax = fmaxf(amax, fabsf(v));
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s += __shfl_xor_sync(FULL_MASK, s, o);
-    amax = fmaxf(amax, __shfl_xor_sync(FULL_MASK, amax, o));
-  }
-  // s = 2^e with amax / s in [0.5, 1): the scaled row is exact and within FP16's range
-  int e = 0;
-  if (amax > 0.f) frexpf(amax, &e);
-  for (int t = lane; t < dpad; t += 32) {
-    const float v = t < d ? ldexpf(x[row * d + t], -e) : 0.f;
-    const __half h = __float2half_rn(v);
-    hi[row * dpad + t] = h;
-    lo[row * dpad + t] = __float2half_rn(v - __half2float(h));
-  }
-  if (lane == 0) {
-    norms[row] = s;
-    scale[row] = ldexpf(1.f, e);
+  for (int r = 0; r < PREP16_ROWS; r++) {
+    const int64_t row = row0 + r;
+    if (row >= nrows_pad) return;
+    if (row >= n) {
+      if (lane == 0) {
+        norms[row] = pad_norm;
+        scale[row] = 0.f;
+      }
+      continue;
+    }
+    // sum of squares in element order per lane, then across lanes (the same order for
+    // every row length)
+    float s = 0.f, amax = 0.f;
+    if (in_regs) {
+#pragma unroll
+      for (int i = 0; i < MAXE; i++) {
+        if (lane + 32 * i < dpad) {
+          s = fmaf(v[r][i], v[r][i], s);
+          amax = fmaxf(amax, fabsf(v[r][i]));
+        }
+      }
+    } else {
+      for (int t = lane; t < dpad; t += 32) {
+        const float u = t < d ? x[row * d + t] : 0.f;
+        s = fmaf(u, u, s);
+        amax = fmaxf(amax, fabsf(u));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(FULL_MASK, s, o);
+      amax = fmaxf(amax, __shfl_xor_sync(FULL_MASK, amax, o));
+    }
+    // s = 2^e with amax / s in [0.5, 1): the scaled row is exact and within FP16's range
+    int e = 0;
+    if (amax > 0.f) frexpf(amax, &e);
+    if (in_regs) {
+#pragma unroll
+      for (int i = 0; i < MAXE; i++) {
+        const int t = lane + 32 * i;
+        if (t < dpad) {
+          const float u = ldexpf(v[r][i], -e);
+          const __half h = __float2half_rn(u);
+          hi[row * dpad + t] = h;
+          lo[row * dpad + t] = __float2half_rn(u - __half2float(h));
+        }
+      }
+    } else {
+      for (int t = lane; t < dpad; t += 32) {
+        const float u = t < d ? ldexpf(x[row * d + t], -e) : 0.f;
+        const __half h = __float2half_rn(u);
+        hi[row * dpad + t] = h;
+        lo[row * dpad + t] = __float2half_rn(u - __half2float(h));
+      }
+    }
+    if (lane == 0) {
+      norms[row] = s;
+      scale[row] = ldexpf(1.f, e);
+    }
   }
 }
 
@@ -452,7 +500,8 @@ gbk_status prepare_operand(const float* x, int64_t n, int d, int prec, int64_t n
     prep_bf16_kernel<<<blocks, warps * 32, 0, st>>>(x, n, d, dpad, (__nv_bfloat16*)out->piece[0],
                                                    out->norms.as<float>(), nrows_pad, pad_norm);
   else if (kind == KIND_FP16X3)
-    prep_fp16x3_kernel<<<blocks, warps * 32, 0, st>>>(
+    prep_fp16x3_kernel<<<(unsigned)((nrows_pad + warps * PREP16_ROWS - 1) / (warps * PREP16_ROWS)),
+                         warps * 32, 0, st>>>(
         x, n, d, dpad, (__half*)out->piece[0], (__half*)out->piece[1], out->scale.as<float>(),
         out->norms.as<float>(), nrows_pad, pad_norm);
   else
