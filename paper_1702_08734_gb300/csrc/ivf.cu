@@ -58,8 +58,10 @@ __global__ void stage_ids_kernel(const int64_t* __restrict__ ids, int64_t n, int
 }
 
 // codes/ids in list order: position j takes staged vector order[j]; its code is stored
-// rotated by r = (j - start of its list) mod M (byte s = sub-quantizer (s + r) mod M, the
-// layout the scan's conflict-free look-ups need) and, with the term-1 table T [nlist][256][M]
+// rotated by r = ((j - start of its list) mod 32) mod M (byte s = sub-quantizer (s + r) mod
+// M, the layout the scan's conflict-free look-ups need: a lane knows its position modulo
+// the warp width; for M <= 32, a divisor of 32, r is the position mod M) and, with the
+// term-1 table T [nlist][256][M]
 // given, s1[j] = sum_m T[L][code_m][m] is formed in sub-quantizer order.
 __global__ void gather_codes_kernel(const uint8_t* __restrict__ in, const int64_t* __restrict__ order,
                                     int64_t n, int M, const int32_t* __restrict__ st_list,
@@ -71,7 +73,7 @@ __global__ void gather_codes_kernel(const uint8_t* __restrict__ in, const int64_
        j += (int64_t)gridDim.x * blockDim.x) {
     const int64_t src = order[j];
     const int64_t L = st_list[src];
-    const int r = (int)((j - list_off[L]) % M);
+    const int r = (int)(((j - list_off[L]) & 31) % M);
     const uint8_t* c = in + src * M;
     for (int m = 0; m < M; m++) out[j * M + m] = c[(m + r) % M];
     if (T) {
@@ -96,7 +98,7 @@ __global__ void unrotate_codes_kernel(const uint8_t* __restrict__ in, int64_t n,
       if (list_off[mid] <= j) lo = mid;
       else hi = mid;
     }
-    const int r = (int)((j - list_off[lo]) % M);
+    const int r = (int)(((j - list_off[lo]) & 31) % M);
     for (int m = 0; m < M; m++) out[j * M + (m + r) % M] = in[j * M + m];
   }
 }
@@ -158,8 +160,8 @@ gbk_status gbk_ivfpq_create(int32_t d, int32_t nlist, int32_t M, int32_t nbits, 
   if (nbits != 8) return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: only 8-bit codes");
   if (metric != GBK_METRIC_L2)
     return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: IVFADC is defined for L2 (Eq. 6)");
-  if (M != 4 && M != 8 && M != 16 && M != 32)
-    return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: M must be 4, 8, 16 or 32");
+  if (M != 4 && M != 8 && M != 16 && M != 32 && M != 64)
+    return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: M must be 4, 8, 16, 32 or 64");
   if (d / M > 32) return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: d/M must be <= 32");
   gbk_index* ix = new gbk_index();
   ix->d = d;

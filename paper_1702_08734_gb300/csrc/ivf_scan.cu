@@ -13,9 +13,9 @@
 //
 // Bank-conflict-free look-ups: the 32 lanes of a warp look up 32 different codes at once.
 // Stored codes are rotated per list position: the code at position r of its list holds
-// sub-quantizer (s + r) mod M in byte s.  A warp scans 32 consecutive positions of one
-// list, so lane l (= r mod 32) reads sub-table (s + l) mod M at step s, and the tables are
-// laid out so that those 32 reads fall in 32 different banks whatever the codes are.
+// sub-quantizer (s + (r mod 32)) mod M in byte s.  A warp scans 32 consecutive positions of
+// one list, so lane l (= r mod 32) reads sub-table (s + l) mod M at step s, and the tables
+// are laid out so that those 32 reads fall in 32 different banks whatever the codes are.
 #include <algorithm>
 
 #include "common.cuh"
@@ -146,7 +146,8 @@ gbk_status ivf_scan_run(int M, int64_t nq, int nprobe, int k, const int64_t* cl_
   if (M == 8) return scan_k<8>(a, tun, st);
   if (M == 16) return scan_k<16>(a, tun, st);
   if (M == 32) return scan_k<32>(a, tun, st);
-  return set_error(GBK_EUNSUPPORTED, "IVFPQ scan supports M in {4, 8, 16, 32}");
+  if (M == 64) return scan_k<64>(a, tun, st);
+  return set_error(GBK_EUNSUPPORTED, "IVFPQ scan supports M in {4, 8, 16, 32, 64}");
 }
 
 // Work of each query (codes scanned) for longest-first scheduling: key = 31 - log2(work)

@@ -27,17 +27,15 @@ __device__ __forceinline__ void load_code(const uint8_t* codes, int64_t i, uint3
     w[1] = v.y;
     w[2] = v.z;
     w[3] = v.w;
-  } else {
-    const uint4 a = __ldg(reinterpret_cast<const uint4*>(codes) + 2 * i);
-    const uint4 b = __ldg(reinterpret_cast<const uint4*>(codes) + 2 * i + 1);
-    w[0] = a.x;
-    w[1] = a.y;
-    w[2] = a.z;
-    w[3] = a.w;
-    w[4] = b.x;
-    w[5] = b.y;
-    w[6] = b.z;
-    w[7] = b.w;
+  } else {  // 32 or 64 bytes: M / 16 16-byte loads
+#pragma unroll
+    for (int h = 0; h < M / 16; h++) {
+      const uint4 a = __ldg(reinterpret_cast<const uint4*>(codes) + (M / 16) * i + h);
+      w[4 * h + 0] = a.x;
+      w[4 * h + 1] = a.y;
+      w[4 * h + 2] = a.z;
+      w[4 * h + 3] = a.w;
+    }
   }
 }
 
@@ -118,27 +116,34 @@ struct TableStep {
   float base[U];         // term 2 of the list
 };
 
+// Words per row of the table kernel's term-3 table: lane l reads word l + s at step s < M.
+template <int M>
+constexpr int table_row_words() {
+  return M <= 32 ? 64 : 128;
+}
+
 // Byte offset of the table kernel's list records in dynamic shared memory: after the
 // term-3 table and the selection state, rounded up to 16 bytes for the 16-byte records.
-template <int KP>
+template <int M, int KP>
 constexpr size_t table_rec_offset() {
-  return (sizeof(float) * 256 * 64 + sizeof(typename BlockSelect<256, KP, 4096>::Smem) + 15) /
+  return (sizeof(float) * 256 * table_row_words<M>() +
+          sizeof(typename BlockSelect<256, KP, 4096>::Smem) + 15) /
          16 * 16;
 }
 
 template <int M, int KP, int U, int THREADS>
 __global__ void __launch_bounds__(THREADS, 2)
     ivf_scan_table_kernel(const ScanArgs a) {
-  constexpr int CAP = 4096, LW = 64;
+  constexpr int CAP = 4096, LW = table_row_words<M>();
   constexpr int STEP = THREADS * U;
   constexpr uint32_t NONE = 0xffffffffu;
   using Sel = BlockSelect<THREADS, KP, CAP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* lut = reinterpret_cast<float*>(smem_raw);  // [256][64]
+  float* lut = reinterpret_cast<float*>(smem_raw);  // [256][LW]
   typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(lut + 256 * LW);
   // per probed list p: {virtual start, stored position - virtual position, virtual end,
   // term 2}; record npq holds {virtual total, ...}
-  uint4* rec = reinterpret_cast<uint4*>(smem_raw + table_rec_offset<KP>());  // [nprobe + 1]
+  uint4* rec = reinterpret_cast<uint4*>(smem_raw + table_rec_offset<M, KP>());  // [nprobe + 1]
   __shared__ int64_t q_sh;
   __shared__ uint32_t wsum[THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -235,20 +240,37 @@ __global__ void __launch_bounds__(THREADS, 2)
       for (int u = 0; u < U; u++) {
         cc[u] = ~0ull;
         if (b.pos[u] != NONE) {
-          // all M look-ups first, then a pairwise sum: the loads overlap instead of each
-          // waiting on the previous add
-          float t[M];
+          // all look-ups first, then a pairwise sum: the loads overlap instead of each
+          // waiting on the previous add (64-byte codes: four groups of 16, each summed
+          // pairwise, then the group sums pairwise, to bound the registers)
+          constexpr int G = M <= 32 ? M : 16;
+          float gs[M / G];
 #pragma unroll
-          for (int st = 0; st < M; st++) {
-            // (code byte st) * 256 + 4 lane: row of the code, word lane (+ st below)
-            const uint32_t addr = __byte_perm(b.w[u][st >> 2], lane4, 0x6504u | ((st & 3) << 4));
-            t[st] = *reinterpret_cast<const float*>(smem_raw + addr + st * 4);
+          for (int gi = 0; gi < M / G; gi++) {
+            float t[G];
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+              const int st = gi * G + j;
+              uint32_t addr;
+              if constexpr (LW == 64) {
+                // (code byte st) * 256 + 4 lane: row of the code, word lane (+ st below)
+                addr = __byte_perm(b.w[u][st >> 2], lane4, 0x6504u | ((st & 3) << 4));
+              } else {
+                addr = ((b.w[u][st >> 2] >> (8 * (st & 3))) & 255u) * (LW * 4u) + lane4;
+              }
+              t[j] = *reinterpret_cast<const float*>(smem_raw + addr + st * 4);
+            }
+#pragma unroll
+            for (int h = G / 2; h >= 1; h >>= 1)
+#pragma unroll
+              for (int j = 0; j < h; j++) t[j] += t[j + h];
+            gs[gi] = t[0];
           }
 #pragma unroll
-          for (int h = M / 2; h >= 1; h >>= 1)
+          for (int h = M / G / 2; h >= 1; h >>= 1)
 #pragma unroll
-            for (int j = 0; j < h; j++) t[j] += t[j + h];
-          const float dist = b.base[u] + (b.s1[u] + t[0]);
+            for (int j = 0; j < h; j++) gs[j] += gs[j + h];
+          const float dist = b.base[u] + (b.s1[u] + gs[0]);
           if (!(dist > thr)) {  // exact order is settled at compaction
             mask |= 1u << u;
             cc[u] = composite(ordered_key(dist, false), b.pos[u]);
@@ -281,18 +303,19 @@ __global__ void __launch_bounds__(THREADS, 2)
 }
 
 // Direct mode (no precomputed tables).  Block per query; for each probed list the LUT
-// [256][32] holds LUT[m][c] = ||(x - c_L)^m - C_m[c]||^2 at word c*32 + h*M + m for every
-// copy h < 32/M, and lane l (copy h = l / M) reads sub-table (s + l) mod M at step s: 32
-// distinct banks.  Codes are streamed U per thread per step from the list's start, so lane
-// l always holds a position r = l (mod 32) of the list.
+// [256][DW] (DW = 32, or M for 64-byte codes) holds LUT[m][c] = ||(x - c_L)^m - C_m[c]||^2
+// at word c*DW + h*M + m for every copy h < DW/M, and lane l (copy h = l / M) reads
+// sub-table (s + l) mod M at step s: 32 distinct banks.  Codes are streamed U per thread
+// per step from the list's start, so lane l always holds a position r = l (mod 32) of the
+// list.
 template <int M, int KP, int U>
 __global__ void __launch_bounds__(256)
     ivf_scan_direct_kernel(const ScanArgs a) {
-  constexpr int THREADS = 256, CAP = 4096, STEP = THREADS * U;
+  constexpr int THREADS = 256, CAP = 4096, STEP = THREADS * U, DW = M <= 32 ? 32 : M;
   using Sel = BlockSelect<THREADS, KP, CAP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* lut = reinterpret_cast<float*>(smem_raw);  // [256][32]
-  typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(lut + 256 * 32);
+  float* lut = reinterpret_cast<float*>(smem_raw);  // [256][DW]
+  typename Sel::Smem& s = *reinterpret_cast<typename Sel::Smem*>(lut + 256 * DW);
   __shared__ int64_t q_sh;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rot = lane % M, h = lane / M;
@@ -313,17 +336,22 @@ __global__ void __launch_bounds__(256)
       if (L < 0) continue;  // uniform across the block
       const int64_t o0 = a.list_off[L], o1 = a.list_off[L + 1];
       __syncthreads();  // the previous list's look-ups are done
-      // warp w fills rows c of its 32; lane l computes entry (c, m = l mod M) of copy l / M
+      // warp w fills rows c of its 32; lane l computes the entries w = l, l + 32, ... < DW
+      // of row c (entry w: sub-quantizer w mod M, copy w / M)
       for (int i = 0; i < 32; i++) {
-        const int c = warp * 32 + i, m = rot;
-        const float* C = a.pq + ((int64_t)m * 256 + c) * dsub;
-        float v = 0.f;
-        for (int t = 0; t < dsub; t++) {
-          const float r = a.xq[q * a.d + m * dsub + t] - a.coarse[L * a.d + m * dsub + t];
-          const float e2 = r - C[t];
-          v = fmaf(e2, e2, v);
+        const int c = warp * 32 + i;
+#pragma unroll
+        for (int wd = lane; wd < DW; wd += 32) {
+          const int m = wd % M;
+          const float* C = a.pq + ((int64_t)m * 256 + c) * dsub;
+          float v = 0.f;
+          for (int t = 0; t < dsub; t++) {
+            const float r = a.xq[q * a.d + m * dsub + t] - a.coarse[L * a.d + m * dsub + t];
+            const float e2 = r - C[t];
+            v = fmaf(e2, e2, v);
+          }
+          lut[c * DW + wd] = v;
         }
-        lut[c * 32 + lane] = v;
       }
       __syncthreads();
       for (int64_t b0 = o0; b0 < o1; b0 += STEP) {
@@ -341,7 +369,7 @@ __global__ void __launch_bounds__(256)
             for (int st = 0; st < M; st++) {
               const uint32_t c = (w[st >> 2] >> ((st & 3) * 8)) & 255u;
               const int m = (st + rot) & (M - 1);
-              acc += lut[c * 32 + h * M + m];
+              acc += lut[c * DW + h * M + m];
             }
             if (f.pass(acc)) {
               mask |= 1u << u;
@@ -367,9 +395,14 @@ static gbk_status launch_scan(const ScanArgs& a, const ScanTuning& tun, cudaStre
   size_t smem;
   void (*kern)(const ScanArgs);
   int threads = 256;
+  // 64-byte codes: two codes per thread at most (16 code words each in registers)
+  constexpr int UC = M > 32 ? 2 : U;
   if (a.direct) {
-    kern = ivf_scan_direct_kernel<M, KP, U>;
-    smem = sizeof(float) * 256 * 32 + sizeof(typename Sel::Smem);
+    kern = ivf_scan_direct_kernel<M, KP, UC>;
+    smem = sizeof(float) * 256 * (M <= 32 ? 32 : M) + sizeof(typename Sel::Smem);
+  } else if constexpr (M > 32) {
+    kern = ivf_scan_table_kernel<M, KP, UC, 256>;  // a 128 KB table: one block per SM
+    smem = table_rec_offset<M, KP>() + sizeof(uint4) * ((size_t)a.nprobe + 1);
   } else {
     // the selection's shared state does not depend on the block size
     static_assert(sizeof(typename BlockSelect<512, KP, 4096>::Smem) == sizeof(typename Sel::Smem),
@@ -385,7 +418,7 @@ static gbk_status launch_scan(const ScanArgs& a, const ScanTuning& tun, cudaStre
     } else {
       kern = ivf_scan_table_kernel<M, KP, U, 256>;
     }
-    smem = table_rec_offset<KP>() + sizeof(uint4) * ((size_t)a.nprobe + 1);
+    smem = table_rec_offset<M, KP>() + sizeof(uint4) * ((size_t)a.nprobe + 1);
   }
   GBK_TRY(set_smem_limit(kern, smem));
   // persistent mode: blocks_per_sm resident blocks per SM pull queries from the counter
@@ -415,10 +448,11 @@ gbk_status scan_k(const ScanArgs& a, const ScanTuning& tun, cudaStream_t st) {
   return scan_u<M, 1024>(a, tun, st);
 }
 
-// one instantiation per code size (ivf_scan_m4.cu ... ivf_scan_m32.cu)
+// one instantiation per code size (ivf_scan_m4.cu ... ivf_scan_m64.cu)
 extern template gbk_status scan_k<4>(const ScanArgs&, const ScanTuning&, cudaStream_t);
 extern template gbk_status scan_k<8>(const ScanArgs&, const ScanTuning&, cudaStream_t);
 extern template gbk_status scan_k<16>(const ScanArgs&, const ScanTuning&, cudaStream_t);
 extern template gbk_status scan_k<32>(const ScanArgs&, const ScanTuning&, cudaStream_t);
+extern template gbk_status scan_k<64>(const ScanArgs&, const ScanTuning&, cudaStream_t);
 
 }  // namespace gbk

@@ -48,8 +48,8 @@ def _quantizers(d, seed, n=20000, nlist=32, M=16):
     return _CACHE[key]
 
 
-def _index(gbk, d, precomputed, seed=400, nlist=32):
-    x, cen, coarse, books = _quantizers(d, seed, nlist=nlist)
+def _index(gbk, d, precomputed, seed=400, nlist=32, M=16):
+    x, cen, coarse, books = _quantizers(d, seed, nlist=nlist, M=M)
     ix = gbk.IVFPQIndex(d, coarse.shape[0], books.shape[0])
     ix.set_quantizers(torch.from_numpy(coarse).cuda(), torch.from_numpy(books).cuda(),
                       use_precomputed=precomputed)
@@ -120,8 +120,10 @@ def check_strict(D, I, Do, Io, xq, adc, direct, skip=None):
         assert np.all(ids >= 0) and np.unique(ids).size == nf, q
         de, A = adc.dist_and_mag(xq[q], ids)
         _, Ao = adc.dist_and_mag(xq[q], Ik[q][:nf])
-        tol_g = 1e-5 * np.abs(de) if direct else 32 * U32 * A
-        tol_o = 1e-5 * np.abs(Dk[q][:nf]) if direct else 32 * U32 * Ao
+        # table mode: max(32, 2M) u A (the per-vector term-1 sum alone rounds M - 1 times)
+        cm = max(32, 2 * adc.M)
+        tol_g = 1e-5 * np.abs(de) if direct else cm * U32 * A
+        tol_o = 1e-5 * np.abs(Dk[q][:nf]) if direct else cm * U32 * Ao
         # the GPU's distance is its id's ADC distance, and that is the oracle's at the rank
         assert np.all(np.abs(D[q][:nf] - de) <= tol_g), (q, np.abs(D[q][:nf] - de).max())
         assert np.all(np.abs(de - Dk[q][:nf]) <= tol_g + tol_o), q
@@ -156,6 +158,27 @@ def test_pq16_search_matches_oracle(gbk, d, precomputed, nprobe, k):
     nsep = check_strict(D.cpu().numpy(), I.cpu().numpy(), Do, Io, xq, Adc(ex, coarse, books),
                         not precomputed, skip)
     assert nsep >= 0.9 * (~skip).sum() * k  # nearly every rank is decided by its distance
+
+
+@pytest.mark.parametrize("precomputed", [True, False])
+@pytest.mark.parametrize("nprobe,k", [(1, 10), (8, 100)])
+def test_search_64_byte_codes_match_oracle(gbk, precomputed, nprobe, k):
+    # 64-byte codes at d = 128 (sub-vectors of 2): the term-3 table in 128-word rows, the
+    # look-ups summed in groups of 16, codes rotated by list position mod 32; both table
+    # modes against the oracle's ADC search under the same strict check as PQ16
+    ix, x, cen, coarse, books = _index(gbk, 128, precomputed, seed=470, M=64)
+    ex = ix.export()
+    xq = _queries(cen, 480, 200, 128)
+    D, I = ix.search(torch.from_numpy(xq).cuda(), k, nprobe)
+    Do, Io = oracle.ivfadc_search(xq, coarse, books, ex["list_off"], ex["codes"], ex["ids"],
+                                  k + 1, nprobe)
+    skip = _ambiguous_probes(xq, coarse, nprobe)
+    assert skip.mean() <= 0.02
+    nsep = check_strict(D.cpu().numpy(), I.cpu().numpy(), Do, Io, xq, Adc(ex, coarse, books),
+                        not precomputed, skip)
+    # the table-mode bound is 2M u A, four times PQ16's, so more neighbouring ranks fall
+    # within it (74% of them decided by distance at nprobe 8, k = 100; 90% in direct mode)
+    assert nsep >= (0.9 if not precomputed else 0.7) * (~skip).sum() * k
 
 
 def test_scan_shape_does_not_change_results(gbk):
