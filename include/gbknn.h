@@ -274,7 +274,7 @@ gbk_status gbk_kmeans(const float* x, int64_t n, int32_t d, int32_t nc, int32_t 
  * owns its device memory.  Not thread-safe: serialise calls on one index. */
 typedef struct gbk_index gbk_index;
 
-/* d % M == 0, M in {4, 8, 16, 32, 64}, d / M <= 32, nbits == 8, metric == GBK_METRIC_L2 (the
+/* d % M == 0, M a multiple of 4 up to 64, d / M <= 32, nbits == 8, metric == GBK_METRIC_L2 (the
  * paper's IVFADC is defined for L2, Eq. 6; others give GBK_EUNSUPPORTED). */
 gbk_status gbk_ivfpq_create(int32_t d, int32_t nlist, int32_t M, int32_t nbits, int32_t metric,
                             gbk_index** out);

@@ -160,8 +160,8 @@ gbk_status gbk_ivfpq_create(int32_t d, int32_t nlist, int32_t M, int32_t nbits, 
   if (nbits != 8) return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: only 8-bit codes");
   if (metric != GBK_METRIC_L2)
     return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: IVFADC is defined for L2 (Eq. 6)");
-  if (M != 4 && M != 8 && M != 16 && M != 32 && M != 64)
-    return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: M must be 4, 8, 16, 32 or 64");
+  if (M % 4 != 0 || M > 64)
+    return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: M must be a multiple of 4 up to 64");
   if (d / M > 32) return set_error(GBK_EUNSUPPORTED, "gbk_ivfpq_create: d/M must be <= 32");
   gbk_index* ix = new gbk_index();
   ix->d = d;

@@ -142,12 +142,25 @@ gbk_status ivf_scan_run(int M, int64_t nq, int nprobe, int k, const int64_t* cl_
   ScanArgs a{nq,     nprobe, k,     cl_I, cl_D, s1,      t3,   xq,      coarse, pq, d,
              direct ? 1 : 0, list_off, codes, ids, D, I, kq, npq, out_off, order, counter};
   ProfScope prof("ivf_scan", st);
-  if (M == 4) return scan_k<4>(a, tun, st);
-  if (M == 8) return scan_k<8>(a, tun, st);
-  if (M == 16) return scan_k<16>(a, tun, st);
-  if (M == 32) return scan_k<32>(a, tun, st);
-  if (M == 64) return scan_k<64>(a, tun, st);
-  return set_error(GBK_EUNSUPPORTED, "IVFPQ scan supports M in {4, 8, 16, 32, 64}");
+  switch (M) {
+    case 4: return scan_k<4>(a, tun, st);
+    case 8: return scan_k<8>(a, tun, st);
+    case 12: return scan_k<12>(a, tun, st);
+    case 16: return scan_k<16>(a, tun, st);
+    case 20: return scan_k<20>(a, tun, st);
+    case 24: return scan_k<24>(a, tun, st);
+    case 28: return scan_k<28>(a, tun, st);
+    case 32: return scan_k<32>(a, tun, st);
+    case 36: return scan_k<36>(a, tun, st);
+    case 40: return scan_k<40>(a, tun, st);
+    case 44: return scan_k<44>(a, tun, st);
+    case 48: return scan_k<48>(a, tun, st);
+    case 52: return scan_k<52>(a, tun, st);
+    case 56: return scan_k<56>(a, tun, st);
+    case 60: return scan_k<60>(a, tun, st);
+    case 64: return scan_k<64>(a, tun, st);
+    default: return set_error(GBK_EUNSUPPORTED, "IVFPQ scan supports M a multiple of 4 up to 64");
+  }
 }
 
 // Work of each query (codes scanned) for longest-first scheduling: key = 31 - log2(work)

@@ -27,7 +27,7 @@ __device__ __forceinline__ void load_code(const uint8_t* codes, int64_t i, uint3
     w[1] = v.y;
     w[2] = v.z;
     w[3] = v.w;
-  } else {  // 32 or 64 bytes: M / 16 16-byte loads
+  } else if constexpr (M % 16 == 0) {  // 32, 48, 64 bytes: 16-byte loads
 #pragma unroll
     for (int h = 0; h < M / 16; h++) {
       const uint4 a = __ldg(reinterpret_cast<const uint4*>(codes) + (M / 16) * i + h);
@@ -36,7 +36,38 @@ __device__ __forceinline__ void load_code(const uint8_t* codes, int64_t i, uint3
       w[4 * h + 2] = a.z;
       w[4 * h + 3] = a.w;
     }
+  } else if constexpr (M % 8 == 0) {  // 24, 40, 56 bytes: 8-byte loads
+#pragma unroll
+    for (int h = 0; h < M / 8; h++) {
+      const uint2 a = __ldg(reinterpret_cast<const uint2*>(codes) + (M / 8) * i + h);
+      w[2 * h + 0] = a.x;
+      w[2 * h + 1] = a.y;
+    }
+  } else {  // other multiples of 4 bytes: 4-byte loads
+#pragma unroll
+    for (int h = 0; h < M / 4; h++)
+      w[h] = __ldg(reinterpret_cast<const uint32_t*>(codes) + (M / 4) * i + h);
   }
+}
+
+// Pairwise sum of N values in place (t[j] += t[j + h] for h = P/2, ..., 1 with P the
+// power of two >= N; for a power-of-two N the usual halving tree).
+template <int N>
+__device__ __forceinline__ float pair_sum(float (&t)[N]) {
+  constexpr int P = N <= 1 ? 1 : N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : N <= 16 ? 16 : N <= 32 ? 32 : 64;
+#pragma unroll
+  for (int h = P / 2; h >= 1; h >>= 1)
+#pragma unroll
+    for (int j = 0; j < h; j++)
+      if (j + h < N) t[j] += t[j + h];
+  return t[0];
+}
+
+// Code sizes other than 4, 8, 16, 32 bytes get one light launch shape (256 threads, two
+// codes per thread) to keep the number of instantiated kernels small.
+template <int M>
+constexpr bool light_shape() {
+  return (M & (M - 1)) != 0 || M > 32;
 }
 
 struct ScanArgs {
@@ -160,7 +191,7 @@ __global__ void __launch_bounds__(THREADS, 2)
       float4* l4 = reinterpret_cast<float4*>(lut);
       for (int e = tid; e < 256 * LW / 4; e += THREADS) {
         const int c = e / (LW / 4), w4 = e % (LW / 4);  // words 4 w4 .. 4 w4 + 3 of row c
-        const float4 t = __ldg(t3q + (c * M + ((4 * w4) & (M - 1))) / 4);
+        const float4 t = __ldg(t3q + (c * M + (4 * w4) % M) / 4);  // M % 4 == 0: no wrap
         l4[e] = make_float4(-2.f * t.x, -2.f * t.y, -2.f * t.z, -2.f * t.w);
       }
     }
@@ -241,9 +272,9 @@ __global__ void __launch_bounds__(THREADS, 2)
         cc[u] = ~0ull;
         if (b.pos[u] != NONE) {
           // all look-ups first, then a pairwise sum: the loads overlap instead of each
-          // waiting on the previous add (64-byte codes: four groups of 16, each summed
-          // pairwise, then the group sums pairwise, to bound the registers)
-          constexpr int G = M <= 32 ? M : 16;
+          // waiting on the previous add (codes over 32 bytes: groups of 16, 8 or 4 look-ups,
+          // each summed pairwise, then the group sums pairwise, to bound the registers)
+          constexpr int G = M <= 32 ? M : M % 16 == 0 ? 16 : M % 8 == 0 ? 8 : 4;
           float gs[M / G];
 #pragma unroll
           for (int gi = 0; gi < M / G; gi++) {
@@ -260,17 +291,9 @@ __global__ void __launch_bounds__(THREADS, 2)
               }
               t[j] = *reinterpret_cast<const float*>(smem_raw + addr + st * 4);
             }
-#pragma unroll
-            for (int h = G / 2; h >= 1; h >>= 1)
-#pragma unroll
-              for (int j = 0; j < h; j++) t[j] += t[j + h];
-            gs[gi] = t[0];
+            gs[gi] = pair_sum<G>(t);
           }
-#pragma unroll
-          for (int h = M / G / 2; h >= 1; h >>= 1)
-#pragma unroll
-            for (int j = 0; j < h; j++) gs[j] += gs[j + h];
-          const float dist = b.base[u] + (b.s1[u] + gs[0]);
+          const float dist = b.base[u] + (b.s1[u] + pair_sum<M / G>(gs));
           if (!(dist > thr)) {  // exact order is settled at compaction
             mask |= 1u << u;
             cc[u] = composite(ordered_key(dist, false), b.pos[u]);
@@ -303,15 +326,16 @@ __global__ void __launch_bounds__(THREADS, 2)
 }
 
 // Direct mode (no precomputed tables).  Block per query; for each probed list the LUT
-// [256][DW] (DW = 32, or M for 64-byte codes) holds LUT[m][c] = ||(x - c_L)^m - C_m[c]||^2
-// at word c*DW + h*M + m for every copy h < DW/M, and lane l (copy h = l / M) reads
-// sub-table (s + l) mod M at step s: 32 distinct banks.  Codes are streamed U per thread
+// [256][DW] (DW = M ceil(32 / M): 32 for M dividing 32, M above 32) holds LUT[m][c] =
+// ||(x - c_L)^m - C_m[c]||^2 at word c*DW + h*M + m for every copy h < DW/M, and lane l
+// (copy h = l / M) reads sub-table (s + l) mod M at step s: 32 distinct words of a row (32
+// distinct banks when M divides 32 or is 64).  Codes are streamed U per thread
 // per step from the list's start, so lane l always holds a position r = l (mod 32) of the
 // list.
 template <int M, int KP, int U>
 __global__ void __launch_bounds__(256)
     ivf_scan_direct_kernel(const ScanArgs a) {
-  constexpr int THREADS = 256, CAP = 4096, STEP = THREADS * U, DW = M <= 32 ? 32 : M;
+  constexpr int THREADS = 256, CAP = 4096, STEP = THREADS * U, DW = (32 + M - 1) / M * M;
   using Sel = BlockSelect<THREADS, KP, CAP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* lut = reinterpret_cast<float*>(smem_raw);  // [256][DW]
@@ -368,7 +392,13 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int st = 0; st < M; st++) {
               const uint32_t c = (w[st >> 2] >> ((st & 3) * 8)) & 255u;
-              const int m = (st + rot) & (M - 1);
+              int m;
+              if constexpr ((M & (M - 1)) == 0) {
+                m = (st + rot) & (M - 1);
+              } else {
+                m = st + rot;  // < 2M
+                m -= m >= M ? M : 0;
+              }
               acc += lut[c * DW + h * M + m];
             }
             if (f.pass(acc)) {
@@ -395,13 +425,14 @@ static gbk_status launch_scan(const ScanArgs& a, const ScanTuning& tun, cudaStre
   size_t smem;
   void (*kern)(const ScanArgs);
   int threads = 256;
-  // 64-byte codes: two codes per thread at most (16 code words each in registers)
-  constexpr int UC = M > 32 ? 2 : U;
+  // the light shape: two codes per thread (up to 16 code words each in registers)
+  constexpr int UC = light_shape<M>() ? 2 : U;
   if (a.direct) {
     kern = ivf_scan_direct_kernel<M, KP, UC>;
-    smem = sizeof(float) * 256 * (M <= 32 ? 32 : M) + sizeof(typename Sel::Smem);
-  } else if constexpr (M > 32) {
-    kern = ivf_scan_table_kernel<M, KP, UC, 256>;  // a 128 KB table: one block per SM
+    smem = sizeof(float) * 256 * ((32 + M - 1) / M * M) + sizeof(typename Sel::Smem);
+  } else if constexpr (light_shape<M>()) {
+    // (above 32 bytes a 128 KB table: one block per SM)
+    kern = ivf_scan_table_kernel<M, KP, UC, 256>;
     smem = table_rec_offset<M, KP>() + sizeof(uint4) * ((size_t)a.nprobe + 1);
   } else {
     // the selection's shared state does not depend on the block size
@@ -448,11 +479,14 @@ gbk_status scan_k(const ScanArgs& a, const ScanTuning& tun, cudaStream_t st) {
   return scan_u<M, 1024>(a, tun, st);
 }
 
-// one instantiation per code size (ivf_scan_m4.cu ... ivf_scan_m64.cu)
-extern template gbk_status scan_k<4>(const ScanArgs&, const ScanTuning&, cudaStream_t);
-extern template gbk_status scan_k<8>(const ScanArgs&, const ScanTuning&, cudaStream_t);
-extern template gbk_status scan_k<16>(const ScanArgs&, const ScanTuning&, cudaStream_t);
-extern template gbk_status scan_k<32>(const ScanArgs&, const ScanTuning&, cudaStream_t);
-extern template gbk_status scan_k<64>(const ScanArgs&, const ScanTuning&, cudaStream_t);
+// instantiations: one translation unit per power-of-two code size (ivf_scan_m4.cu ...
+// ivf_scan_m64.cu), the other multiples of 4 bytes grouped (ivf_scan_m12_28.cu, ...)
+#define GBK_SCAN_SIZE(M) \
+  extern template gbk_status scan_k<M>(const ScanArgs&, const ScanTuning&, cudaStream_t);
+GBK_SCAN_SIZE(4) GBK_SCAN_SIZE(8) GBK_SCAN_SIZE(12) GBK_SCAN_SIZE(16) GBK_SCAN_SIZE(20)
+GBK_SCAN_SIZE(24) GBK_SCAN_SIZE(28) GBK_SCAN_SIZE(32) GBK_SCAN_SIZE(36) GBK_SCAN_SIZE(40)
+GBK_SCAN_SIZE(44) GBK_SCAN_SIZE(48) GBK_SCAN_SIZE(52) GBK_SCAN_SIZE(56) GBK_SCAN_SIZE(60)
+GBK_SCAN_SIZE(64)
+#undef GBK_SCAN_SIZE
 
 }  // namespace gbk

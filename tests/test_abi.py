@@ -62,7 +62,10 @@ def test_index_argument_errors_need_no_gpu(lib):
     lib.gbk_ivfflat_destroy.argtypes = [vp]
     h = ctypes.c_void_p()
     assert lib.gbk_ivfpq_create(30, 16, 8, 8, 0, ctypes.byref(h)) == 1   # M does not divide d
-    assert lib.gbk_ivfpq_create(36, 16, 12, 8, 0, ctypes.byref(h)) == 5  # M = 12 unsupported
+    assert lib.gbk_ivfpq_create(30, 16, 10, 8, 0, ctypes.byref(h)) == 5  # M not a multiple of 4
+    assert lib.gbk_ivfpq_create(136, 16, 68, 8, 0, ctypes.byref(h)) == 5  # M above 64
+    assert lib.gbk_ivfpq_create(36, 16, 12, 8, 0, ctypes.byref(h)) == 0  # 12-byte codes
+    lib.gbk_ivfpq_destroy(h)
     assert lib.gbk_ivfpq_create(32, 16, 8, 8, 1, ctypes.byref(h)) == 5   # inner product
     assert lib.gbk_ivfpq_create(32, 16, 4, 8, 0, ctypes.byref(h)) == 0   # 4-byte codes
     assert lib.gbk_ivfpq_set_coarse_precision(h, 7) == 1

@@ -181,6 +181,31 @@ def test_search_64_byte_codes_match_oracle(gbk, precomputed, nprobe, k):
     assert nsep >= (0.9 if not precomputed else 0.7) * (~skip).sum() * k
 
 
+@pytest.mark.parametrize("precomputed", [True, False])
+@pytest.mark.parametrize("d,M", [(96, 12), (120, 20), (96, 24), (112, 28), (108, 36), (120, 40),
+                                 (132, 44), (96, 48), (104, 52), (112, 56), (120, 60)])
+def test_search_other_multiples_of_4_match_oracle(gbk, precomputed, d, M):
+    # code sizes between the powers of two (the light launch shape: 4-, 8- or 16-byte code
+    # loads, pairwise sums over lengths that are not powers of two, a direct LUT of
+    # M ceil(32 / M) words per row) against the oracle's ADC search, strict check
+    x, cen, coarse, books = _quantizers(d, 500 + M, n=12000, M=M)
+    ix = gbk.IVFPQIndex(d, coarse.shape[0], M)
+    ix.set_quantizers(torch.from_numpy(coarse).cuda(), torch.from_numpy(books).cuda(),
+                      use_precomputed=precomputed)
+    ix.add(torch.from_numpy(x).cuda())
+    ex = ix.export()
+    xq = _queries(cen, 510 + M, 100, d)
+    k, nprobe = 50, 8
+    D, I = ix.search(torch.from_numpy(xq).cuda(), k, nprobe)
+    Do, Io = oracle.ivfadc_search(xq, coarse, books, ex["list_off"], ex["codes"], ex["ids"],
+                                  k + 1, nprobe)
+    skip = _ambiguous_probes(xq, coarse, nprobe)
+    assert skip.mean() <= 0.03
+    nsep = check_strict(D.cpu().numpy(), I.cpu().numpy(), Do, Io, xq, Adc(ex, coarse, books),
+                        not precomputed, skip)
+    assert nsep >= (0.85 if not precomputed else 0.6) * (~skip).sum() * k
+
+
 def test_scan_shape_does_not_change_results(gbk):
     # block size, codes per thread and query order change the schedule, not the arithmetic
     ix, x, cen, coarse, books = _index(gbk, 128, True)

@@ -77,9 +77,9 @@ def _index_with_oracle_quantizers(gbk, seed, n=20000, d=32, nlist=16, M=8, preco
     return ix, x, coarse, books
 
 
-@pytest.mark.parametrize("M", [4, 8, 16, 32, 64])
-def test_encode_and_lists_match_oracle(gbk, M):
-    d = 64
+@pytest.mark.parametrize("d,M", [(64, 4), (64, 8), (64, 16), (64, 32), (64, 64), (96, 12),
+                                 (96, 24), (96, 48), (120, 20), (120, 60)])
+def test_encode_and_lists_match_oracle(gbk, d, M):
     ix, x, coarse, books = _index_with_oracle_quantizers(gbk, 30 + M, d=d, M=M)
     ex = ix.export()
     lists, codes = oracle.ivfpq_encode(x, coarse, books)
